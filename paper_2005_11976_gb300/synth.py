@@ -1,0 +1,295 @@
+"""Seeded synthetic inputs: scan descriptions, phantoms, weight maps, noise.
+
+This module is shared by the tests, the benchmark and the oracle checks.  It holds no
+reconstruction arithmetic (no rays, no intersection lengths, no SART): only the
+description of each workload and the voxel values of the phantoms placed on the
+cylindrical grid.
+
+Workloads mirror the parts the paper inspects (Sec. 2.4 and 3.3: axisymmetric
+industrial parts with metal inserts, some with a component missing).  Sizes follow
+the five workloads the library is benchmarked on:
+
+* ``tiny``      grid (16, 64, 16), R 10 mm, H 20 mm; SOD 100, SDD 400; 32 views over
+                360 deg; 32x32 detector at 1.6 mm; mu = 0.02/mm cylinder with two
+                full-height r = 2 mm holes at r = 5 mm, seeded azimuths.
+* ``medium``    grid (128, 512, 128), R 25, H 50; SOD 200, SDD 800; 180 views;
+                256x256 detector at 0.8 mm; five concentric shells plus eight r = 2 mm
+                inserts at r = 15 mm (one removed); seeded pose |T| <= 2 mm, beta <= 1 deg.
+* ``precision`` grid (256, 1024, 256); 360 views; 512x512 detector at 0.4 mm.
+* ``batched``   64 scans on the medium grid, N_p in {60, 90, 120, 180}, T in +-5 mm,
+                beta in +-3 deg.
+* ``serving``   Poisson arrivals of mixed part types (64,256,64) / (128,512,128) /
+                (256,1024,256) with detectors 128^2 / 256^2 / 512^2.
+
+Seeds: numpy PCG64, base seed 20051197 + workload index; per-scan seed = base + scan id.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+BASE_SEED = 20051197
+WORKLOAD_INDEX = {"tiny": 0, "medium": 1, "precision": 2, "batched": 3, "serving": 4}
+
+
+@dataclasses.dataclass
+class Scan:
+    """One scan: cylindrical grid, circular cone-beam geometry and object pose.
+
+    Lengths in mm, angles in radians.  ``angles`` are the stage angles phi_p.
+    """
+    n_h: int
+    n_theta: int
+    n_r: int
+    radius: float
+    height: float
+    sod: float
+    sdd: float
+    det_w: int
+    det_h: int
+    pitch_u: float
+    pitch_v: float
+    angles: np.ndarray
+    off_u: float = 0.0
+    off_v: float = 0.0
+    alpha: float = 0.0
+    beta: float = 0.0
+    gamma: float = 0.0
+    tx: float = 0.0
+    ty: float = 0.0
+    tz: float = 0.0
+
+    @property
+    def n_proj(self) -> int:
+        return int(len(self.angles))
+
+    @property
+    def vol_shape(self):
+        return (self.n_h, self.n_theta, self.n_r)
+
+    @property
+    def sino_shape(self):
+        return (self.n_proj, self.det_h, self.det_w)
+
+    @property
+    def n_vox(self) -> int:
+        return self.n_h * self.n_theta * self.n_r
+
+    @property
+    def n_rays(self) -> int:
+        return self.n_proj * self.det_h * self.det_w
+
+    def fields(self) -> dict:
+        return dataclasses.asdict(self)
+
+
+def rng_for(workload: str, scan_id: int = 0) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(BASE_SEED + WORKLOAD_INDEX[workload] + scan_id))
+
+
+def full_circle(n_proj: int) -> np.ndarray:
+    """Equally spaced stage angles over 360 degrees."""
+    return 2.0 * math.pi * np.arange(n_proj) / n_proj
+
+
+def limited_arc(n_proj: int, last_angle_deg: float) -> np.ndarray:
+    """n_proj angles from 0 to the last scan angle inclusive (the Table 1 style of scan)."""
+    return np.deg2rad(last_angle_deg) * np.arange(n_proj) / max(n_proj - 1, 1)
+
+
+# --------------------------------------------------------------------------- scans
+
+def tiny_scan() -> Scan:
+    return Scan(16, 64, 16, 10.0, 20.0, 100.0, 400.0, 32, 32, 1.6, 1.6, full_circle(32))
+
+
+def medium_scan(pose_seed_rng: np.random.Generator | None = None, n_proj: int = 180,
+                grid=(128, 512, 128), det: int = 256, pitch: float = 0.8,
+                pose=None) -> Scan:
+    n_h, n_t, n_r = grid
+    s = Scan(n_h, n_t, n_r, 25.0, 50.0, 200.0, 800.0, det, det, pitch, pitch,
+             full_circle(n_proj))
+    if pose is not None:
+        s.alpha, s.beta, s.gamma, s.tx, s.ty, s.tz = pose
+    elif pose_seed_rng is not None:
+        s.alpha, s.beta, s.gamma, s.tx, s.ty, s.tz = seeded_pose(pose_seed_rng, 2.0, 1.0)
+    return s
+
+
+def precision_scan(rng: np.random.Generator | None = None) -> Scan:
+    return medium_scan(rng, n_proj=360, grid=(256, 1024, 256), det=512, pitch=0.4)
+
+
+def seeded_pose(rng: np.random.Generator, t_max_mm: float, tilt_max_deg: float):
+    """(alpha, beta, gamma, tx, ty, tz): |T| <= t_max, |beta| <= tilt_max."""
+    while True:
+        t = rng.uniform(-t_max_mm, t_max_mm, size=3)
+        if np.linalg.norm(t) <= t_max_mm:
+            break
+    alpha = rng.uniform(0.0, 2.0 * math.pi)
+    beta = math.radians(rng.uniform(-tilt_max_deg, tilt_max_deg))
+    gamma = rng.uniform(0.0, 2.0 * math.pi)
+    return (alpha, beta, gamma, float(t[0]), float(t[1]), float(t[2]))
+
+
+def batched_scans(n_scans: int = 64, base: str = "batched"):
+    """Scans of one part type: N_p ~ U{60,90,120,180}, T ~ U[-5,5]^3 mm, beta ~ U[-3,3] deg."""
+    out = []
+    for i in range(n_scans):
+        rng = rng_for(base, i)
+        n_proj = int(rng.choice([60, 90, 120, 180]))
+        t = rng.uniform(-5.0, 5.0, size=3)
+        pose = (rng.uniform(0, 2 * math.pi), math.radians(rng.uniform(-3.0, 3.0)),
+                rng.uniform(0, 2 * math.pi), float(t[0]), float(t[1]), float(t[2]))
+        out.append(medium_scan(n_proj=n_proj, pose=pose))
+    return out
+
+
+SERVING_PART_TYPES = {
+    "small": dict(grid=(64, 256, 64), det=128),
+    "medium": dict(grid=(128, 512, 128), det=256),
+    "large": dict(grid=(256, 1024, 256), det=512),
+}
+
+
+def serving_stream(rate_per_s: float = 20.0, duration_s: float = 60.0, seed_offset: int = 0,
+                   part_types=("small", "medium", "large"), n_proj_choices=(60, 90, 120, 180, 240, 360)):
+    """Poisson arrival stream: list of (arrival_s, part_type, Scan, removed_insert or -1)."""
+    rng = rng_for("serving", seed_offset)
+    t = 0.0
+    out = []
+    k = 0
+    while True:
+        t += rng.exponential(1.0 / rate_per_s)
+        if t > duration_s:
+            break
+        pt = part_types[int(rng.integers(len(part_types)))]
+        cfg = SERVING_PART_TYPES[pt]
+        n_proj = int(rng.choice(list(n_proj_choices)))
+        pose = seeded_pose(rng, 2.0, 1.0)
+        scan = medium_scan(n_proj=n_proj, grid=cfg["grid"], det=cfg["det"],
+                           pitch=204.8 / cfg["det"], pose=pose)
+        removed = int(rng.integers(8)) if rng.uniform() < 0.1 else -1
+        out.append((t, pt, scan, removed))
+        k += 1
+    return out
+
+
+# ------------------------------------------------------------------------- phantoms
+
+def _annulus_fraction(scan: Scan, r_a: float, r_b: float) -> np.ndarray:
+    """Area fraction of each radial bin covered by r_a <= r <= r_b (exact)."""
+    dr = scan.radius / scan.n_r
+    lo = np.arange(scan.n_r) * dr
+    hi = lo + dr
+    a = np.clip(np.maximum(lo, r_a), None, None)
+    b = np.minimum(hi, r_b)
+    cov = np.where(b > a, b * b - a * a, 0.0)
+    return cov / (hi * hi - lo * lo)
+
+
+def _disk_fraction(scan: Scan, cx: float, cy: float, rad: float, ss: int = 8) -> np.ndarray:
+    """(n_theta, n_r) area fraction of each (theta, r) cell inside a disk, by ss x ss
+    samples uniform in (r^2, theta) per cell (equal-area sampling)."""
+    n_t, n_r = scan.n_theta, scan.n_r
+    dr = scan.radius / n_r
+    dth = 2.0 * math.pi / n_t
+    frac = np.zeros((n_t, n_r))
+    dc = math.hypot(cx, cy)
+    r_lo = max(dc - rad, 0.0)
+    r_hi = dc + rad
+    ir0 = max(int(r_lo / dr) - 1, 0)
+    ir1 = min(int(r_hi / dr) + 2, n_r)
+    off = (np.arange(ss) + 0.5) / ss
+    for ir in range(ir0, ir1):
+        r2 = ((ir * dr) ** 2 + off * (((ir + 1) * dr) ** 2 - (ir * dr) ** 2))
+        rs = np.sqrt(r2)
+        if dc - rad > 1e-12 + (ir + 1) * dr or dc + rad < ir * dr - 1e-12:
+            continue
+        if dc > rad:
+            half = math.asin(min(rad / max(dc, 1e-12), 1.0))
+            phi = math.atan2(cy, cx) % (2 * math.pi)
+            it = np.arange(int(math.floor((phi - half) / dth)) - 1,
+                           int(math.floor((phi + half) / dth)) + 2) % n_t
+            it = np.unique(it)
+        else:
+            it = np.arange(n_t)
+        th = (it[:, None] + off[None, :]) * dth          # (cells, ss)
+        x = rs[None, None, :] * np.cos(th)[:, :, None]
+        y = rs[None, None, :] * np.sin(th)[:, :, None]
+        inside = (x - cx) ** 2 + (y - cy) ** 2 <= rad * rad
+        frac[it, ir] = inside.mean(axis=(1, 2))
+    return frac
+
+
+def _slab_fraction(scan: Scan, h_a: float, h_b: float) -> np.ndarray:
+    dh = scan.height / scan.n_h
+    lo = -0.5 * scan.height + np.arange(scan.n_h) * dh
+    hi = lo + dh
+    return np.clip(np.minimum(hi, h_b) - np.maximum(lo, h_a), 0.0, None) / dh
+
+
+def tiny_phantom(scan: Scan, rng: np.random.Generator) -> np.ndarray:
+    """mu = 0.02/mm over the whole grid cylinder with two full-height r = 2 mm holes
+    centred at r = 5 mm, at seeded azimuths."""
+    x = np.full(scan.vol_shape, 0.02)
+    for _ in range(2):
+        phi = rng.uniform(0.0, 2.0 * math.pi)
+        f = _disk_fraction(scan, 5.0 * math.cos(phi), 5.0 * math.sin(phi), 2.0)
+        x *= (1.0 - f)[None, :, :]
+    return x
+
+
+def insert_azimuths(rng: np.random.Generator, n: int = 8) -> np.ndarray:
+    """Seeded insert azimuths: evenly spread with a jitter, so inserts never overlap."""
+    base = 2.0 * math.pi * np.arange(n) / n
+    return base + rng.uniform(-0.25, 0.25, size=n) * (2.0 * math.pi / n)
+
+
+def part_phantom(scan: Scan, azimuths: np.ndarray, removed: int = -1,
+                 insert_mu: float = 0.10) -> np.ndarray:
+    """Five equal concentric shells, mu 0.05 .. 0.01/mm inner to outer, plus r = 2 mm
+    inserts (mu 0.10/mm) centred at 0.6 R over h in [-H/4, H/4]; insert ``removed``
+    (if >= 0) is left out (the missing component)."""
+    R = scan.radius
+    radial = np.zeros(scan.n_r)
+    mus = [0.05, 0.04, 0.03, 0.02, 0.01]
+    for k, mu in enumerate(mus):
+        radial += mu * _annulus_fraction(scan, k * R / 5.0, (k + 1) * R / 5.0)
+    x = np.broadcast_to(radial, scan.vol_shape).copy()
+    hf = _slab_fraction(scan, -0.25 * scan.height, 0.25 * scan.height)
+    rc = 0.6 * R
+    rad = 0.08 * R
+    for k, phi in enumerate(azimuths):
+        if k == removed:
+            continue
+        f = _disk_fraction(scan, rc * math.cos(phi), rc * math.sin(phi), rad)
+        # the insert replaces the shell material it occupies
+        x += hf[:, None, None] * f[None, :, :] * (insert_mu - radial[None, None, :])
+    return x
+
+
+def roi_weights(scan: Scan, r_a: float = 12.0, r_b: float = 18.0, inside: float = 4.0,
+                scale_to_radius: bool = True) -> np.ndarray:
+    """Weight map on the grid: ``inside`` for voxel centres in the annulus r_a..r_b, 1
+    elsewhere (radii given for R = 25 mm and scaled with the grid radius)."""
+    dr = scan.radius / scan.n_r
+    rc = (np.arange(scan.n_r) + 0.5) * dr
+    s = scan.radius / 25.0 if scale_to_radius else 1.0
+    wr = np.where((rc >= r_a * s) & (rc <= r_b * s), inside, 1.0)
+    return np.broadcast_to(wr, scan.vol_shape).copy()
+
+
+def random_volume(scan: Scan, rng: np.random.Generator, lo=0.0, hi=0.05) -> np.ndarray:
+    return rng.uniform(lo, hi, size=scan.vol_shape)
+
+
+def random_sinogram(scan: Scan, rng: np.random.Generator, lo=0.0, hi=2.0) -> np.ndarray:
+    return rng.uniform(lo, hi, size=scan.sino_shape)
+
+
+def poisson_counts(p_clean: np.ndarray, i0: float, rng: np.random.Generator) -> np.ndarray:
+    """Detector counts for line integrals p_clean: I ~ Poisson(I0 exp(-p))."""
+    return rng.poisson(i0 * np.exp(-np.asarray(p_clean, dtype=np.float64))).astype(np.float64)
