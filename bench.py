@@ -1,0 +1,371 @@
+#!/usr/bin/env python3
+"""Benchmark: SART reconstruction of the medium cylindrical workload on GB300.
+
+Workload (one "step" = one whole reconstruction of one scan, every stage of the path):
+  grid (N_h, N_theta, N_r) = (128, 512, 128), R 25 mm, H 50 mm; SOD 200, SDD 800 mm;
+  180 views over 360 deg; 256 x 256 detector at 0.8 mm; seeded pose (|T| <= 2 mm,
+  tilt <= 1 deg); five-shell part with eight inserts, one removed; Poisson counts at
+  I0 = 1e4.  Step = re-pose the plan (ray tables) -> log transform of the counts ->
+  20 SART sweeps (lambda 0.5) warm-started from the defect-free part's volume, with a
+  4x weight inside the annulus r in [12, 18] mm.
+
+Output: one JSON line (rank 0).  value = SART sweeps per second (whole job), with
+GRays/s, the roofline of the dominant kernel, the CPU oracle baseline and the
+end-to-end (host buffers) figure alongside.  ``--impl reference`` times the FP64 CPU
+oracle instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SART iters/sec and GRays/s at stated rel err; batched-serve vs plain scans/s, p99"
+UNIT = "SART iters/s"
+N_ITER = 20
+LAMBDA = 0.5
+I0 = 1.0e4
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload(rank: int = 0):
+    from paper_2005_11976_gb300 import synth
+    rng = synth.rng_for("medium", rank)
+    scan = synth.medium_scan(rng)
+    az = synth.insert_azimuths(rng)
+    removed = int(rng.integers(8))
+    x_part = synth.part_phantom(scan, az, removed=removed)     # the scanned part
+    x_warm = synth.part_phantom(scan, az)                       # defect-free warm start
+    w = synth.roi_weights(scan)
+    return scan, x_part, x_warm, w, removed
+
+
+def oracle_sample(scan, x_warm, counts_view, w, view: int):
+    """FP64 oracle on one SART subset (one view) of the workload: (seconds, volume)."""
+    import dataclasses
+    import oracle
+    s1 = dataclasses.replace(scan, angles=scan.angles[view:view + 1])
+    o = oracle.Setup(**s1.fields())
+    t0 = time.perf_counter()
+    p = oracle.log_transform(counts_view, I0)
+    x1 = oracle.sart(o, p, x0=x_warm, w=w, n_iter=1, lam=LAMBDA)
+    return time.perf_counter() - t0, x1, o
+
+
+def run_reference(args):
+    """The FP64 CPU oracle as it stands, timed on this host's cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2005_11976_gb300 import synth
+    oracle.build()
+    scan, x_part, x_warm, w, _ = workload(0)
+    rng = np.random.default_rng(5)
+    # counts for one view from the oracle's own projection of the part
+    view = 37
+    import dataclasses
+    s1 = dataclasses.replace(scan, angles=scan.angles[view:view + 1])
+    p_clean = oracle.project(oracle.Setup(**s1.fields()), x_part)
+    counts = synth.poisson_counts(p_clean, I0, rng)
+    times = []
+    for k in range(args.warmup + args.steps):
+        dt, _, _ = oracle_sample(scan, x_warm, counts, w, view)
+        if k >= args.warmup:
+            times.append(dt)
+    t_subset = sum(times) / len(times)
+    value = 1.0 / (t_subset * scan.n_proj)
+    cores = oracle.num_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_subset * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "medium plain SART (128,512,128) grid, 180 views 256x256, 20 sweeps",
+                   "sample": "one SART subset (view 37) per step, scaled x180 views"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "one SART subset (1 of 180 views) of the medium workload per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--graph", action="store_true",
+                    help="replay captured graphs instead of instrumented eager launches")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2005_11976_gb300 import build as cbuild
+    from paper_2005_11976_gb300 import cylct, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or not os.path.exists(cylct.LIB_PATH):
+        cbuild.build()
+    if world > 1:
+        dist.barrier()
+    lib = cylct.load()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    scan, x_part, x_warm, w, removed = workload(rank)
+    n_vox, n_pix = scan.n_vox, scan.det_w * scan.det_h
+    plan = cylct.Plan(scan, device=local)
+    pose = (scan.alpha, scan.beta, scan.gamma, scan.tx, scan.ty, scan.tz)
+
+    # synthetic data: project the part on the GPU, draw Poisson counts (seeded)
+    xp = torch.from_numpy(x_part.astype(np.float32)).to(dev)
+    p_clean = torch.empty(scan.sino_shape, dtype=torch.float32, device=dev)
+    plan.cyl_project(xp, cylct.CYL_F32, 0, scan.n_proj, p_clean, cylct.CYL_F32, stream)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(20051197 + rank)
+    counts = torch.poisson(I0 * torch.exp(-p_clean), generator=gen)
+    del xp
+    x0 = torch.from_numpy(x_warm.astype(np.float32)).to(dev)
+    wd = torch.from_numpy(w.astype(np.float32)).to(dev)
+    p = torch.empty_like(counts)
+    x_out = torch.empty(scan.vol_shape, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
+    prm = cylct.sart_params(n_iter=N_ITER, lam=LAMBDA, use_graph=bool(args.graph))
+    plan.cyl_plan_set_timing(not args.graph)
+
+    def step(st):
+        plan.cyl_plan_set_pose(pose, st)
+        cylct.cyl_log_transform(counts, cylct.CYL_F32, I0, p, cylct.CYL_F32, counts.numel(), st)
+        plan.cyl_sart_solve(p, cylct.CYL_F32, x0, wd, prm, x_out, cylct.CYL_F32, st)
+
+    for _ in range(args.warmup):
+        step(stream)
+    torch.cuda.synchronize()
+
+    # segments per view (algorithmic bytes of the projector)
+    seg = torch.zeros(scan.n_proj, dtype=torch.int64, device=dev)
+    plan.cyl_count_segments(0, scan.n_proj, seg, stream)
+    torch.cuda.synchronize()
+    seg = seg.cpu().numpy()
+
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall0 = time.perf_counter()
+    step_ms = []
+    k_ms = [0.0, 0.0, 0.0]
+    k_n = [0, 0, 0]
+    for _ in range(args.steps):
+        flush.fill_(1.0)                                # evict L2 between timed steps
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(stream)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        if not args.graph:
+            for k in range(3):
+                ms, n = plan.cyl_plan_kernel_time(k)
+                k_ms[k] += ms
+                k_n[k] += n
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    sweeps = world * args.steps * N_ITER
+    value = sweeps / (total_ms / 1e3)
+    rays_per_sweep = 2 * scan.n_proj * n_pix         # forward + back-projected rays
+    grays = world * args.steps * N_ITER * rays_per_sweep / (total_ms / 1e3) / 1e9
+
+    # --- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        h_counts = counts.cpu().pin_memory()
+        h_out = torch.empty(scan.vol_shape, dtype=torch.float32).pin_memory()
+        d_counts = torch.empty_like(counts)
+
+        def e2e_step(st):
+            d_counts.copy_(h_counts, non_blocking=True)
+            plan.cyl_plan_set_pose(pose, st)
+            cylct.cyl_log_transform(d_counts, cylct.CYL_F32, I0, p, cylct.CYL_F32,
+                                    counts.numel(), st)
+            plan.cyl_sart_solve(p, cylct.CYL_F32, x0, wd, prm, h_out, cylct.CYL_F32, st)
+
+        e2e_step(stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step(stream)
+        torch.cuda.synchronize()
+        e2e_t = time.perf_counter() - t0
+        e2e = {"value": world * args.steps * N_ITER / e2e_t, "unit": UNIT,
+               "h2d_bytes_per_step": int(counts.numel() * 4),
+               "d2h_bytes_per_step": int(n_vox * 4)}
+
+    # --- roofline of the dominant kernel (segment-touch algorithmic bytes)
+    hbm, peak_kind = peaks()
+    kinds = ["forward projection + residual", "matched back-projection (atomic scatter)",
+             "SART update"]
+    roof = None
+    if not args.graph and k_n[0]:
+        S = float(seg.sum())
+        fwd_bytes = (S * 4 + scan.n_proj * n_pix * (4 + 4 + 4)) / scan.n_proj   # x gathers + p, res, L
+        bp_bytes = (S * 4 * 2 + scan.n_proj * n_pix * 4) / scan.n_proj          # num, den + res
+        upd_bytes = n_vox * (4 * 2 + 4 + 4 + 4 + 4 * 2)                          # x rw, num, den, w, clears
+        per = [fwd_bytes, bp_bytes, upd_bytes]
+        avg_ms = [k_ms[k] / k_n[k] for k in range(3)]
+        dom = int(np.argmax(k_ms))
+        achieved = per[dom] / (avg_ms[dom] / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None, "kernel": kinds[dom],
+                "peak_source": peak_kind,
+                "kernel_ms_avg": {kinds[k]: avg_ms[k] for k in range(3)},
+                "kernel_share": {kinds[k]: k_ms[k] / sum(k_ms) for k in range(3)},
+                "segments_per_view": S / scan.n_proj}
+
+    # --- CPU oracle on a bounded sample, and a live parity check on that sample
+    cpu = None
+    parity = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import dataclasses
+        import oracle
+        oracle.build()
+        view = 37
+        dt, x1_or, o = oracle_sample(scan, x_warm, counts[view:view + 1].cpu().numpy().astype(np.float64),
+                                     w, view)
+        cpu = {"value": 1.0 / (dt * scan.n_proj), "unit": UNIT, "cores": oracle.num_threads(),
+               "kind": "oracle",
+               "sample": f"one SART subset (view {view} of {scan.n_proj}) of the medium workload, "
+                         f"{dt:.2f} s, scaled x{scan.n_proj}"}
+        s1 = dataclasses.replace(scan, angles=scan.angles[view:view + 1])
+        with cylct.Plan(s1, device=local) as p1:
+            pv = torch.empty((1,) + scan.sino_shape[1:], dtype=torch.float32, device=dev)
+            cylct.cyl_log_transform(counts[view:view + 1].contiguous(), cylct.CYL_F32, I0, pv,
+                                    cylct.CYL_F32, n_pix, stream)
+            xg = torch.empty_like(x_out)
+            p1.cyl_sart_solve(pv, cylct.CYL_F32, x0, wd, cylct.sart_params(n_iter=1, lam=LAMBDA),
+                              xg, cylct.CYL_F32, stream)
+            torch.cuda.synchronize()
+            xg = xg.cpu().numpy().astype(np.float64)
+        parity = float(np.linalg.norm(xg - x1_or) / np.linalg.norm(x1_or))
+
+    n_launch = args.steps * (1 + N_ITER * scan.n_proj * 3 + 2)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "medium plain SART: grid (128,512,128) R25 H50, 180 views over 360 deg, "
+                               "256x256 det 0.8 mm, SOD 200 SDD 800, 20 sweeps lambda 0.5, warm start, "
+                               "ROI weights 4x, Poisson I0 1e4",
+                   "l2": "flushed (256 MB write) before every timed step",
+                   "launch": "graph" if args.graph else "eager, CUDA events per kernel",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "grays_per_s": grays, "rel_err_vs_oracle_one_subset": parity,
+        "rel_err_bound": "<=1e-5 rel L2 per projection and per iterate (tests)",
+        "wall_s_timed": t_wall, "clocks": clk, "gpu_launches": n_launch,
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

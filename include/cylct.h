@@ -1,0 +1,177 @@
+/*
+ * cylct.h -- C ABI of the GB300 cylindrical-grid SART library (libcylct.so).
+ *
+ * Method: Goethals, Heyndrickx, Boone, "Fast tomographic inspection of cylindrical
+ * objects" (J. Nondestructive Evaluation).  Cone-beam X-ray CT reconstructed by SART
+ * (Eq. 6) on a cylindrical (N_h, N_theta, N_r) grid attached to the part's own axis
+ * (Sec. 2, Eq. 1-2), with an initial volume and a weight map (Sec. 2.2, Sec. 3.3).
+ *
+ * Conventions (the paper leaves them open; every entry point uses these):
+ *   - Lab frame: source at (-SOD, 0, 0); detector plane x = SDD - SOD, columns u along
+ *     +y, rows v along +z; pixel (iu, iv) centre at
+ *     (SDD - SOD, (iu - (W-1)/2) pitch_u + off_u, (iv - (H-1)/2) pitch_v + off_v).
+ *   - Projection p: the stage is turned by angles_rad[p] about z; stage coordinates are
+ *     X = Rz(-phi_p) X_lab.
+ *   - Pose (Eq. 1): object coordinates X' = R (X - T), R the transpose of the intrinsic
+ *     zxz orientation Rz(alpha) Rx(beta) Rz(gamma) (gamma spins the part about its own
+ *     axis), T the part's position in stage coordinates, mm.
+ *   - Grid (Eq. 2, theta = atan2(y', x') in [0, 2 pi)): shells r_k = k R / N_r, wedges
+ *     theta_k = 2 pi k / N_theta, slabs h_k = -H/2 + k H / N_h.
+ *   - Volumes are [N_h][N_theta][N_r] (r fastest), voxel l = (ih N_theta + it) N_r + ir.
+ *     Sinograms are [N_p][H][W] (u fastest).  mu in 1/mm, lengths in mm.
+ *   - System matrix (Sec. 2.2, Eq. 5): t_jl = exact length of ray j (source -> pixel
+ *     centre) inside voxel l.
+ *
+ * Memory and ownership: the caller owns every array argument.  Unless an entry point
+ * says otherwise, array pointers are DEVICE pointers on the plan's device.  The library
+ * owns plans, their geometry tables and scratch, and servers.
+ *
+ * Streams: `stream` is a cudaStream_t passed as void*; NULL means the legacy default
+ * stream.  Calls are asynchronous on that stream unless stated otherwise.
+ *
+ * Errors: every int-returning call returns CYL_OK (0) or a negative CYL_E* code; no call
+ * throws, prints, or aborts the process.  Arguments are validated on the host before any
+ * work is queued.  cyl_last_error_detail() gives a one-line reason for the last failure
+ * on the calling thread.
+ */
+#ifndef CYLCT_H
+#define CYLCT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CYL_OK 0
+#define CYL_EINVAL (-1)    /* invalid argument (sizes, geometry, pointers, dtype) */
+#define CYL_ENOMEM (-2)    /* device or host allocation failed */
+#define CYL_EDEVICE (-3)   /* a CUDA call failed */
+#define CYL_EADMIT (-4)    /* request can never fit the server's HBM budget */
+#define CYL_ETIMEOUT (-5)  /* a bounded wait ran out */
+#define CYL_ENOTFOUND (-6) /* unknown ticket */
+#define CYL_EPENDING (-7)  /* result not ready yet (cyl_poll) */
+#define CYL_ECANCELLED (-8) /* request cancelled or server shut down */
+
+typedef enum { CYL_F32 = 0, CYL_F16 = 1, CYL_BF16 = 2 } cyl_dtype;
+
+/* Cylindrical grid about the part's axis (Sec. 2, Eq. 2). */
+typedef struct cyl_grid {
+    int32_t n_h, n_theta, n_r;   /* slabs, wedges, shells; each >= 1 */
+    double radius_mm, height_mm; /* grid cylinder: r <= radius, |h| <= height / 2 */
+} cyl_grid;
+
+/* Circular cone-beam acquisition (Table 1 lists one such geometry). */
+typedef struct cyl_geom {
+    double sod_mm, sdd_mm;       /* 0 < sod < sdd */
+    int32_t n_proj, det_w, det_h;
+    double pitch_u_mm, pitch_v_mm, off_u_mm, off_v_mm;
+    const double *angles_rad;    /* host array of n_proj stage angles; copied */
+} cyl_geom;
+
+/* Part pose (Sec. 2, Eq. 1); see the conventions above. */
+typedef struct cyl_pose {
+    double alpha, beta, gamma;   /* radians */
+    double tx, ty, tz;           /* mm */
+} cyl_pose;
+
+/* SART parameters (Eq. 6). */
+typedef struct cyl_sart_params {
+    int32_t n_iter;        /* full sweeps over all projections; >= 0 */
+    int32_t subset_size;   /* consecutive projections per subset (OS); >= 1 */
+    double lambda;         /* relaxation */
+    int32_t clamp_nonneg;  /* 1: x = max(x, 0) after each update */
+    int32_t weight_mode;   /* 1: w_hat = w / max(w); 0: w_hat = w */
+    int32_t strict_16bit;  /* 16-bit x_out only: 1 = keep the iterate itself in 16 bits
+                              (rounded after every subset); 0 = FP32 working iterate with a
+                              16-bit copy that the projector reads */
+    int32_t use_graph;     /* 1: replay each sweep as a captured CUDA graph */
+} cyl_sart_params;
+
+typedef struct cyl_plan cyl_plan;
+
+/* One-line reason for the last failing call on this thread (static storage). */
+const char *cyl_last_error_detail(void);
+/* Name of a CYL_E* code. */
+const char *cyl_strerror(int code);
+/* Library version, e.g. "cylct 1.0". */
+const char *cyl_version(void);
+
+/* Create a plan for one scan: validates the grid, geometry and pose, builds the
+ * per-projection ray tables (FP64, from the pose of Eq. 1, "only the alignment matrix
+ * needs to be precomputed", Sec. 2.2) on `device` and allocates the scratch of a SART
+ * solve.  *out receives the plan.  Errors: CYL_EINVAL, CYL_ENOMEM, CYL_EDEVICE. */
+int cyl_plan_create(const cyl_grid *grid, const cyl_geom *geom, const cyl_pose *pose,
+                    int device, cyl_plan **out);
+
+/* Synchronises the plan's work and frees it.  NULL is accepted. */
+int cyl_plan_destroy(cyl_plan *plan);
+
+/* Re-pose a plan for the next scan of the same part type: rebuilds the per-projection
+ * ray tables for `pose` (Eq. 1; the grid, geometry, scratch and any captured graph stay
+ * resident, since the grid is fixed to the part, Sec. 2.2) and uploads them on `stream`,
+ * ordered after the plan's earlier work.  Errors: CYL_EINVAL (non-finite pose),
+ * CYL_EDEVICE. */
+int cyl_plan_set_pose(cyl_plan *plan, const cyl_pose *pose, void *stream);
+
+/* Eq. 5, left side: p = -ln(max(I, 1) / I0) for n detector values.  counts: device
+ * array of `in` type; p_out: device array of `out` type; n >= 0.  In-place (counts ==
+ * p_out, same dtype) is allowed. */
+int cyl_log_transform(const void *counts, cyl_dtype in, double i0, void *p_out,
+                      cyl_dtype out, int64_t n, void *stream);
+
+/* Row sums L_j = sum_l t_jl (the denominator of Eq. 6's row normalisation) of the rays
+ * of projections p0 .. p0+np-1, as the FP64 chord of each ray through the grid cylinder
+ * rounded to FP32.  L_out: device float[np][H][W]. */
+int cyl_row_sums(cyl_plan *plan, int32_t p0, int32_t np, float *L_out, void *stream);
+
+/* Forward projection q = A x (Eq. 5 right side) for projections p0 .. p0+np-1.
+ * vol: device [N_h][N_theta][N_r] of vol_dtype.  sino_out: device [np][H][W] of
+ * sino_dtype (FP32 accumulation, rounded once on store). */
+int cyl_project(cyl_plan *plan, const void *vol, cyl_dtype vol_dtype, int32_t p0,
+                int32_t np, void *sino_out, cyl_dtype sino_dtype, void *stream);
+
+/* Matched back-projection out = A^T y over projections p0 .. p0+np-1 (the transpose of
+ * exactly the t_jl cyl_project uses; Sec. 2.2 back-projection).  sino: device [np][H][W]
+ * of sino_dtype.  vol_out: device float volume, OVERWRITTEN with A^T y.  colsum_out:
+ * NULL or device float volume, overwritten with A^T 1 (Eq. 6's column sums). */
+int cyl_backproject(cyl_plan *plan, const void *sino, cyl_dtype sino_dtype, int32_t p0,
+                    int32_t np, float *vol_out, float *colsum_out, void *stream);
+
+/* SART (Eq. 6) over all projections: x0 (warm start, Sec. 2.2 / 3.3 "initial volume";
+ * NULL = zeros), weight map w (weighted back-projection, Sec. 2.2; NULL = none; FP32),
+ * n_iter sweeps of ordered subsets in index order; the result goes to x_out.
+ *   sino:  [N_p][H][W] line integrals of sino_dtype;
+ *   x0:    [N_h][N_theta][N_r] of x_dtype, or NULL;
+ *   w:     [N_h][N_theta][N_r] float, or NULL;
+ *   x_out: [N_h][N_theta][N_r] of x_dtype (may equal x0).
+ * Pointers may be device or host memory (each is checked); host arrays are staged
+ * through plan-owned device buffers and the call then returns after x_out is written.
+ * Rays with L_j = 0 contribute nothing; voxels no ray of a subset touches keep their
+ * value.  Errors: CYL_EINVAL, CYL_ENOMEM, CYL_EDEVICE. */
+int cyl_sart_solve(cyl_plan *plan, const void *sino, cyl_dtype sino_dtype, const void *x0,
+                   const float *w, const cyl_sart_params *params, void *x_out,
+                   cyl_dtype x_dtype, void *stream);
+
+/* Segments (pieces of positive length between consecutive crossings, i.e. the
+ * non-zero entries of each row of A counted with multiplicity) of each projection
+ * p0 .. p0+np-1.  counts_out: device int64[np].  Used to state algorithmic bytes. */
+int cyl_count_segments(cyl_plan *plan, int32_t p0, int32_t np, int64_t *counts_out,
+                       void *stream);
+
+/* Per-kernel device time of the plan's last cyl_sart_solve run with timing enabled.
+ * kind: 0 forward projection, 1 back-projection, 2 update.  Timing adds a CUDA event
+ * pair around every launch of that solve (eager launches, no graph).  ms_total and
+ * launches receive the sum of event durations and the number of launches. */
+int cyl_plan_set_timing(cyl_plan *plan, int enable);
+int cyl_plan_kernel_time(cyl_plan *plan, int kind, double *ms_total, int64_t *launches);
+
+/* Sizes of a plan: voxels, rays per projection, projections, and the device bytes the
+ * plan holds. */
+int cyl_plan_sizes(const cyl_plan *plan, int64_t *n_vox, int64_t *n_pix, int32_t *n_proj,
+                   int64_t *device_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

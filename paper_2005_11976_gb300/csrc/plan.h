@@ -1,0 +1,103 @@
+// The plan object behind the opaque cyl_plan handle.
+#pragma once
+
+#include <mutex>
+#include <vector>
+
+#include "cylct_internal.h"
+
+namespace cylct {
+
+int set_error(int code, const char *msg);
+int cuda_error(cudaError_t e, const char *what);
+int validate_scan(const cyl_grid *grid, const cyl_geom *geom, const cyl_pose *pose);
+void build_tables(const cyl_grid &grid, const cyl_geom &geom, const cyl_pose &pose,
+                  std::vector<ProjGeom> &geo, std::vector<float2> &trig, GridDev &g);
+
+// Buffers and settings of one SART solve.
+struct SolveState {
+    const void *sino = nullptr;
+    cyl_dtype sino_t = CYL_F32;
+    const void *x_proj = nullptr;  // volume the projector reads
+    cyl_dtype x_proj_t = CYL_F32;
+    float *x32 = nullptr;          // FP32 iterate (null in strict 16-bit mode)
+    void *x16 = nullptr;           // 16-bit copy / iterate (null in FP32 mode)
+    cyl_dtype x16_t = CYL_F16;
+    int strict16 = 0;
+    const float *w = nullptr;
+    double lambda = 0.5;
+    int clamp = 0;
+    int subset = 1;
+
+    bool operator==(const SolveState &o) const
+    {
+        return sino == o.sino && sino_t == o.sino_t && x_proj == o.x_proj &&
+               x_proj_t == o.x_proj_t && x32 == o.x32 && x16 == o.x16 && x16_t == o.x16_t &&
+               strict16 == o.strict16 && w == o.w && lambda == o.lambda && clamp == o.clamp &&
+               subset == o.subset;
+    }
+};
+
+int queue_sweep(struct ::cyl_plan *pl, const SolveState &s, cudaStream_t st, bool timed);
+
+}  // namespace cylct
+
+struct cyl_plan {
+    int device = 0;
+    cyl_grid grid{};
+    cyl_geom geom{};
+    cyl_pose pose{};
+    std::vector<double> angles;
+    cylct::GridDev g{};
+    cylct::TileShape tile{32};
+    int64_t n_vox = 0, n_pix = 0;
+    size_t bytes = 0;
+
+    cylct::ProjGeom *d_geo = nullptr;
+    float2 *d_trig = nullptr;
+    float *d_wscale = nullptr;
+    unsigned long long *d_counts = nullptr;
+    float *d_num = nullptr, *d_den = nullptr;
+    float *d_res = nullptr;
+    size_t res_cap = 0;
+    float *d_x32 = nullptr;
+    size_t x32_cap = 0;
+    void *d_stage[4] = {nullptr, nullptr, nullptr, nullptr};  // sino, x0, w, x_out
+    size_t stage_cap[4] = {0, 0, 0, 0};
+
+    cudaStream_t ws = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_geo = nullptr;
+    void *h_geo = nullptr;  // pinned staging of the ray tables (cyl_plan_set_pose)
+
+    bool timing = false;
+    double kernel_ms[3] = {0, 0, 0};
+    int64_t kernel_launches[3] = {0, 0, 0};
+    std::vector<cudaEvent_t> events;
+    size_t ev_used = 0;
+
+    cudaGraphExec_t gexec = nullptr;
+    cylct::SolveState gkey{};
+
+    std::mutex mu;
+    std::vector<void *> allocs;
+
+    template <class T> int alloc(T **p, size_t nbytes)
+    {
+        void *q = nullptr;
+        if (cudaMalloc(&q, nbytes ? nbytes : 1) != cudaSuccess) {
+            cudaGetLastError();
+            return cylct::set_error(CYL_ENOMEM, "device allocation failed");
+        }
+        allocs.push_back(q);
+        bytes += nbytes;
+        *p = static_cast<T *>(q);
+        return CYL_OK;
+    }
+    // Grow-only scratch buffer.
+    int ensure(void **p, size_t &cap, size_t nbytes);
+    // Timing events for one subset: 4 consecutive events.
+    cudaEvent_t *next_events(int n_kernels);
+    int solve(const void *sino, cyl_dtype sino_t, const void *x0, const float *w,
+              const cyl_sart_params &prm, void *x_out, cyl_dtype x_t, cudaStream_t user);
+    ~cyl_plan();
+};

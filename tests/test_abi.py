@@ -1,0 +1,86 @@
+"""The C-ABI library builds, loads and exports every entry point of include/cylct.h, and
+its host-side validation answers without a GPU."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2005_11976_gb300 import cylct, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2005_11976_gb300 import build
+    build.build()
+    return cylct.load()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "cylct.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(cyl_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("cyl_plan_create", "cyl_plan_destroy", "cyl_project", "cyl_backproject",
+                     "cyl_sart_solve", "cyl_log_transform", "cyl_row_sums"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", cylct.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r" T (cyl_[a-z0-9_]+)$", out, flags=re.M))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    # the binding marshals every entry point
+    assert not [n for n in declared_functions() if n not in cylct.SIGNATURES]
+
+
+def test_built_for_sm_103a(lib):
+    out = subprocess.run(["cuobjdump", "--list-elf", cylct.LIB_PATH], capture_output=True,
+                         text=True).stdout
+    assert "sm_103a" in out
+
+
+def test_host_validation_without_gpu(lib):
+    assert lib.cyl_strerror(cylct.CYL_EINVAL) == b"CYL_EINVAL"
+    assert lib.cyl_version().startswith(b"cylct")
+    scan = synth.tiny_scan()
+    grid, geom, pose, ang = cylct.structs_from_scan(scan)
+    h = ctypes.c_void_p()
+    bad = cylct.cyl_grid(0, 4, 4, 1.0, 1.0)
+    assert lib.cyl_plan_create(ctypes.byref(bad), ctypes.byref(geom), ctypes.byref(pose), 0,
+                               ctypes.byref(h)) == cylct.CYL_EINVAL
+    assert b"grid" in lib.cyl_last_error_detail()
+    g2 = cylct.cyl_geom(400.0, 100.0, geom.n_proj, geom.det_w, geom.det_h, 1.0, 1.0, 0.0, 0.0,
+                        geom.angles_rad)
+    assert lib.cyl_plan_create(ctypes.byref(grid), ctypes.byref(g2), ctypes.byref(pose), 0,
+                               ctypes.byref(h)) == cylct.CYL_EINVAL
+    p2 = cylct.cyl_pose(float("nan"), 0, 0, 0, 0, 0)
+    assert lib.cyl_plan_create(ctypes.byref(grid), ctypes.byref(geom), ctypes.byref(p2), 0,
+                               ctypes.byref(h)) == cylct.CYL_EINVAL
+    assert lib.cyl_plan_create(ctypes.byref(grid), ctypes.byref(geom), ctypes.byref(pose), 0,
+                               None) == cylct.CYL_EINVAL
+    # zero-length work and bad arguments are answered on the host
+    assert lib.cyl_log_transform(None, 0, 1e4, None, 0, 0, None) == cylct.CYL_OK
+    assert lib.cyl_log_transform(None, 7, 1e4, None, 0, 10, None) == cylct.CYL_EINVAL
+    assert lib.cyl_log_transform(1, 0, -1.0, 2, 0, 10, None) == cylct.CYL_EINVAL
+    assert lib.cyl_sart_solve(None, None, 0, None, None, None, None, 0, None) == cylct.CYL_EINVAL
+    assert lib.cyl_plan_destroy(None) == cylct.CYL_OK
+
+
+def test_binding_fails_loudly_without_library(tmp_path):
+    with pytest.raises(RuntimeError):
+        saved = cylct._lib
+        cylct._lib = None
+        try:
+            cylct.load(str(tmp_path / "missing.so"))
+        finally:
+            cylct._lib = saved

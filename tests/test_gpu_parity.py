@@ -1,0 +1,284 @@
+"""GPU path vs the FP64 oracle, element by element, on seeded inputs.
+
+Tolerances: the FP32 path must match the oracle to <= 1e-5 relative L2 per projection
+and per SART iterate; the 16-bit storage path to <= 2e-3 relative L2 of the
+reconstruction.  Row sums are FP64 chords rounded to FP32 (<= 1e-6 relative).
+"""
+import dataclasses
+import math
+
+import numpy as np
+import pytest
+
+from paper_2005_11976_gb300 import cylct, synth
+import gpu_util as gu
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP32 = 1e-5
+TOL_16 = 2e-3
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2005_11976_gb300 import build
+    build.build()
+    return cylct.load()
+
+
+def osetup(orc, scan):
+    return orc.Setup(**scan.fields())
+
+
+def tilted_scan(n_h=24, n_t=96, n_r=20, n_proj=7, det_w=77, det_h=45):
+    # ragged detector (77 x 45 is no multiple of the 32 x 4 ray tile), tilted pose
+    s = synth.Scan(n_h, n_t, n_r, 10.0, 20.0, 100.0, 400.0, det_w, det_h, 1.2, 1.2,
+                   synth.full_circle(n_proj) + 0.3)
+    s.alpha, s.beta, s.gamma, s.tx, s.ty, s.tz = 0.4, 0.2, 1.1, 0.7, -0.4, 0.3
+    return s
+
+
+def per_projection_rel(a, b):
+    return max(gu.rel_l2(a[k], b[k]) for k in range(a.shape[0]))
+
+
+# ------------------------------------------------------------- projector
+
+@pytest.mark.parametrize("case", ["tiny", "tilted", "ntheta1", "ntheta2", "ntheta3"])
+def test_project_matches_oracle(lib, orc, case):
+    rng = np.random.default_rng(101)
+    if case == "tiny":
+        s = synth.tiny_scan()
+        x = synth.tiny_phantom(s, synth.rng_for("tiny"))
+    else:
+        s = tilted_scan()
+        if case.startswith("ntheta"):
+            s = dataclasses.replace(s, n_theta=int(case[-1]))
+        x = rng.uniform(0.0, 0.05, size=s.vol_shape)
+    ref = orc.project(osetup(orc, s), x)
+    with cylct.Plan(s) as plan:
+        got = gu.project(plan, x)
+    assert per_projection_rel(got, ref) <= TOL_FP32
+
+
+def test_set_pose_equals_fresh_plan(lib):
+    s = tilted_scan(n_proj=3)
+    s2 = dataclasses.replace(s, alpha=1.3, beta=-0.1, gamma=0.2, tx=-0.5, ty=0.9, tz=-0.2)
+    x = np.random.default_rng(8).uniform(0, 0.05, size=s.vol_shape)
+    with cylct.Plan(s2) as fresh:
+        ref = gu.project(fresh, x)
+    with cylct.Plan(s) as plan:
+        gu.project(plan, x)
+        plan.cyl_plan_set_pose((s2.alpha, s2.beta, s2.gamma, s2.tx, s2.ty, s2.tz))
+        got = gu.project(plan, x)
+    np.testing.assert_array_equal(got, ref)
+
+
+def test_row_sums_match_oracle(lib, orc):
+    s = tilted_scan()
+    ref = orc.row_sums(osetup(orc, s))
+    with cylct.Plan(s) as plan:
+        got = gu.row_sums(plan)
+    np.testing.assert_allclose(got, ref, rtol=1e-6, atol=1e-6)
+
+
+def test_backproject_and_colsums_match_oracle(lib, orc):
+    s = tilted_scan()
+    rng = np.random.default_rng(7)
+    y = rng.uniform(-1.0, 1.0, size=s.sino_shape)
+    o = osetup(orc, s)
+    ref = orc.backproject(o, y)
+    ref1 = orc.backproject(o, np.ones(s.sino_shape))
+    with cylct.Plan(s) as plan:
+        got, cs = gu.backproject(plan, y, colsum=True)
+        # sub-range of projections
+        got_sub = gu.backproject(plan, y[2:5], p0=2, np_=3)
+    assert gu.rel_l2(got, ref) <= TOL_FP32
+    assert gu.rel_l2(cs, ref1) <= TOL_FP32
+    assert gu.rel_l2(got_sub, orc.backproject(o, y[2:5], 2, 3)) <= TOL_FP32
+
+
+def test_adjoint_identity_on_gpu(lib):
+    s = tilted_scan()
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal(s.vol_shape)
+    y = rng.standard_normal(s.sino_shape)
+    with cylct.Plan(s) as plan:
+        ax = gu.project(plan, x)
+        aty = gu.backproject(plan, y)
+    lhs = float(np.sum(ax * y))
+    rhs = float(np.sum(x * aty))
+    scale = float(np.sqrt(np.sum(ax * ax) * np.sum(y * y)))
+    assert abs(lhs - rhs) <= 1e-5 * scale
+
+
+def test_segment_counts_match_oracle(lib, orc):
+    s = tilted_scan()
+    ref = orc.row_nnz(osetup(orc, s)).reshape(s.n_proj, -1).sum(axis=1)
+    with cylct.Plan(s) as plan:
+        got = gu.count_segments(plan)
+    assert np.all(np.abs(got - ref) <= 4 + 5e-4 * ref), (got, ref)
+
+
+def test_axis_parallel_ray(lib, orc):
+    # alpha = beta = pi/2 turns the part's axis onto the beam: the central ray runs along
+    # the z' axis (no shell or wedge crossings); use a theta-independent volume
+    s = synth.Scan(8, 16, 6, 5.0, 10.0, 50.0, 150.0, 9, 9, 0.7, 0.7, np.array([0.0, 0.2]))
+    s.alpha, s.beta = math.pi / 2, math.pi / 2
+    radial = np.linspace(0.01, 0.06, s.n_r)
+    slabs = np.linspace(1.0, 2.0, s.n_h)
+    x = slabs[:, None, None] * radial[None, None, :] * np.ones(s.vol_shape)
+    ref = orc.project(osetup(orc, s), x)
+    with cylct.Plan(s) as plan:
+        got = gu.project(plan, x)
+    assert per_projection_rel(got, ref) <= TOL_FP32
+    # the central ray of view 0 sees the whole height in shell 0
+    assert math.isclose(got[0, 4, 4], float(np.sum(x[:, 0, 0]) * s.height / s.n_h), rel_tol=1e-5)
+
+
+def test_rays_that_miss_give_zero(lib):
+    s = dataclasses.replace(tilted_scan(n_proj=2), off_u=500.0)
+    with cylct.Plan(s) as plan:
+        got = gu.project(plan, np.ones(s.vol_shape))
+        L = gu.row_sums(plan)
+        res = gu.sart(plan, np.ones(s.sino_shape), n_iter=1, x0=np.full(s.vol_shape, 0.5))
+    assert np.all(got == 0) and np.all(L == 0)
+    np.testing.assert_array_equal(res, np.full(s.vol_shape, 0.5, dtype=np.float32))
+
+
+def test_empty_projection_range(lib):
+    import torch
+    s = tilted_scan(n_proj=2)
+    with cylct.Plan(s) as plan:
+        out = torch.full((1,), 7.0, device="cuda")
+        plan.cyl_project(torch.zeros(s.vol_shape, device="cuda"), cylct.CYL_F32, 1, 0, out,
+                         cylct.CYL_F32)
+        torch.cuda.synchronize()
+        assert out.item() == 7.0
+        with pytest.raises(cylct.CylError):
+            plan.cyl_project(torch.zeros(s.vol_shape, device="cuda"), cylct.CYL_F32, 1, 2, out,
+                             cylct.CYL_F32)
+
+
+@pytest.mark.parametrize("vol_dt", [cylct.CYL_F16, cylct.CYL_BF16])
+def test_project_16bit_storage(lib, orc, vol_dt):
+    s = tilted_scan()
+    rng = np.random.default_rng(5)
+    x = rng.uniform(0.0, 0.05, size=s.vol_shape)
+    import torch
+    xr = gu.to_np(gu.to_dev(x, vol_dt))         # the stored 16-bit volume
+    ref = orc.project(osetup(orc, s), xr)
+    with cylct.Plan(s) as plan:
+        got = gu.project(plan, x, vol_dt=vol_dt, out_dt=cylct.CYL_F32)
+    assert per_projection_rel(got, ref) <= TOL_FP32
+
+
+def test_log_transform(lib, orc):
+    import torch
+    rng = np.random.default_rng(9)
+    counts = rng.poisson(1e4 * np.exp(-rng.uniform(0, 4, size=1000))).astype(np.float64)
+    counts[:5] = 0.0
+    ref = orc.log_transform(counts, 1e4)
+    c = gu.to_dev(counts)
+    out = torch.empty_like(c)
+    cylct.cyl_log_transform(c, cylct.CYL_F32, 1e4, out, cylct.CYL_F32, counts.size)
+    np.testing.assert_allclose(gu.to_np(out), ref, rtol=0, atol=2e-6)
+
+
+# ------------------------------------------------------------------ SART
+
+def test_sart_tiny_per_iterate(lib, orc):
+    # tiny workload: consistent data, zero start, 10 iterations, lambda 0.5
+    s = synth.tiny_scan()
+    x_true = synth.tiny_phantom(s, synth.rng_for("tiny"))
+    o = osetup(orc, s)
+    p = orc.project(o, x_true)
+    x_o = np.zeros(s.vol_shape)
+    x_g = np.zeros(s.vol_shape)
+    with cylct.Plan(s) as plan:
+        for it in range(10):
+            x_o = orc.sart(o, p, x0=x_o, n_iter=1, lam=0.5)
+            x_g = gu.sart(plan, p, x0=x_g, n_iter=1, lam=0.5)
+            assert gu.rel_l2(x_g, x_o) <= TOL_FP32, it
+        # ten sweeps in one call (one captured graph replayed) give the same iterate
+        x_10 = gu.sart(plan, p, n_iter=10, lam=0.5)
+    assert gu.rel_l2(x_10, x_o) <= TOL_FP32
+
+
+def test_sart_weighted_warm_started_subsets(lib, orc):
+    s = tilted_scan(n_proj=8)
+    rng = np.random.default_rng(21)
+    x0 = rng.uniform(0.0, 0.05, size=s.vol_shape)
+    p = rng.uniform(0.0, 1.0, size=s.sino_shape)
+    w = synth.roi_weights(s, 4.0, 7.0, 4.0, scale_to_radius=False)
+    o = osetup(orc, s)
+    for kw in (dict(subset_size=1, clamp_nonneg=False, weight_mode=1),
+               dict(subset_size=3, clamp_nonneg=True, weight_mode=1),
+               dict(subset_size=2, clamp_nonneg=False, weight_mode=0, lam=0.2)):
+        lam = kw.pop("lam", 0.5)
+        ref = orc.sart(o, p, x0=x0, w=w, n_iter=2, lam=lam, **kw)
+        with cylct.Plan(s) as plan:
+            got = gu.sart(plan, p, x0=x0, w=w, n_iter=2, lam=lam, **kw)
+            eager = gu.sart(plan, p, x0=x0, w=w, n_iter=2, lam=lam, use_graph=False, **kw)
+        assert gu.rel_l2(got, ref) <= TOL_FP32, kw
+        assert gu.rel_l2(eager, got) <= 1e-6
+
+
+def test_sart_host_buffers_equal_device_buffers(lib):
+    import torch
+    s = tilted_scan(n_proj=4)
+    rng = np.random.default_rng(2)
+    p = rng.uniform(0.0, 1.0, size=s.sino_shape).astype(np.float32)
+    x0 = rng.uniform(0.0, 0.05, size=s.vol_shape).astype(np.float32)
+    with cylct.Plan(s) as plan:
+        dev = gu.sart(plan, p, x0=x0, n_iter=2)
+        out = np.zeros(s.vol_shape, dtype=np.float32)
+        plan.cyl_sart_solve(p, cylct.CYL_F32, x0, None, cylct.sart_params(n_iter=2), out,
+                            cylct.CYL_F32)
+        pinned = torch.from_numpy(p).pin_memory()
+        out2 = torch.zeros(s.vol_shape).pin_memory()
+        plan.cyl_sart_solve(pinned, cylct.CYL_F32, x0, None, cylct.sart_params(n_iter=2), out2,
+                            cylct.CYL_F32)
+    assert gu.rel_l2(out, dev) <= 1e-6
+    assert gu.rel_l2(out2.numpy(), dev) <= 1e-6
+
+
+@pytest.mark.parametrize("x_dt", [cylct.CYL_F16, cylct.CYL_BF16])
+@pytest.mark.parametrize("strict", [False, True])
+def test_sart_16bit_storage(lib, orc, x_dt, strict):
+    s = synth.tiny_scan()
+    x_true = synth.tiny_phantom(s, synth.rng_for("tiny"))
+    o = osetup(orc, s)
+    p = orc.project(o, x_true)
+    ref = orc.sart(o, p, n_iter=10, lam=0.5)
+    with cylct.Plan(s) as plan:
+        got = gu.sart(plan, p, n_iter=10, lam=0.5, x_dt=x_dt, sino_dt=x_dt, strict_16bit=strict)
+    err = gu.rel_l2(got, ref)
+    assert err <= TOL_16 * (1 if not strict or x_dt == cylct.CYL_F16 else 4), err
+
+
+# ------------------------------------------------- medium workload, sampled
+
+def test_medium_single_view_projection_and_subset(lib, orc):
+    # full medium grid (128, 512, 128) and 256^2 detector in the bench's launch
+    # configuration; one view so the oracle finishes in seconds
+    full = synth.medium_scan(synth.rng_for("medium"))
+    s = dataclasses.replace(full, angles=full.angles[37:38])
+    az = synth.insert_azimuths(synth.rng_for("medium"))
+    x = synth.part_phantom(s, az)
+    o = osetup(orc, s)
+    ref_q = orc.project(o, x)
+    with cylct.Plan(s) as plan:
+        got_q = gu.project(plan, x)
+        assert gu.rel_l2(got_q, ref_q) <= TOL_FP32
+        # one SART subset (one view) from the defect-free warm start toward data with an
+        # insert removed
+        p = orc.project(o, synth.part_phantom(s, az, removed=3))
+        w = synth.roi_weights(s)
+        got = gu.sart(plan, p, x0=x, w=w, n_iter=1, lam=0.5)
+    ref = orc.sart(o, p, x0=x, w=w, n_iter=1, lam=0.5)
+    assert gu.rel_l2(got - x, ref - x) <= TOL_FP32 * 10
+    assert gu.rel_l2(got, ref) <= TOL_FP32
