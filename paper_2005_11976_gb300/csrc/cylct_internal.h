@@ -28,42 +28,60 @@ struct GridDev {
     double radius, height;  // FP64 copies for the ray set-up
     double dr_d;            // FP64 shell spacing
     float dr, inv_dr;       // shell spacing
-    float inv_dth;          // 1 / wedge angle
+    float dth, inv_dth;     // wedge angle and its inverse
     float dh, inv_dh, h0;   // slab spacing, first slab plane (-H/2)
 };
 
-// Ray-tile shape of the ray-driven kernels: a warp covers wu x (32 / wu) pixels, a
-// block stacks 4 warps along v.
-struct TileShape {
-    int wu;
+// Volume tiling of the projector / back-projector: tt wedges x th slabs x all shells
+// per tile (ragged last tiles), n_tt x n_th tiles, tile index = slab_tile * n_tt +
+// wedge_tile.  One tile's voxels are staged in shared memory.
+struct TileDev {
+    int tt, th, n_tt, n_th, n_tiles;
+    int smem_fp, smem_bp;   // dynamic shared memory bytes of the two kernels
 };
 
-inline dim3 ray_block() { return dim3(128, 1, 1); }
+// Device tables of one scan.
+struct ScanDev {
+    GridDev g;
+    TileDev td;
+    const float2 *trig;     // (cos, sin) of theta_k, k < N_theta
+    const float4 *ray_a;    // ray records [view][pixel], see RayRec
+    const float4 *ray_b;
+    const float4 *ray_c;
+    const int4 *bbox;       // candidate pixel box [view][tile]: u0, v0, u1, v1 (inclusive)
+};
 
-// One subset of a SART sweep or one batched step: which projections, and where.
-struct SubsetArgs {
-    int p0, np;
+constexpr int kTileThreads = 256;
+
+// SART update of one subset, fused into the back-projection epilogue.
+struct UpdateArgs {
+    float *x32;             // FP32 iterate (null in strict 16-bit mode)
+    void *x16;              // 16-bit copy / iterate (null in FP32 mode)
+    cyl_dtype x16_t;
+    int strict16;
+    const float *w;         // weight map or null
+    const float *wscale;    // device scalar lambda / max(w) (or lambda), or null
+    float lambda;
+    int clamp;
 };
 
 // Kernel launchers (kernels.cu).  All return cudaError_t of the launch.
-cudaError_t launch_project(const GridDev &g, const ProjGeom *geo, const float2 *trig,
-                           int p0, int np, const void *vol, cyl_dtype vt, void *out,
-                           cyl_dtype ot, TileShape ts, cudaStream_t st);
-cudaError_t launch_residual(const GridDev &g, const ProjGeom *geo, const float2 *trig,
-                            int p0, int np, const void *vol, cyl_dtype vt,
-                            const void *sino, cyl_dtype sdt, int64_t sino_proj_stride,
-                            float *res, TileShape ts, cudaStream_t st);
-cudaError_t launch_backproject(const GridDev &g, const ProjGeom *geo, const float2 *trig,
-                               int p0, int np, const void *y, cyl_dtype yt, float *num,
-                               float *den, TileShape ts, cudaStream_t st);
-cudaError_t launch_update(int64_t n_vox, float *x32, void *x16, cyl_dtype x16t,
-                          int strict16, float *num, float *den, const float *w,
-                          const float *wscale, float lambda, int clamp, cudaStream_t st);
-cudaError_t launch_row_sums(const GridDev &g, const ProjGeom *geo, int p0, int np,
-                            float *L, cudaStream_t st);
-cudaError_t launch_count(const GridDev &g, const ProjGeom *geo, const float2 *trig,
-                         int p0, int np, unsigned long long *counts, TileShape ts,
+cudaError_t launch_rays(const GridDev &g, const ProjGeom *geo, int n_proj, float4 *ra,
+                        float4 *rb, float4 *rc, cudaStream_t st);
+// q[v][pix] += sum over tiles of the tile's part of A x, views p0 .. p0+np-1 (q must be
+// zeroed by the caller).
+cudaError_t launch_fp_tiles(const ScanDev &sd, int p0, int np, const void *vol, cyl_dtype vt,
+                            float *q, cudaStream_t st);
+// SART mode (upd != null): residual (p - q) / L of the subset's rays back-projected into
+// shared memory per tile, then the fused update of x.  Pure mode (upd == null): A^T y
+// written to num_out and A^T 1 to den_out (if not null) for every voxel.
+cudaError_t launch_bp_tiles(const ScanDev &sd, int p0, int np, const void *sino, cyl_dtype sdt,
+                            const float *q, const UpdateArgs *upd, float *num_out,
+                            float *den_out, cudaStream_t st);
+cudaError_t launch_row_sums(const ScanDev &sd, int p0, int np, float *L, cudaStream_t st);
+cudaError_t launch_count(const ScanDev &sd, int p0, int np, unsigned long long *counts,
                          cudaStream_t st);
+cudaError_t set_kernel_attributes();
 cudaError_t launch_log(const void *in, cyl_dtype it, double i0, void *out, cyl_dtype ot,
                        int64_t n, cudaStream_t st);
 cudaError_t launch_convert(const void *in, cyl_dtype it, void *out, cyl_dtype ot,

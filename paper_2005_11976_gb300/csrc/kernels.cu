@@ -1,5 +1,8 @@
-// Kernels of the SART path: forward projection / residual, matched back-projection,
-// SART update, row sums, segment counts, log transform, dtype conversion.
+// Kernels of the SART path: ray records, tiled forward projection, tiled matched
+// back-projection with the fused SART update, row sums, segment counts, log transform,
+// dtype conversion.
+#include <type_traits>
+
 #include "traverse.cuh"
 
 namespace cylct {
@@ -16,157 +19,234 @@ template <> __device__ __forceinline__ float from_f32<float>(float v) { return v
 template <> __device__ __forceinline__ __half from_f32<__half>(float v) { return __float2half_rn(v); }
 template <> __device__ __forceinline__ __nv_bfloat16 from_f32<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
 
-template <class T> __device__ __forceinline__ float ldg_f32(const T *p) { return to_f32<T>(__ldg(p)); }
+__device__ __forceinline__ RayRec load_ray(const ScanDev &sd, int64_t r)
+{
+    RayRec rr;
+    rr.a = __ldg(sd.ray_a + r);
+    rr.b = __ldg(sd.ray_b + r);
+    rr.c = __ldg(sd.ray_c + r);
+    return rr;
+}
 
-// Map a thread to its ray: a warp covers a wu x (32/wu) pixel tile, a block 4 warps
-// stacked along v; blockIdx.z is the projection within the subset.
-struct RayIndex {
-    int iu, iv;
-    bool valid;
+// ------------------------------------------------------------------ ray records
+
+__global__ void k_rays(GridDev g, const ProjGeom *__restrict__ geo, float4 *ra, float4 *rb, float4 *rc)
+{
+    const int64_t npix = (int64_t)g.det_w * g.det_h;
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= npix) return;
+    const int p = blockIdx.y;
+    RayRec rr = setup_ray(g, geo[p], (int)(j % g.det_w), (int)(j / g.det_w));
+    const int64_t o = (int64_t)p * npix + j;
+    ra[o] = rr.a;
+    rb[o] = rr.b;
+    rc[o] = rr.c;
+}
+
+// ----------------------------------------------------------- tile staging helpers
+
+struct TileSpan {
+    int tw, th, chunk, n;   // wedges, slabs, voxels per slab, voxels
 };
 
-__device__ __forceinline__ RayIndex ray_of_thread(const GridDev &g, int wu)
+__device__ __forceinline__ TileSpan span_of(const GridDev &g, const Tile &t)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int wv = 32 / wu;
-    RayIndex r;
-    r.iu = blockIdx.x * wu + (lane % wu);
-    r.iv = (blockIdx.y * 4 + warp) * wv + lane / wu;
-    r.valid = r.iu < g.det_w && r.iv < g.det_h;
-    return r;
+    TileSpan s;
+    s.tw = t.t1 - t.t0;
+    s.th = t.s1 - t.s0;
+    s.chunk = s.tw * g.n_r;
+    s.n = s.th * s.chunk;
+    return s;
 }
 
-__device__ __forceinline__ void load_trig(const float2 *trig, int n_t, float2 *sm)
+// global voxel index of local voxel i of a tile
+__device__ __forceinline__ int64_t tile_global(const GridDev &g, const Tile &t, const TileSpan &s, int i)
 {
-    for (int k = threadIdx.x; k < n_t; k += blockDim.x) sm[k] = trig[k];
-    __syncthreads();
+    const int lh = i / s.chunk, rem = i - lh * s.chunk;
+    return ((int64_t)(t.s0 + lh) * g.n_t + t.t0) * g.n_r + rem;
 }
 
-template <class T>
-struct GatherOp {
-    const T *__restrict__ x;
+__device__ __forceinline__ void stage_trig(const ScanDev &sd, float2 *s_trig)
+{
+    for (int k = threadIdx.x; k < sd.g.n_t; k += blockDim.x) s_trig[k] = sd.trig[k];
+}
+
+// ------------------------------------------------------------- forward projection
+
+struct SmemGather {
+    const float *x;
     float acc;
-    __device__ __forceinline__ void operator()(int idx, float seg) { acc = fmaf(seg, ldg_f32(x + idx), acc); }
+    __device__ __forceinline__ void operator()(int idx, float seg) { acc = fmaf(seg, x[idx], acc); }
 };
 
-// q = A x (cyl_project) when RESID is false; the SART residual (p - q) / L when true.
-template <class T, class S, bool RESID>
-__global__ void __launch_bounds__(128)
-k_forward(GridDev g, const ProjGeom *__restrict__ geo, const float2 *__restrict__ trig, int p0,
-          const T *__restrict__ x, const S *__restrict__ sino, int64_t sino_stride,
-          void *__restrict__ out, int wu)
+// One CTA per (tile, view): stage the tile's voxels in shared memory, walk every
+// candidate ray of the view through the tile, add the partial line integral to q.
+template <class T>
+__global__ void __launch_bounds__(kTileThreads)
+k_fp_tile(ScanDev sd, int p0, const T *__restrict__ x, float *__restrict__ q)
 {
-    extern __shared__ float2 s_trig[];
-    load_trig(trig, g.n_t, s_trig);
-    RayIndex ri = ray_of_thread(g, wu);
-    if (!ri.valid) return;
-    const int pl = blockIdx.z;
-    const ProjGeom pg = geo[p0 + pl];
-    Ray ry = setup_ray(g, pg, ri.iu, ri.iv);
-    GatherOp<T> op{x, 0.f};
-    if (ry.hit) walk_ray(g, s_trig, ry, op);
-    const int64_t pix = (int64_t)ri.iv * g.det_w + ri.iu;
-    const int64_t o = (int64_t)pl * g.det_w * g.det_h + pix;
-    if (RESID) {
-        float p = to_f32<S>(sino[(int64_t)pl * sino_stride + pix]);
-        float r = (ry.hit && ry.L > 0.f) ? (p - op.acc) / ry.L : 0.f;
-        static_cast<float *>(out)[o] = r;
-    } else {
-        static_cast<S *>(out)[o] = from_f32<S>(op.acc);
+    extern __shared__ float4 smem4[];
+    const GridDev &g = sd.g;
+    const int tile = blockIdx.x, v = blockIdx.y, p = p0 + v;
+    const int4 bb = sd.bbox[(int64_t)p * sd.td.n_tiles + tile];
+    if (bb.x > bb.z || bb.y > bb.w) return;
+    float2 *s_trig = reinterpret_cast<float2 *>(smem4);
+    float *s_x = reinterpret_cast<float *>(s_trig + ((g.n_t + 1) & ~1));
+    const Tile t = tile_of(sd.td, g, tile);
+    const TileSpan s = span_of(g, t);
+    stage_trig(sd, s_trig);
+    for (int i = threadIdx.x; i < s.n; i += blockDim.x) s_x[i] = to_f32<T>(__ldg(x + tile_global(g, t, s, i)));
+    __syncthreads();
+    const int bw = bb.z - bb.x + 1;
+    const int nc = bw * (bb.w - bb.y + 1);
+    const int64_t npix = (int64_t)g.det_w * g.det_h;
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+        const int iv = bb.y + c / bw, iu = bb.x + c % bw;
+        const int64_t j = (int64_t)iv * g.det_w + iu;
+        const RayRec rr = load_ray(sd, (int64_t)p * npix + j);
+        SmemGather op{s_x, 0.f};
+        if (walk_tile(g, s_trig, rr, t, op) && op.acc != 0.f) atomicAdd(q + (int64_t)v * npix + j, op.acc);
     }
 }
 
-struct ScatterOp {
-    float *__restrict__ num;
-    float *__restrict__ den;
+// ----------------------------------------------------------------- back-projection
+
+template <bool DEN>
+struct SmemScatter {
+    float *num, *den;
     float y;
     __device__ __forceinline__ void operator()(int idx, float seg)
     {
         if (seg > 0.f) {
             atomicAdd(num + idx, seg * y);
-            if (den) atomicAdd(den + idx, seg);
+            if (DEN) atomicAdd(den + idx, seg);
         }
     }
 };
 
-// num += A^T y, den += A^T 1 over the subset's rays (same walk as k_forward, so the
-// transpose matches the projector piece by piece).
-template <class Y>
-__global__ void __launch_bounds__(128)
-k_backproject(GridDev g, const ProjGeom *__restrict__ geo, const float2 *__restrict__ trig, int p0,
-              const Y *__restrict__ y, float *__restrict__ num, float *__restrict__ den, int wu)
+template <class X>
+__device__ __forceinline__ void sart_update(const UpdateArgs &u, int64_t m, float num, float den, float sc)
 {
-    extern __shared__ float2 s_trig[];
-    load_trig(trig, g.n_t, s_trig);
-    RayIndex ri = ray_of_thread(g, wu);
-    if (!ri.valid) return;
-    const int pl = blockIdx.z;
-    const int64_t o = (int64_t)pl * g.det_w * g.det_h + (int64_t)ri.iv * g.det_w + ri.iu;
-    float yv = to_f32<Y>(y[o]);
-    if (yv == 0.f && den == nullptr) return;
-    const ProjGeom pg = geo[p0 + pl];
-    Ray ry = setup_ray(g, pg, ri.iu, ri.iv);
-    if (!ry.hit) return;
-    ScatterOp op{num, den, yv};
-    walk_ray(g, s_trig, ry, op);
+    if (!(den > 0.f)) return;
+    X *x16 = static_cast<X *>(u.x16);
+    float xv = u.strict16 ? to_f32<X>(x16[m]) : u.x32[m];
+    const float wm = u.w ? __ldg(u.w + m) : 1.f;
+    xv = fmaf(sc * wm, num / den, xv);
+    if (u.clamp) xv = fmaxf(xv, 0.f);
+    if (!u.strict16) u.x32[m] = xv;
+    if (x16) x16[m] = from_f32<X>(xv);
 }
+
+// One CTA per tile: accumulate num = A^T y and den = A^T 1 of the subset's views in
+// shared memory (y = SART residual (p - q) / L, or the given data in pure mode), then
+// either apply Eq. 6 to the tile's voxels (SART) or write num / den out (pure).
+template <class S, class X, bool SART>
+__global__ void __launch_bounds__(kTileThreads)
+k_bp_tile(ScanDev sd, int p0, int np, const S *__restrict__ y, const float *__restrict__ q,
+          UpdateArgs upd, float *__restrict__ num_out, float *__restrict__ den_out)
+{
+    extern __shared__ float4 smem4[];
+    const GridDev &g = sd.g;
+    const int tile = blockIdx.x;
+    float2 *s_trig = reinterpret_cast<float2 *>(smem4);
+    const Tile t = tile_of(sd.td, g, tile);
+    const TileSpan s = span_of(g, t);
+    float *s_num = reinterpret_cast<float *>(s_trig + ((g.n_t + 1) & ~1));
+    float *s_den = s_num + s.n;
+    const bool want_den = SART || den_out != nullptr;
+    stage_trig(sd, s_trig);
+    for (int i = threadIdx.x; i < s.n; i += blockDim.x) {
+        s_num[i] = 0.f;
+        s_den[i] = 0.f;
+    }
+    __syncthreads();
+    const int64_t npix = (int64_t)g.det_w * g.det_h;
+    for (int v = 0; v < np; ++v) {
+        const int p = p0 + v;
+        const int4 bb = sd.bbox[(int64_t)p * sd.td.n_tiles + tile];
+        if (bb.x > bb.z || bb.y > bb.w) continue;
+        const int bw = bb.z - bb.x + 1;
+        const int nc = bw * (bb.w - bb.y + 1);
+        for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+            const int iv = bb.y + c / bw, iu = bb.x + c % bw;
+            const int64_t j = (int64_t)iv * g.det_w + iu;
+            const int64_t jv = (int64_t)v * npix + j;
+            const RayRec rr = load_ray(sd, (int64_t)p * npix + j);
+            if (!(rr.c.y > rr.c.x)) continue;
+            float yv;
+            if (SART) {
+                const float L = rr.c.z;
+                yv = L > 0.f ? (to_f32<S>(y[jv]) - q[jv]) / L : 0.f;
+            } else {
+                yv = to_f32<S>(y[jv]);
+                if (yv == 0.f && !want_den) continue;
+            }
+            if (want_den) {
+                SmemScatter<true> op{s_num, s_den, yv};
+                walk_tile(g, s_trig, rr, t, op);
+            } else {
+                SmemScatter<false> op{s_num, s_den, yv};
+                walk_tile(g, s_trig, rr, t, op);
+            }
+        }
+    }
+    __syncthreads();
+    if (SART) {
+        const float sc = upd.wscale ? *upd.wscale : upd.lambda;
+        for (int i = threadIdx.x; i < s.n; i += blockDim.x)
+            sart_update<X>(upd, tile_global(g, t, s, i), s_num[i], s_den[i], sc);
+    } else {
+        for (int i = threadIdx.x; i < s.n; i += blockDim.x) {
+            const int64_t m = tile_global(g, t, s, i);
+            num_out[m] = s_num[i];
+            if (den_out) den_out[m] = s_den[i];
+        }
+    }
+}
+
+// ------------------------------------------------------------ counts, row sums
 
 struct CountOp {
     unsigned int n;
     __device__ __forceinline__ void operator()(int, float seg) { n += seg > 0.f; }
 };
 
-__global__ void __launch_bounds__(128)
-k_count(GridDev g, const ProjGeom *__restrict__ geo, const float2 *__restrict__ trig, int p0,
-        unsigned long long *counts, int wu)
+__global__ void __launch_bounds__(kTileThreads)
+k_count_tile(ScanDev sd, int p0, unsigned long long *counts)
 {
-    extern __shared__ float2 s_trig[];
-    load_trig(trig, g.n_t, s_trig);
-    RayIndex ri = ray_of_thread(g, wu);
-    CountOp op{0u};
-    if (ri.valid) {
-        Ray ry = setup_ray(g, geo[p0 + blockIdx.z], ri.iu, ri.iv);
-        if (ry.hit) walk_ray(g, s_trig, ry, op);
-    }
-    unsigned int v = op.n;
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0 && v) atomicAdd(counts + blockIdx.z, (unsigned long long)v);
-}
-
-__global__ void k_row_sums(GridDev g, const ProjGeom *__restrict__ geo, int p0, float *L)
-{
+    extern __shared__ float4 smem4[];
+    const GridDev &g = sd.g;
+    const int tile = blockIdx.x, v = blockIdx.y, p = p0 + v;
+    const int4 bb = sd.bbox[(int64_t)p * sd.td.n_tiles + tile];
+    if (bb.x > bb.z || bb.y > bb.w) return;
+    float2 *s_trig = reinterpret_cast<float2 *>(smem4);
+    const Tile t = tile_of(sd.td, g, tile);
+    stage_trig(sd, s_trig);
+    __syncthreads();
+    const int bw = bb.z - bb.x + 1;
+    const int nc = bw * (bb.w - bb.y + 1);
     const int64_t npix = (int64_t)g.det_w * g.det_h;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= npix) return;
-    const int iu = (int)(i % g.det_w), iv = (int)(i / g.det_w);
-    Ray ry = setup_ray(g, geo[p0 + blockIdx.y], iu, iv);
-    L[(int64_t)blockIdx.y * npix + i] = ry.hit ? ry.L : 0.f;
+    CountOp op{0u};
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+        const int iv = bb.y + c / bw, iu = bb.x + c % bw;
+        const RayRec rr = load_ray(sd, (int64_t)p * npix + (int64_t)iv * g.det_w + iu);
+        walk_tile(g, s_trig, rr, t, op);
+    }
+    unsigned int n = op.n;
+    for (int o = 16; o > 0; o >>= 1) n += __shfl_down_sync(0xffffffffu, n, o);
+    if ((threadIdx.x & 31) == 0 && n) atomicAdd(counts + v, (unsigned long long)n);
 }
 
-// x += wscale * w * num / den where den > 0 (Eq. 6), then clear num/den for the next
-// subset.  X16 (if any) receives the rounded iterate; in strict mode it IS the iterate.
-template <class X16>
-__global__ void k_update(int64_t n, float *__restrict__ x32, X16 *__restrict__ x16, int strict16,
-                         float *__restrict__ num, float *__restrict__ den,
-                         const float *__restrict__ w, const float *__restrict__ wscale, float lambda,
-                         int clamp)
+__global__ void k_row_sums(ScanDev sd, int p0, float *L)
 {
-    const float sc = wscale ? *wscale : lambda;
-    for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < n;
-         m += (int64_t)gridDim.x * blockDim.x) {
-        float d = den[m];
-        if (d > 0.f) {
-            float wm = w ? __ldg(w + m) : 1.f;
-            float xv = strict16 ? to_f32<X16>(x16[m]) : x32[m];
-            xv = fmaf(sc * wm, num[m] / d, xv);
-            if (clamp) xv = fmaxf(xv, 0.f);
-            if (!strict16) x32[m] = xv;
-            if (x16) x16[m] = from_f32<X16>(xv);
-            num[m] = 0.f;
-            den[m] = 0.f;
-        }
-    }
+    const int64_t npix = (int64_t)sd.g.det_w * sd.g.det_h;
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= npix) return;
+    const float4 c = __ldg(sd.ray_c + (int64_t)(p0 + blockIdx.y) * npix + j);
+    L[(int64_t)blockIdx.y * npix + j] = c.y > c.x ? c.z : 0.f;
 }
+
+// ------------------------------------------------------------ elementwise kernels
 
 __global__ void k_wmax(const float *__restrict__ w, int64_t n, unsigned int *out)
 {
@@ -187,10 +267,11 @@ __global__ void k_wscale(const unsigned int *wmax_bits, int mode, float lambda, 
 template <class I, class O>
 __global__ void k_log(const I *__restrict__ in, float i0, O *__restrict__ out, int64_t n)
 {
+    const float l0 = logf(i0);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         float c = fmaxf(to_f32<I>(in[i]), 1.f);
-        out[i] = from_f32<O>(logf(i0) - logf(c));
+        out[i] = from_f32<O>(l0 - logf(c));
     }
 }
 
@@ -204,14 +285,6 @@ __global__ void k_convert(const I *__restrict__ in, O *__restrict__ out, int64_t
 
 // ------------------------------------------------------------------ launchers
 
-static inline dim3 ray_grid(const GridDev &g, int np, int wu)
-{
-    int wv = 32 / wu;
-    return dim3((g.det_w + wu - 1) / wu, (g.det_h + 4 * wv - 1) / (4 * wv), np);
-}
-
-static inline size_t trig_smem(const GridDev &g) { return sizeof(float2) * (size_t)g.n_t; }
-
 template <class F>
 static cudaError_t dispatch1(cyl_dtype t, F &&f)
 {
@@ -223,92 +296,95 @@ static cudaError_t dispatch1(cyl_dtype t, F &&f)
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_project(const GridDev &g, const ProjGeom *geo, const float2 *trig, int p0,
-                           int np, const void *vol, cyl_dtype vt, void *out, cyl_dtype ot,
-                           TileShape ts, cudaStream_t st)
-{
-    if (np <= 0) return cudaSuccess;
-    return dispatch1(vt, [&](auto *tv) {
-        using T = std::remove_pointer_t<decltype(tv)>;
-        return dispatch1(ot, [&](auto *to) {
-            using S = std::remove_pointer_t<decltype(to)>;
-            k_forward<T, S, false><<<ray_grid(g, np, ts.wu), ray_block(), trig_smem(g), st>>>(
-                g, geo, trig, p0, (const T *)vol, (const S *)nullptr, 0, out, ts.wu);
-            return cudaGetLastError();
-        });
-    });
-}
-
-cudaError_t launch_residual(const GridDev &g, const ProjGeom *geo, const float2 *trig, int p0,
-                            int np, const void *vol, cyl_dtype vt, const void *sino,
-                            cyl_dtype sdt, int64_t sino_proj_stride, float *res, TileShape ts,
-                            cudaStream_t st)
-{
-    if (np <= 0) return cudaSuccess;
-    return dispatch1(vt, [&](auto *tv) {
-        using T = std::remove_pointer_t<decltype(tv)>;
-        return dispatch1(sdt, [&](auto *ts_) {
-            using S = std::remove_pointer_t<decltype(ts_)>;
-            k_forward<T, S, true><<<ray_grid(g, np, ts.wu), ray_block(), trig_smem(g), st>>>(
-                g, geo, trig, p0, (const T *)vol, (const S *)sino, sino_proj_stride, res, ts.wu);
-            return cudaGetLastError();
-        });
-    });
-}
-
-cudaError_t launch_backproject(const GridDev &g, const ProjGeom *geo, const float2 *trig, int p0,
-                               int np, const void *y, cyl_dtype yt, float *num, float *den,
-                               TileShape ts, cudaStream_t st)
-{
-    if (np <= 0) return cudaSuccess;
-    return dispatch1(yt, [&](auto *ty) {
-        using Y = std::remove_pointer_t<decltype(ty)>;
-        k_backproject<Y><<<ray_grid(g, np, ts.wu), ray_block(), trig_smem(g), st>>>(
-            g, geo, trig, p0, (const Y *)y, num, den, ts.wu);
-        return cudaGetLastError();
-    });
-}
-
 static inline int elementwise_blocks(int64_t n)
 {
     int64_t b = (n + 255) / 256;
     return (int)(b < 152 * 16 ? (b > 0 ? b : 1) : 152 * 16);
 }
 
-cudaError_t launch_update(int64_t n, float *x32, void *x16, cyl_dtype x16t, int strict16,
-                          float *num, float *den, const float *w, const float *wscale,
-                          float lambda, int clamp, cudaStream_t st)
+static inline size_t trig_bytes(const GridDev &g) { return sizeof(float2) * (size_t)((g.n_t + 1) & ~1); }
+
+cudaError_t set_kernel_attributes()
 {
-    if (n <= 0) return cudaSuccess;
-    const int nb = elementwise_blocks(n);
-    if (!x16) {
-        k_update<float><<<nb, 256, 0, st>>>(n, x32, (float *)nullptr, 0, num, den, w, wscale,
-                                            lambda, clamp);
-        return cudaGetLastError();
-    }
-    return dispatch1(x16t, [&](auto *tx) {
-        using X = std::remove_pointer_t<decltype(tx)>;
-        k_update<X><<<nb, 256, 0, st>>>(n, x32, (X *)x16, strict16, num, den, w, wscale,
-                                        lambda, clamp);
+    int dev = 0, maxsm = 0;
+    cudaGetDevice(&dev);
+    cudaError_t e = cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    auto set = [&](const void *fn) {
+        cudaError_t r = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm);
+        if (r != cudaSuccess && e == cudaSuccess) e = r;
+    };
+    set((const void *)k_fp_tile<float>);
+    set((const void *)k_fp_tile<__half>);
+    set((const void *)k_fp_tile<__nv_bfloat16>);
+#define CYL_SET_BP(S)                                                  \
+    set((const void *)k_bp_tile<S, float, true>);                      \
+    set((const void *)k_bp_tile<S, __half, true>);                     \
+    set((const void *)k_bp_tile<S, __nv_bfloat16, true>);              \
+    set((const void *)k_bp_tile<S, float, false>);
+    CYL_SET_BP(float)
+    CYL_SET_BP(__half)
+    CYL_SET_BP(__nv_bfloat16)
+#undef CYL_SET_BP
+    set((const void *)k_count_tile);
+    return e;
+}
+
+cudaError_t launch_rays(const GridDev &g, const ProjGeom *geo, int n_proj, float4 *ra, float4 *rb,
+                        float4 *rc, cudaStream_t st)
+{
+    const int64_t npix = (int64_t)g.det_w * g.det_h;
+    k_rays<<<dim3((unsigned)((npix + 255) / 256), n_proj), 256, 0, st>>>(g, geo, ra, rb, rc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fp_tiles(const ScanDev &sd, int p0, int np, const void *vol, cyl_dtype vt,
+                            float *q, cudaStream_t st)
+{
+    if (np <= 0) return cudaSuccess;
+    return dispatch1(vt, [&](auto *tv) {
+        using T = std::remove_pointer_t<decltype(tv)>;
+        k_fp_tile<T><<<dim3(sd.td.n_tiles, np), kTileThreads, sd.td.smem_fp, st>>>(
+            sd, p0, (const T *)vol, q);
         return cudaGetLastError();
     });
 }
 
-cudaError_t launch_row_sums(const GridDev &g, const ProjGeom *geo, int p0, int np, float *L,
+cudaError_t launch_bp_tiles(const ScanDev &sd, int p0, int np, const void *sino, cyl_dtype sdt,
+                            const float *q, const UpdateArgs *upd, float *num_out, float *den_out,
                             cudaStream_t st)
 {
+    return dispatch1(sdt, [&](auto *ts) {
+        using S = std::remove_pointer_t<decltype(ts)>;
+        if (!upd) {
+            UpdateArgs none{};
+            k_bp_tile<S, float, false><<<sd.td.n_tiles, kTileThreads, sd.td.smem_bp, st>>>(
+                sd, p0, np, (const S *)sino, q, none, num_out, den_out);
+            return cudaGetLastError();
+        }
+        const cyl_dtype xt = upd->x16 ? upd->x16_t : CYL_F32;
+        return dispatch1(xt, [&](auto *tx) {
+            using X = std::remove_pointer_t<decltype(tx)>;
+            k_bp_tile<S, X, true><<<sd.td.n_tiles, kTileThreads, sd.td.smem_bp, st>>>(
+                sd, p0, np, (const S *)sino, q, *upd, nullptr, nullptr);
+            return cudaGetLastError();
+        });
+    });
+}
+
+cudaError_t launch_row_sums(const ScanDev &sd, int p0, int np, float *L, cudaStream_t st)
+{
     if (np <= 0) return cudaSuccess;
-    int64_t npix = (int64_t)g.det_w * g.det_h;
-    k_row_sums<<<dim3((unsigned)((npix + 255) / 256), np), 256, 0, st>>>(g, geo, p0, L);
+    const int64_t npix = (int64_t)sd.g.det_w * sd.g.det_h;
+    k_row_sums<<<dim3((unsigned)((npix + 255) / 256), np), 256, 0, st>>>(sd, p0, L);
     return cudaGetLastError();
 }
 
-cudaError_t launch_count(const GridDev &g, const ProjGeom *geo, const float2 *trig, int p0,
-                         int np, unsigned long long *counts, TileShape ts, cudaStream_t st)
+cudaError_t launch_count(const ScanDev &sd, int p0, int np, unsigned long long *counts,
+                         cudaStream_t st)
 {
     if (np <= 0) return cudaSuccess;
-    k_count<<<ray_grid(g, np, ts.wu), ray_block(), trig_smem(g), st>>>(g, geo, trig, p0, counts,
-                                                                        ts.wu);
+    k_count_tile<<<dim3(sd.td.n_tiles, np), kTileThreads, trig_bytes(sd.g), st>>>(sd, p0, counts);
     return cudaGetLastError();
 }
 
@@ -343,7 +419,7 @@ cudaError_t launch_convert(const void *in, cyl_dtype it, void *out, cyl_dtype ot
 cudaError_t launch_weight_scale(const float *w, int64_t n, int mode, float lambda, float *wscale,
                                 cudaStream_t st)
 {
-    // wscale[0] holds lambda / max(w) (mode 1) or lambda (mode 0); wscale[1] is the
+    // wscale[0] receives lambda / max(w) (mode 1) or lambda (mode 0); wscale[1] is the
     // max-reduction word.
     unsigned int *bits = reinterpret_cast<unsigned int *>(wscale + 1);
     cudaError_t e = cudaMemsetAsync(bits, 0, sizeof(unsigned int), st);

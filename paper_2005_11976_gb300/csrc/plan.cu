@@ -1,4 +1,4 @@
-// SART solve driver of a plan (Eq. 6 over ordered subsets, n_iter sweeps).
+// Plan set-up and the SART solve driver (Eq. 6 over ordered subsets, n_iter sweeps).
 #include <algorithm>
 #include <cstring>
 
@@ -29,6 +29,59 @@ PtrKind kind_of(const void *p)
         if (e_ != cudaSuccess) return cuda_error(e_, #call);    \
     } while (0)
 
+int cyl_plan::init(const cyl_grid &gr, const cyl_geom &ge, const cyl_pose &po, int dev)
+{
+    device = dev;
+    grid = gr;
+    geom = ge;
+    pose = po;
+    angles.assign(ge.angles_rad, ge.angles_rad + ge.n_proj);
+    geom.angles_rad = angles.data();
+    n_vox = (int64_t)gr.n_h * gr.n_theta * gr.n_r;
+    n_pix = (int64_t)ge.det_w * ge.det_h;
+    int maxsm = 0;
+    PL_CUDA(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    int rc = choose_tiles(grid, maxsm, td);
+    if (rc) return rc;
+    PL_CUDA(set_kernel_attributes());
+    std::vector<float2> trig;
+    build_grid(grid, geom, g, trig);
+    const size_t n_rays = (size_t)geom.n_proj * n_pix;
+    if ((rc = alloc(&d_geo, sizeof(ProjGeom) * geom.n_proj))) return rc;
+    if ((rc = alloc(&d_trig, sizeof(float2) * trig.size()))) return rc;
+    if ((rc = alloc(&d_bbox, sizeof(int4) * (size_t)geom.n_proj * td.n_tiles))) return rc;
+    for (int k = 0; k < 3; ++k)
+        if ((rc = alloc(&d_ray[k], sizeof(float4) * n_rays))) return rc;
+    if ((rc = alloc(&d_wscale, 2 * sizeof(float)))) return rc;
+    PL_CUDA(cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking));
+    PL_CUDA(cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming));
+    PL_CUDA(cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming));
+    PL_CUDA(cudaEventCreateWithFlags(&ev_geo, cudaEventDisableTiming));
+    PL_CUDA(cudaMallocHost(&h_geo, sizeof(ProjGeom) * geom.n_proj));
+    PL_CUDA(cudaMallocHost(&h_bbox, sizeof(int4) * (size_t)geom.n_proj * td.n_tiles));
+    PL_CUDA(cudaMemcpyAsync(d_trig, trig.data(), sizeof(float2) * trig.size(), cudaMemcpyHostToDevice, ws));
+    if ((rc = upload_pose(pose, ws))) return rc;
+    PL_CUDA(cudaStreamSynchronize(ws));
+    return CYL_OK;
+}
+
+int cyl_plan::upload_pose(const cyl_pose &po, cudaStream_t st)
+{
+    std::vector<ProjGeom> geo;
+    std::vector<int4> bb;
+    build_views(grid, geom, po, td, geo, bb);
+    // the pinned staging copies may still feed the previous upload
+    PL_CUDA(cudaEventSynchronize(ev_geo));
+    std::memcpy(h_geo, geo.data(), sizeof(ProjGeom) * geo.size());
+    std::memcpy(h_bbox, bb.data(), sizeof(int4) * bb.size());
+    PL_CUDA(cudaMemcpyAsync(d_geo, h_geo, sizeof(ProjGeom) * geo.size(), cudaMemcpyHostToDevice, st));
+    PL_CUDA(cudaMemcpyAsync(d_bbox, h_bbox, sizeof(int4) * bb.size(), cudaMemcpyHostToDevice, st));
+    PL_CUDA(cudaEventRecord(ev_geo, st));
+    PL_CUDA(launch_rays(g, d_geo, geom.n_proj, d_ray[0], d_ray[1], d_ray[2], st));
+    pose = po;
+    return CYL_OK;
+}
+
 int cyl_plan::ensure(void **p, size_t &cap, size_t nbytes)
 {
     if (*p && cap >= nbytes) return CYL_OK;
@@ -40,15 +93,19 @@ int cyl_plan::ensure(void **p, size_t &cap, size_t nbytes)
         bytes -= cap;
         *p = nullptr;
         cap = 0;
+        if (gexec) {                 // a captured graph may point at the old buffer
+            cudaGraphExecDestroy(gexec);
+            gexec = nullptr;
+        }
     }
     int rc = alloc(p, nbytes);
     if (!rc) cap = nbytes;
     return rc;
 }
 
-cudaEvent_t *cyl_plan::next_events(int n_kernels)
+cudaEvent_t *cyl_plan::next_events(int n)
 {
-    const size_t need = ev_used + (size_t)n_kernels + 1;
+    const size_t need = ev_used + (size_t)n;
     while (events.size() < need) {
         cudaEvent_t e;
         if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
@@ -68,8 +125,39 @@ cyl_plan::~cyl_plan()
     if (ev_out) cudaEventDestroy(ev_out);
     if (ev_geo) cudaEventDestroy(ev_geo);
     if (h_geo) cudaFreeHost(h_geo);
+    if (h_bbox) cudaFreeHost(h_bbox);
     if (ws) cudaStreamDestroy(ws);
     for (void *p : allocs) cudaFree(p);
+}
+
+// One sweep: for every subset, zero q, forward-project the subset (tiles), then
+// back-project its residuals with the fused update.  Timed runs put an event before the
+// forward projection, between the two kernels and after the back-projection.
+int cyl_plan::queue_sweep(const SolveState &s, cudaStream_t st, bool timed)
+{
+    const ScanDev sd = scan_dev();
+    UpdateArgs upd;
+    upd.x32 = s.x32;
+    upd.x16 = s.x16;
+    upd.x16_t = s.x16_t;
+    upd.strict16 = s.strict16;
+    upd.w = s.w;
+    upd.wscale = s.w ? d_wscale : nullptr;
+    upd.lambda = (float)s.lambda;
+    upd.clamp = s.clamp;
+    for (int p0 = 0; p0 < geom.n_proj; p0 += s.subset) {
+        const int np = std::min(s.subset, geom.n_proj - p0);
+        const void *sino_p = static_cast<const char *>(s.sino) + (size_t)p0 * n_pix * dtype_size(s.sino_t);
+        cudaEvent_t *ev = timed ? next_events(3) : nullptr;
+        if (timed && !ev) return set_error(CYL_EDEVICE, "event creation failed");
+        if (ev) PL_CUDA(cudaEventRecord(ev[0], st));
+        PL_CUDA(cudaMemsetAsync(d_q, 0, sizeof(float) * (size_t)np * n_pix, st));
+        PL_CUDA(launch_fp_tiles(sd, p0, np, s.x_proj, s.x_proj_t, d_q, st));
+        if (ev) PL_CUDA(cudaEventRecord(ev[1], st));
+        PL_CUDA(launch_bp_tiles(sd, p0, np, sino_p, s.sino_t, d_q, &upd, nullptr, nullptr, st));
+        if (ev) PL_CUDA(cudaEventRecord(ev[2], st));
+    }
+    return CYL_OK;
 }
 
 int cyl_plan::solve(const void *sino, cyl_dtype sino_t, const void *x0, const float *w,
@@ -81,7 +169,7 @@ int cyl_plan::solve(const void *sino, cyl_dtype sino_t, const void *x0, const fl
     const size_t sino_bytes = (size_t)geom.n_proj * n_pix * sb;
     const int subset = std::min(prm.subset_size, geom.n_proj);
     int rc;
-    if ((rc = ensure((void **)&d_res, res_cap, sizeof(float) * (size_t)n_pix * subset))) return rc;
+    if ((rc = ensure((void **)&d_q, q_cap, sizeof(float) * (size_t)n_pix * subset))) return rc;
 
     PL_CUDA(cudaEventRecord(ev_in, user));
     PL_CUDA(cudaStreamWaitEvent(ws, ev_in, 0));
@@ -118,20 +206,18 @@ int cyl_plan::solve(const void *sino, cyl_dtype sino_t, const void *x0, const fl
     s.lambda = prm.lambda;
     s.clamp = prm.clamp_nonneg ? 1 : 0;
     s.subset = subset;
+    if (d_x0 && d_x0 != d_xo) PL_CUDA(cudaMemcpyAsync(d_xo, d_x0, xb * n_vox, cudaMemcpyDeviceToDevice, ws));
+    if (!d_x0) PL_CUDA(cudaMemsetAsync(d_xo, 0, xb * n_vox, ws));
     if (x_t == CYL_F32) {
         s.x32 = (float *)d_xo;
         s.x_proj = d_xo;
         s.x_proj_t = CYL_F32;
-        if (d_x0 && d_x0 != d_xo) PL_CUDA(cudaMemcpyAsync(d_xo, d_x0, xb * n_vox, cudaMemcpyDeviceToDevice, ws));
-        if (!d_x0) PL_CUDA(cudaMemsetAsync(d_xo, 0, xb * n_vox, ws));
     } else {
         s.x16 = d_xo;
         s.x16_t = x_t;
         s.x_proj = d_xo;
         s.x_proj_t = x_t;
         s.strict16 = prm.strict_16bit ? 1 : 0;
-        if (d_x0 && d_x0 != d_xo) PL_CUDA(cudaMemcpyAsync(d_xo, d_x0, xb * n_vox, cudaMemcpyDeviceToDevice, ws));
-        if (!d_x0) PL_CUDA(cudaMemsetAsync(d_xo, 0, xb * n_vox, ws));
         if (!s.strict16) {
             if ((rc = ensure((void **)&d_x32, x32_cap, sizeof(float) * n_vox))) return rc;
             s.x32 = d_x32;
@@ -139,13 +225,11 @@ int cyl_plan::solve(const void *sino, cyl_dtype sino_t, const void *x0, const fl
         }
     }
     if (d_w) PL_CUDA(launch_weight_scale(d_w, n_vox, prm.weight_mode, (float)prm.lambda, d_wscale, ws));
-    PL_CUDA(cudaMemsetAsync(d_num, 0, sizeof(float) * n_vox, ws));
-    PL_CUDA(cudaMemsetAsync(d_den, 0, sizeof(float) * n_vox, ws));
 
     if (timing) {
         ev_used = 0;
         for (int it = 0; it < prm.n_iter; ++it)
-            if ((rc = queue_sweep(this, s, ws, true))) return rc;
+            if ((rc = queue_sweep(s, ws, true))) return rc;
     } else if (prm.use_graph && prm.n_iter > 0) {
         if (!gexec || !(gkey == s)) {
             if (gexec) {
@@ -154,7 +238,7 @@ int cyl_plan::solve(const void *sino, cyl_dtype sino_t, const void *x0, const fl
             }
             cudaGraph_t graph = nullptr;
             PL_CUDA(cudaStreamBeginCapture(ws, cudaStreamCaptureModeThreadLocal));
-            rc = queue_sweep(this, s, ws, false);
+            rc = queue_sweep(s, ws, false);
             cudaError_t ce = cudaStreamEndCapture(ws, &graph);
             if (rc) {
                 if (graph) cudaGraphDestroy(graph);
@@ -172,7 +256,7 @@ int cyl_plan::solve(const void *sino, cyl_dtype sino_t, const void *x0, const fl
         for (int it = 0; it < prm.n_iter; ++it) PL_CUDA(cudaGraphLaunch(gexec, ws));
     } else {
         for (int it = 0; it < prm.n_iter; ++it)
-            if ((rc = queue_sweep(this, s, ws, false))) return rc;
+            if ((rc = queue_sweep(s, ws, false))) return rc;
     }
 
     if (kxo == kHost) PL_CUDA(cudaMemcpyAsync(x_out, d_xo, xb * n_vox, cudaMemcpyDeviceToHost, ws));
@@ -184,9 +268,8 @@ int cyl_plan::solve(const void *sino, cyl_dtype sino_t, const void *x0, const fl
             kernel_ms[k] = 0.0;
             kernel_launches[k] = 0;
         }
-        const size_t per = 4;
-        for (size_t base = 0; base + per <= ev_used; base += per)
-            for (int k = 0; k < 3; ++k) {
+        for (size_t base = 0; base + 3 <= ev_used; base += 3)
+            for (int k = 0; k < 2; ++k) {
                 float ms = 0.f;
                 PL_CUDA(cudaEventElapsedTime(&ms, events[base + k], events[base + k + 1]));
                 kernel_ms[k] += ms;

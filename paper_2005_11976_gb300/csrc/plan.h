@@ -1,4 +1,4 @@
-// The plan object behind the opaque cyl_plan handle.
+// The plan object behind the opaque cyl_plan handle, and the host geometry helpers.
 #pragma once
 
 #include <mutex>
@@ -10,9 +10,13 @@ namespace cylct {
 
 int set_error(int code, const char *msg);
 int cuda_error(cudaError_t e, const char *what);
+
+// geometry.cu
 int validate_scan(const cyl_grid *grid, const cyl_geom *geom, const cyl_pose *pose);
-void build_tables(const cyl_grid &grid, const cyl_geom &geom, const cyl_pose &pose,
-                  std::vector<ProjGeom> &geo, std::vector<float2> &trig, GridDev &g);
+int choose_tiles(const cyl_grid &grid, int max_smem, TileDev &td);
+void build_grid(const cyl_grid &grid, const cyl_geom &geom, GridDev &g, std::vector<float2> &trig);
+void build_views(const cyl_grid &grid, const cyl_geom &geom, const cyl_pose &pose,
+                 const TileDev &td, std::vector<ProjGeom> &geo, std::vector<int4> &bbox);
 
 // Buffers and settings of one SART solve.
 struct SolveState {
@@ -38,8 +42,6 @@ struct SolveState {
     }
 };
 
-int queue_sweep(struct ::cyl_plan *pl, const SolveState &s, cudaStream_t st, bool timed);
-
 }  // namespace cylct
 
 struct cyl_plan {
@@ -49,17 +51,17 @@ struct cyl_plan {
     cyl_pose pose{};
     std::vector<double> angles;
     cylct::GridDev g{};
-    cylct::TileShape tile{32};
+    cylct::TileDev td{};
     int64_t n_vox = 0, n_pix = 0;
     size_t bytes = 0;
 
     cylct::ProjGeom *d_geo = nullptr;
     float2 *d_trig = nullptr;
+    float4 *d_ray[3] = {nullptr, nullptr, nullptr};
+    int4 *d_bbox = nullptr;
     float *d_wscale = nullptr;
-    unsigned long long *d_counts = nullptr;
-    float *d_num = nullptr, *d_den = nullptr;
-    float *d_res = nullptr;
-    size_t res_cap = 0;
+    float *d_q = nullptr;          // forward projections of one subset (FP32)
+    size_t q_cap = 0;
     float *d_x32 = nullptr;
     size_t x32_cap = 0;
     void *d_stage[4] = {nullptr, nullptr, nullptr, nullptr};  // sino, x0, w, x_out
@@ -67,7 +69,8 @@ struct cyl_plan {
 
     cudaStream_t ws = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_geo = nullptr;
-    void *h_geo = nullptr;  // pinned staging of the ray tables (cyl_plan_set_pose)
+    void *h_geo = nullptr;         // pinned staging of the view tables (set_pose)
+    void *h_bbox = nullptr;
 
     bool timing = false;
     double kernel_ms[3] = {0, 0, 0};
@@ -81,6 +84,19 @@ struct cyl_plan {
     std::mutex mu;
     std::vector<void *> allocs;
 
+    cylct::ScanDev scan_dev() const
+    {
+        cylct::ScanDev sd;
+        sd.g = g;
+        sd.td = td;
+        sd.trig = d_trig;
+        sd.ray_a = d_ray[0];
+        sd.ray_b = d_ray[1];
+        sd.ray_c = d_ray[2];
+        sd.bbox = d_bbox;
+        return sd;
+    }
+
     template <class T> int alloc(T **p, size_t nbytes)
     {
         void *q = nullptr;
@@ -93,10 +109,13 @@ struct cyl_plan {
         *p = static_cast<T *>(q);
         return CYL_OK;
     }
+    int init(const cyl_grid &gr, const cyl_geom &ge, const cyl_pose &po, int dev);
+    // Upload view tables for `pose` and rebuild the ray records, on stream st.
+    int upload_pose(const cyl_pose &po, cudaStream_t st);
     // Grow-only scratch buffer.
     int ensure(void **p, size_t &cap, size_t nbytes);
-    // Timing events for one subset: 4 consecutive events.
-    cudaEvent_t *next_events(int n_kernels);
+    cudaEvent_t *next_events(int n);
+    int queue_sweep(const cylct::SolveState &s, cudaStream_t st, bool timed);
     int solve(const void *sino, cyl_dtype sino_t, const void *x0, const float *w,
               const cyl_sart_params &prm, void *x_out, cyl_dtype x_t, cudaStream_t user);
     ~cyl_plan();
