@@ -73,19 +73,31 @@ __device__ __forceinline__ void stage_trig(const ScanDev &sd, float2 *s_trig)
 
 // ------------------------------------------------------------- forward projection
 
-struct SmemGather {
-    const float *x;
-    float acc;
-    __device__ __forceinline__ void operator()(int idx, float seg) { acc = fmaf(seg, x[idx], acc); }
+// per-block scratch of tile_walk_all: chunk counter and one 32-entry map per warp
+struct WalkShared {
+    int chunk;
+    int map[kTileThreads / 32][32];
 };
 
-// One CTA per (tile, view): stage the tile's voxels in shared memory, walk every
-// candidate ray of the view through the tile, add the partial line integral to q.
+struct FpK {
+    const float *x;      // the tile's voxels in shared memory
+    float *q;            // the view's projections
+    __device__ __forceinline__ float payload(int64_t, const RayRec &) const { return 0.f; }
+    __device__ __forceinline__ void piece(int idx, float len, float &acc) const { acc = fmaf(len, x[idx], acc); }
+    __device__ __forceinline__ void end(int64_t j, float acc) const
+    {
+        if (acc != 0.f) atomicAdd(q + j, acc);
+    }
+};
+
+// One CTA per (tile, view): stage the tile's voxels in shared memory, walk every ray of
+// the view that crosses the tile, add its partial line integral to q.
 template <class T>
 __global__ void __launch_bounds__(kTileThreads)
 k_fp_tile(ScanDev sd, int p0, const T *__restrict__ x, float *__restrict__ q)
 {
     extern __shared__ float4 smem4[];
+    __shared__ WalkShared ws;
     const GridDev &g = sd.g;
     const int tile = blockIdx.x, v = blockIdx.y, p = p0 + v;
     const int4 bb = sd.bbox[(int64_t)p * sd.td.n_tiles + tile];
@@ -96,32 +108,41 @@ k_fp_tile(ScanDev sd, int p0, const T *__restrict__ x, float *__restrict__ q)
     const TileSpan s = span_of(g, t);
     stage_trig(sd, s_trig);
     for (int i = threadIdx.x; i < s.n; i += blockDim.x) s_x[i] = to_f32<T>(__ldg(x + tile_global(g, t, s, i)));
+    if (threadIdx.x == 0) ws.chunk = 0;
     __syncthreads();
-    const int bw = bb.z - bb.x + 1;
-    const int nc = bw * (bb.w - bb.y + 1);
     const int64_t npix = (int64_t)g.det_w * g.det_h;
-    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
-        const int iv = bb.y + c / bw, iu = bb.x + c % bw;
-        const int64_t j = (int64_t)iv * g.det_w + iu;
-        const RayRec rr = load_ray(sd, (int64_t)p * npix + j);
-        SmemGather op{s_x, 0.f};
-        if (walk_tile(g, s_trig, rr, t, op) && op.acc != 0.f) atomicAdd(q + (int64_t)v * npix + j, op.acc);
-    }
+    const int64_t r0 = (int64_t)p * npix;
+    FpK k{s_x, q + (int64_t)v * npix};
+    tile_walk_all(g, s_trig, t, sd.ray_a + r0, sd.ray_b + r0, sd.ray_c + r0, bb, k, &ws.chunk,
+                  ws.map[threadIdx.x >> 5]);
 }
 
 // ----------------------------------------------------------------- back-projection
 
-template <bool DEN>
-struct SmemScatter {
+// SART: payload = residual (p_j - q_j) / L_j; pure: payload = y_j.  Each piece adds
+// len * payload to num and len to den in shared memory.
+template <class S, bool SART, bool DEN>
+struct BpK {
     float *num, *den;
-    float y;
-    __device__ __forceinline__ void operator()(int idx, float seg)
+    const S *y;          // the view's data
+    const float *q;      // the view's forward projections (SART)
+    __device__ __forceinline__ float payload(int64_t j, const RayRec &rr) const
     {
-        if (seg > 0.f) {
-            atomicAdd(num + idx, seg * y);
-            if (DEN) atomicAdd(den + idx, seg);
+        if (SART) {
+            const float L = rr.c.z;
+            const float pj = to_f32<S>(y[j]), qj = q[j];
+            return L > 0.f ? (pj - qj) / L : 0.f;
+        }
+        return to_f32<S>(y[j]);
+    }
+    __device__ __forceinline__ void piece(int idx, float len, float &yv) const
+    {
+        if (len > 0.f) {
+            atomicAdd(num + idx, len * yv);
+            if (DEN) atomicAdd(den + idx, len);
         }
     }
+    __device__ __forceinline__ void end(int64_t, float) const {}
 };
 
 template <class X>
@@ -146,6 +167,7 @@ k_bp_tile(ScanDev sd, int p0, int np, const S *__restrict__ y, const float *__re
           UpdateArgs upd, float *__restrict__ num_out, float *__restrict__ den_out)
 {
     extern __shared__ float4 smem4[];
+    __shared__ WalkShared ws;
     const GridDev &g = sd.g;
     const int tile = blockIdx.x;
     float2 *s_trig = reinterpret_cast<float2 *>(smem4);
@@ -153,44 +175,31 @@ k_bp_tile(ScanDev sd, int p0, int np, const S *__restrict__ y, const float *__re
     const TileSpan s = span_of(g, t);
     float *s_num = reinterpret_cast<float *>(s_trig + ((g.n_t + 1) & ~1));
     float *s_den = s_num + s.n;
-    const bool want_den = SART || den_out != nullptr;
     stage_trig(sd, s_trig);
     for (int i = threadIdx.x; i < s.n; i += blockDim.x) {
         s_num[i] = 0.f;
         s_den[i] = 0.f;
     }
-    __syncthreads();
     const int64_t npix = (int64_t)g.det_w * g.det_h;
     for (int v = 0; v < np; ++v) {
         const int p = p0 + v;
         const int4 bb = sd.bbox[(int64_t)p * sd.td.n_tiles + tile];
-        if (bb.x > bb.z || bb.y > bb.w) continue;
-        const int bw = bb.z - bb.x + 1;
-        const int nc = bw * (bb.w - bb.y + 1);
-        for (int c = threadIdx.x; c < nc; c += blockDim.x) {
-            const int iv = bb.y + c / bw, iu = bb.x + c % bw;
-            const int64_t j = (int64_t)iv * g.det_w + iu;
-            const int64_t jv = (int64_t)v * npix + j;
-            const RayRec rr = load_ray(sd, (int64_t)p * npix + j);
-            if (!(rr.c.y > rr.c.x)) continue;
-            float yv;
-            if (SART) {
-                const float L = rr.c.z;
-                yv = L > 0.f ? (to_f32<S>(y[jv]) - q[jv]) / L : 0.f;
+        if (threadIdx.x == 0) ws.chunk = 0;
+        __syncthreads();
+        if (!(bb.x > bb.z || bb.y > bb.w)) {
+            const int64_t r0 = (int64_t)p * npix, y0 = (int64_t)v * npix;
+            if (SART || den_out) {
+                BpK<S, SART, true> k{s_num, s_den, y + y0, SART ? q + y0 : nullptr};
+                tile_walk_all(g, s_trig, t, sd.ray_a + r0, sd.ray_b + r0, sd.ray_c + r0, bb, k,
+                              &ws.chunk, ws.map[threadIdx.x >> 5]);
             } else {
-                yv = to_f32<S>(y[jv]);
-                if (yv == 0.f && !want_den) continue;
-            }
-            if (want_den) {
-                SmemScatter<true> op{s_num, s_den, yv};
-                walk_tile(g, s_trig, rr, t, op);
-            } else {
-                SmemScatter<false> op{s_num, s_den, yv};
-                walk_tile(g, s_trig, rr, t, op);
+                BpK<S, SART, false> k{s_num, s_den, y + y0, nullptr};
+                tile_walk_all(g, s_trig, t, sd.ray_a + r0, sd.ray_b + r0, sd.ray_c + r0, bb, k,
+                              &ws.chunk, ws.map[threadIdx.x >> 5]);
             }
         }
+        __syncthreads();
     }
-    __syncthreads();
     if (SART) {
         const float sc = upd.wscale ? *upd.wscale : upd.lambda;
         for (int i = threadIdx.x; i < s.n; i += blockDim.x)
@@ -206,15 +215,19 @@ k_bp_tile(ScanDev sd, int p0, int np, const S *__restrict__ y, const float *__re
 
 // ------------------------------------------------------------ counts, row sums
 
-struct CountOp {
-    unsigned int n;
-    __device__ __forceinline__ void operator()(int, float seg) { n += seg > 0.f; }
+struct CountK {
+    unsigned int *n;
+    __device__ __forceinline__ float payload(int64_t, const RayRec &) const { return 0.f; }
+    __device__ __forceinline__ void piece(int, float len, float &acc) const { acc += len > 0.f ? 1.f : 0.f; }
+    __device__ __forceinline__ void end(int64_t, float acc) const { atomicAdd(n, (unsigned int)acc); }
 };
 
 __global__ void __launch_bounds__(kTileThreads)
 k_count_tile(ScanDev sd, int p0, unsigned long long *counts)
 {
     extern __shared__ float4 smem4[];
+    __shared__ WalkShared ws;
+    __shared__ unsigned int s_n;
     const GridDev &g = sd.g;
     const int tile = blockIdx.x, v = blockIdx.y, p = p0 + v;
     const int4 bb = sd.bbox[(int64_t)p * sd.td.n_tiles + tile];
@@ -222,19 +235,17 @@ k_count_tile(ScanDev sd, int p0, unsigned long long *counts)
     float2 *s_trig = reinterpret_cast<float2 *>(smem4);
     const Tile t = tile_of(sd.td, g, tile);
     stage_trig(sd, s_trig);
-    __syncthreads();
-    const int bw = bb.z - bb.x + 1;
-    const int nc = bw * (bb.w - bb.y + 1);
-    const int64_t npix = (int64_t)g.det_w * g.det_h;
-    CountOp op{0u};
-    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
-        const int iv = bb.y + c / bw, iu = bb.x + c % bw;
-        const RayRec rr = load_ray(sd, (int64_t)p * npix + (int64_t)iv * g.det_w + iu);
-        walk_tile(g, s_trig, rr, t, op);
+    if (threadIdx.x == 0) {
+        ws.chunk = 0;
+        s_n = 0;
     }
-    unsigned int n = op.n;
-    for (int o = 16; o > 0; o >>= 1) n += __shfl_down_sync(0xffffffffu, n, o);
-    if ((threadIdx.x & 31) == 0 && n) atomicAdd(counts + v, (unsigned long long)n);
+    __syncthreads();
+    const int64_t r0 = (int64_t)p * g.det_w * g.det_h;
+    CountK k{&s_n};
+    tile_walk_all(g, s_trig, t, sd.ray_a + r0, sd.ray_b + r0, sd.ray_c + r0, bb, k, &ws.chunk,
+                  ws.map[threadIdx.x >> 5]);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_n) atomicAdd(counts + v, (unsigned long long)s_n);
 }
 
 __global__ void k_row_sums(ScanDev sd, int p0, float *L)
@@ -311,7 +322,11 @@ cudaError_t set_kernel_attributes()
     cudaError_t e = cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
     auto set = [&](const void *fn) {
-        cudaError_t r = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm);
+        cudaFuncAttributes fa;
+        cudaError_t r = cudaFuncGetAttributes(&fa, fn);
+        if (r == cudaSuccess)
+            r = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     maxsm - (int)fa.sharedSizeBytes);
         if (r != cudaSuccess && e == cudaSuccess) e = r;
     };
     set((const void *)k_fp_tile<float>);

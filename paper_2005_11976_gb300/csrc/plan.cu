@@ -41,7 +41,8 @@ int cyl_plan::init(const cyl_grid &gr, const cyl_geom &ge, const cyl_pose &po, i
     n_pix = (int64_t)ge.det_w * ge.det_h;
     int maxsm = 0;
     PL_CUDA(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    int rc = choose_tiles(grid, maxsm, td);
+    // leave room for the kernels' static shared memory (walk scratch, about 1 KB)
+    int rc = choose_tiles(grid, maxsm - 4096, td);
     if (rc) return rc;
     PL_CUDA(set_kernel_attributes());
     std::vector<float2> trig;

@@ -30,6 +30,11 @@
 // change is a single step, so rounding near a boundary only creates a zero-length piece.
 // Indices never leave the tile (its exits are the clip, not crossings), and a walk stops
 // after max_steps pieces.
+//
+// Work distribution (tile_walk_all): a warp tests 32 candidate pixels of a tile at once,
+// and moves the rays that cross the tile into its idle lanes with shuffles; all lanes
+// then step their rays in lock-step, and the warp refills when half of its lanes are
+// idle.  Candidates that miss the tile therefore never hold a lane while others walk.
 #pragma once
 
 #include "cylct_internal.h"
@@ -38,12 +43,16 @@ namespace cylct {
 
 constexpr float kInf = 3.0e38f;
 constexpr float kTwoPiF = 6.283185307179586f;
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kRefillBelow = 16;   // refill a warp once this many lanes or fewer walk
+constexpr int kStepsPerCheck = 2;  // steps between two refill checks
 
 // FP32 ray record, computed once per plan and pose in FP64 (k_rays).
 //   a = (P*x, P*y, P*z, utan)   utan: |u| of shell boundary kstar
 //   b = (e_x, e_y, e_z, d^2)
 //   c = (u_in, u_out, L, kstar) L: chord in the grid cylinder (row sum of Eq. 6);
-//                               u_in > u_out marks a ray that misses the grid.
+//                               u_in > u_out marks a ray that misses the grid;
+//                               kstar = -1 marks a ray parallel to the axis.
 struct RayRec {
     float4 a, b, c;
 };
@@ -105,7 +114,7 @@ __device__ __forceinline__ RayRec setup_ray(const GridDev &g, const ProjGeom &pg
             utan = (float)sqrt(fmax(rk * rk - d2, 0.0) * inv_a);
         }
     } else {
-        ks = -1;                                  // marks "no shell / wedge crossings"
+        ks = -1;
     }
     rr.a = make_float4((float)(Sx + sstar * ex), (float)(Sy + sstar * ey), (float)(Sz + sstar * ez),
                        utan);
@@ -133,49 +142,40 @@ __device__ __forceinline__ Tile tile_of(const TileDev &td, const GridDev &g, int
     return t;
 }
 
-// Walk the pieces of ray rr inside tile t, calling op(local_index, length) for each,
-// local_index = ((ih - s0) * (t1 - t0) + (it - t0)) * N_r + ir.  Returns false if the
-// ray does not cross the tile.
-template <class Op>
-__device__ __forceinline__ bool walk_tile(const GridDev &g, const float2 *__restrict__ trig,
-                                          const RayRec &rr, const Tile &t, Op &op)
+// Interval [ua, ub] of a ray inside a tile; false if empty.
+__device__ __forceinline__ bool clip_tile(const GridDev &g, const float2 *__restrict__ trig,
+                                          const RayRec &rr, const Tile &t, float &ua_out,
+                                          float &ub_out)
 {
     float ua = rr.c.x, ub = rr.c.y;
     if (!(ub > ua)) return false;
     const float px = rr.a.x, py = rr.a.y, pz = rr.a.z;
     const float ex = rr.b.x, ey = rr.b.y, ez = rr.b.z;
-    const int kstar = __float_as_int(rr.c.w);
-    const bool radial = kstar >= 0;
-    const int n_r = g.n_r, n_t = g.n_t;
-
-    // slab range of the tile
-    const float inv_ez = ez != 0.f ? 1.f / ez : 0.f;
-    const float c0 = (g.h0 - pz) * inv_ez, c1 = g.dh * inv_ez;
+    const bool radial = __float_as_int(rr.c.w) >= 0;
     if (ez != 0.f) {
-        float h_lo = fmaf((float)t.s0, c1, c0), h_hi = fmaf((float)t.s1, c1, c0);
+        const float inv_ez = 1.f / ez;
+        const float c0 = (g.h0 - pz) * inv_ez, c1 = g.dh * inv_ez;
+        const float h_lo = fmaf((float)t.s0, c1, c0), h_hi = fmaf((float)t.s1, c1, c0);
         ua = fmaxf(ua, fminf(h_lo, h_hi));
         ub = fminf(ub, fmaxf(h_lo, h_hi));
     } else {
-        float hz = pz - g.h0;
+        const float hz = pz - g.h0;
         if (hz < t.s0 * g.dh || hz > t.s1 * g.dh) return false;
     }
-    // wedge range of the tile (a sector of angle <= pi/2: two half-planes)
-    const float sense = (px * ey - py * ex) >= 0.f ? 1.f : -1.f;
-    const bool ccw = sense > 0.f;
     if (!t.full_circle && radial) {
-        float2 ca = trig[t.t0], cb = trig[t.t1 == n_t ? 0 : t.t1];
-        // left of theta_t0: n_a . P >= 0
-        float nda = ca.x * ey - ca.y * ex, noa = ca.x * py - ca.y * px;
-        // right of theta_t1: n_b . P <= 0
-        float ndb = cb.x * ey - cb.y * ex, nob = cb.x * py - cb.y * px;
+        // a sector of angle <= pi/2: left of theta_t0 (n_a . P >= 0) and right of
+        // theta_t1 (n_b . P <= 0)
+        const float2 ca = trig[t.t0], cb = trig[t.t1 == g.n_t ? 0 : t.t1];
+        const float nda = ca.x * ey - ca.y * ex, noa = ca.x * py - ca.y * px;
+        const float ndb = cb.x * ey - cb.y * ex, nob = cb.x * py - cb.y * px;
         if (nda != 0.f) {
-            float ux = __fdividef(-noa, nda);
+            const float ux = __fdividef(-noa, nda);
             if (nda > 0.f) ua = fmaxf(ua, ux); else ub = fminf(ub, ux);
         } else if (noa < 0.f) {
             return false;
         }
         if (ndb != 0.f) {
-            float ux = __fdividef(-nob, ndb);
+            const float ux = __fdividef(-nob, ndb);
             if (ndb < 0.f) ua = fmaxf(ua, ux); else ub = fminf(ub, ux);
         } else if (nob > 0.f) {
             return false;
@@ -184,98 +184,264 @@ __device__ __forceinline__ bool walk_tile(const GridDev &g, const float2 *__rest
         // parallel to the axis: one wedge for the whole ray
         float th = atan2f(py, px);
         th = th < 0.f ? th + kTwoPiF : th;
-        int it = min((int)(th * g.inv_dth), n_t - 1);
+        const int it = min((int)(th * g.inv_dth), g.n_t - 1);
         if (it < t.t0 || it >= t.t1) return false;
     }
-    if (!(ub > ua)) return false;
+    ua_out = ua;
+    ub_out = ub;
+    return ub > ua;
+}
 
-    // entry indices
-    float u = ua;
-    float x = fmaf(u, ex, px), y = fmaf(u, ey, py), z = fmaf(u, ez, pz);
-    int ir = min((int)(sqrtf(fmaf(x, x, y * y)) * g.inv_dr), n_r - 1);
-    float th = atan2f(y, x);
-    int it;
-    if (t.full_circle) {
-        th = th < 0.f ? th + kTwoPiF : th;
-        it = min((int)(th * g.inv_dth), n_t - 1);
-    } else {
-        // angle from the tile's first boundary, wrapped to [-pi, pi): a point just below
-        // theta = 2 pi belongs to a tile starting at 0 (the tile spans <= pi/2)
-        float rel = th - (float)t.t0 * g.dth;
-        rel = rel < -0.5f * kTwoPiF ? rel + kTwoPiF : (rel >= 0.5f * kTwoPiF ? rel - kTwoPiF : rel);
-        it = t.t0 + min(max((int)floorf(rel * g.inv_dth), 0), t.t1 - t.t0 - 1);
+// State of one ray walking through one tile.  Each family keeps the index of the next
+// boundary it will cross and the direction it moves in:
+//   shells: kr, sdir (-1 while moving inward, +1 outward); the crossing of shell k is at
+//           u = sdir * sqrt(A k^2 + B), A = dr^2 / a, B = -d^2 / a (utan for k = kstar);
+//   wedges: kt, ccw; crossing at -(n_kt . P*) / (n_kt . e);
+//   slabs:  kh, hdir; crossing at c0 + kh c1.
+struct Walker {
+    float px, py, ex, ey, A, B, utan, c0, c1;
+    float u, ub, ur, ut, uh;
+    int idx, it, kr, kt, kh, kstar, sdir, hdir, hstride, steps;
+    bool ccw;
+
+    __device__ __forceinline__ float shell_u(const GridDev &g) const
+    {
+        if (kr >= g.n_r) return kInf;
+        const float kf = (float)kr;
+        const float q = (kr == kstar) ? utan : fsqrt_fast(fmaxf(fmaf(A * kf, kf, B), 0.f));
+        return fmaxf(sdir < 0 ? -q : q, u);
     }
-    int ih = min(max((int)floorf((z - g.h0) * g.inv_dh), t.s0), t.s1 - 1);
-
-    bool inward = u < 0.f;
-    const float d2 = rr.b.w, utan = rr.a.w, dr = g.dr;
-    const float inv_a = radial ? 1.f / fmaf(ex, ex, ey * ey) : 0.f;
-    auto next_r = [&](int ir_, bool inw, float ucur) -> float {
-        if (!radial) return kInf;
-        int k;
-        float sgn;
-        if (inw && ir_ >= kstar) { k = ir_; sgn = -1.f; }
-        else { k = ir_ + 1; sgn = 1.f; }
-        if (k >= n_r) return kInf;
-        float rk = k * dr;
-        float q = (k == kstar) ? utan : fsqrt_fast(fmaxf(fmaf(rk, rk, -d2), 0.f) * inv_a);
-        return fmaxf(sgn * q, ucur);
-    };
-    auto next_t = [&](int it_, float ucur) -> float {
-        if (n_t == 1 || !radial) return kInf;
-        int k;
+    __device__ __forceinline__ float wedge_u(const float2 *__restrict__ trig, const Tile &t) const
+    {
+        if (kt < 0) return kInf;
+        const float2 cs = trig[kt];
+        const float nd = cs.x * ey - cs.y * ex;
+        if (ccw ? nd <= 0.f : nd >= 0.f) return kInf;
+        const float no = cs.x * py - cs.y * px;
+        return fmaxf(__fdividef(-no, nd), u);
+    }
+    __device__ __forceinline__ float slab_u(const Tile &t) const
+    {
+        return (hdir != 0 && kh > t.s0 && kh < t.s1) ? fmaxf(fmaf((float)kh, c1, c0), u) : kInf;
+    }
+    // next wedge boundary after entering wedge it (-1: none inside the tile)
+    __device__ __forceinline__ int wedge_next(const GridDev &g, const Tile &t, int it_) const
+    {
+        if (g.n_t == 1) return -1;
         if (ccw) {
-            k = it_ + 1;
-            if (!t.full_circle && k >= t.t1) return kInf;
-            k = (k == n_t) ? 0 : k;
-        } else {
-            if (!t.full_circle && it_ <= t.t0) return kInf;
-            k = it_;
+            const int k = it_ + 1;
+            if (!t.full_circle && k >= t.t1) return -1;
+            return k == g.n_t ? 0 : k;
         }
-        float2 cs = trig[k];
-        float nd = cs.x * ey - cs.y * ex;
-        if (sense * nd <= 0.f) return kInf;
-        float no = cs.x * py - cs.y * px;
-        return fmaxf(__fdividef(-no, nd), ucur);
-    };
-    auto next_h = [&](int ih_, float ucur) -> float {
-        if (ez > 0.f) return (ih_ + 1 < t.s1) ? fmaxf(fmaf((float)(ih_ + 1), c1, c0), ucur) : kInf;
-        if (ez < 0.f) return (ih_ > t.s0) ? fmaxf(fmaf((float)ih_, c1, c0), ucur) : kInf;
-        return kInf;
-    };
-
-    float ur = next_r(ir, inward, u);
-    float ut = next_t(it, u);
-    float uh = next_h(ih, u);
-    const int tw = t.t1 - t.t0;
-    const int tstep = n_r, hstep = tw * n_r;
-    int idx = ((ih - t.s0) * tw + (it - t.t0)) * n_r + ir;
-    for (int step = 0; step < g.max_steps; ++step) {
-        float un = fminf(fminf(ur, ut), uh);
-        float ue = fminf(un, ub);
-        op(idx, ue - u);
-        if (un >= ub) break;
-        u = un;
-        if (un == ur) {
-            if (inward && ir >= kstar) { ir -= 1; idx -= 1; }
-            else { inward = false; ir += 1; idx += 1; }
-            ur = next_r(ir, inward, u);
-        } else if (un == ut) {
-            if (ccw) {
-                if (it + 1 == n_t) { it = 0; idx -= (n_t - 1) * tstep; }
-                else { it += 1; idx += tstep; }
-            } else {
-                if (it == 0) { it = n_t - 1; idx += (n_t - 1) * tstep; }
-                else { it -= 1; idx -= tstep; }
-            }
-            ut = next_t(it, u);
-        } else {
-            if (ez > 0.f) { ih += 1; idx += hstep; }
-            else { ih -= 1; idx -= hstep; }
-            uh = next_h(ih, u);
-        }
+        if (!t.full_circle && it_ <= t.t0) return -1;
+        return it_;
     }
-    return true;
+
+    // Start at the tile entry ua of ray rr; the walk ends at ub.
+    __device__ __forceinline__ void init(const GridDev &g, const float2 *__restrict__ trig,
+                                         const Tile &t, const RayRec &rr, float ua, float ub_)
+    {
+        px = rr.a.x;
+        py = rr.a.y;
+        const float pz = rr.a.z;
+        ex = rr.b.x;
+        ey = rr.b.y;
+        const float ez = rr.b.z;
+        utan = rr.a.w;
+        kstar = __float_as_int(rr.c.w);
+        const bool radial = kstar >= 0;
+        const float inv_a = radial ? 1.f / fmaf(ex, ex, ey * ey) : 0.f;
+        A = g.dr * g.dr * inv_a;
+        B = -rr.b.w * inv_a;
+        const float inv_ez = ez != 0.f ? 1.f / ez : 0.f;
+        c0 = (g.h0 - pz) * inv_ez;
+        c1 = g.dh * inv_ez;
+        ccw = (px * ey - py * ex) >= 0.f;
+        u = ua;
+        ub = ub_;
+        steps = 0;
+        const float x = fmaf(u, ex, px), y = fmaf(u, ey, py), z = fmaf(u, ez, pz);
+        const int ir = min((int)(sqrtf(fmaf(x, x, y * y)) * g.inv_dr), g.n_r - 1);
+        float th = atan2f(y, x);
+        if (t.full_circle) {
+            th = th < 0.f ? th + kTwoPiF : th;
+            it = min((int)(th * g.inv_dth), g.n_t - 1);
+        } else {
+            // angle from the tile's first boundary, wrapped to [-pi, pi): a point just
+            // below theta = 2 pi belongs to a tile starting at 0 (tiles span <= pi/2)
+            float rel = th - (float)t.t0 * g.dth;
+            rel = rel < -0.5f * kTwoPiF ? rel + kTwoPiF : (rel >= 0.5f * kTwoPiF ? rel - kTwoPiF : rel);
+            it = t.t0 + min(max((int)floorf(rel * g.inv_dth), 0), t.t1 - t.t0 - 1);
+        }
+        const int ih = min(max((int)floorf((z - g.h0) * g.inv_dh), t.s0), t.s1 - 1);
+        const int tw = t.t1 - t.t0;
+        hstride = tw * g.n_r;
+        idx = ((ih - t.s0) * tw + (it - t.t0)) * g.n_r + ir;
+        if (!radial) {
+            kr = g.n_r;
+            sdir = 1;
+            kt = -1;
+        } else {
+            if (u < 0.f && ir >= kstar) { kr = ir; sdir = -1; }
+            else { kr = ir + 1; sdir = 1; }
+            kt = wedge_next(g, t, it);
+        }
+        hdir = ez > 0.f ? 1 : (ez < 0.f ? -1 : 0);
+        kh = hdir > 0 ? ih + 1 : ih;
+        ur = shell_u(g);
+        ut = wedge_u(trig, t);
+        uh = slab_u(t);
+    }
+
+    // One piece: calls op(idx, length); returns false once the ray has left the tile.
+    // Branch-free: the index update and next crossing of all three families are
+    // evaluated and the one of the family that moved is kept, so the lanes of a warp
+    // never split over which family they advance.
+    template <class Op>
+    __device__ __forceinline__ bool step(const GridDev &g, const float2 *__restrict__ trig,
+                                         const Tile &t, Op &op)
+    {
+        const float un = fminf(fminf(ur, ut), uh);
+        op(idx, fminf(un, ub) - u);
+        if (un >= ub || ++steps >= g.max_steps) return false;
+        u = un;
+        const bool isr = un == ur;
+        const bool ist = !isr && un == ut;
+        const bool ish = !isr && !ist;
+        // shells: inward until kstar, then outward (turnaround re-crosses kstar)
+        const int kr2 = sdir > 0 ? kr + 1 : (kr > kstar ? kr - 1 : kr);
+        const int sdir2 = (sdir < 0 && kr <= kstar) ? 1 : sdir;
+        // wedges: enter wedge it2, next boundary kt2 (-1: none inside the tile)
+        int it2 = ccw ? kt : kt - 1;
+        it2 = it2 < 0 ? it2 + g.n_t : it2;
+        int kc = it2 + 1;
+        const bool stop_c = !t.full_circle && kc >= t.t1;
+        kc = kc == g.n_t ? 0 : kc;
+        const bool stop_w = !t.full_circle && it2 <= t.t0;
+        const int kt2 = ccw ? (stop_c ? -1 : kc) : (stop_w ? -1 : it2);
+        idx += isr ? sdir : (ist ? (it2 - it) * g.n_r : hdir * hstride);
+        kr = isr ? kr2 : kr;
+        sdir = isr ? sdir2 : sdir;
+        it = ist ? it2 : it;
+        kt = ist ? kt2 : kt;
+        kh = ish ? kh + hdir : kh;
+        const float kf = (float)kr;
+        const float qs = (kr == kstar) ? utan : fsqrt_fast(fmaxf(fmaf(A * kf, kf, B), 0.f));
+        const float urn = kr >= g.n_r ? kInf : fmaxf(sdir < 0 ? -qs : qs, u);
+        const float2 cs = trig[max(kt, 0)];
+        const float nd = cs.x * ey - cs.y * ex, no = cs.x * py - cs.y * px;
+        const bool okw = kt >= 0 && (ccw ? nd > 0.f : nd < 0.f);
+        const float utn = okw ? fmaxf(__fdividef(-no, nd), u) : kInf;
+        const float uhn = (hdir != 0 && kh > t.s0 && kh < t.s1) ? fmaxf(fmaf((float)kh, c1, c0), u) : kInf;
+        ur = isr ? urn : ur;
+        ut = ist ? utn : ut;
+        uh = ish ? uhn : uh;
+        return true;
+    }
+};
+
+// Walk every ray of one view whose candidate pixel (inside box bb) crosses tile t.
+// ra/rb/rc point at the view's ray records.  K provides:
+//   float payload(int64_t j, const RayRec &rr)  per candidate ray j (loads overlap the
+//                                               record loads), the ray's start value
+//   void piece(int idx, float len, float &acc)  per piece (acc starts at the payload)
+//   void end(int64_t j, float acc)              per ray, after its last piece
+// s_chunk: a shared int the caller zeroed (chunk counter of this view), s_map: 32 ints
+// of shared memory per warp.
+template <class K>
+__device__ __forceinline__ void tile_walk_all(const GridDev &g, const float2 *__restrict__ trig,
+                                              const Tile &t, const float4 *__restrict__ ra,
+                                              const float4 *__restrict__ rb,
+                                              const float4 *__restrict__ rc, int4 bb,
+                                              K &k, int *s_chunk, int *s_map)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const int bw = bb.z - bb.x + 1;
+    const int nc = bw * (bb.w - bb.y + 1);
+    const int n_chunks = (nc + 31) >> 5;
+    int chunk = 0, pos = 32;                // current chunk of 32 candidates, next offset
+    bool active = false, more = true;
+    Walker w;
+    int64_t j = 0;
+    float acc = 0.f;
+    auto piece = [&](int idx, float len) { k.piece(idx, len, acc); };
+    for (;;) {
+        unsigned amask = __ballot_sync(kFull, active);
+        // refill: fill every idle lane, testing candidates 32 at a time
+        if (__popc(amask) <= kRefillBelow && more) {
+            while (amask != kFull && more) {
+                if (pos >= 32) {
+                    int c0 = 0;
+                    if (lane == 0) c0 = atomicAdd(s_chunk, 1);
+                    chunk = __shfl_sync(kFull, c0, 0);
+                    pos = 0;
+                    if (chunk >= n_chunks) {
+                        more = false;
+                        break;
+                    }
+                }
+                const int c = chunk * 32 + lane;
+                bool hit = false;
+                RayRec rr;
+                float ua = 0.f, ub = 0.f, pay = 0.f;
+                int64_t jc = 0;
+                if (lane >= pos && c < nc) {
+                    jc = (int64_t)(bb.y + c / bw) * g.det_w + (bb.x + c % bw);
+                    rr.a = __ldg(ra + jc);
+                    rr.b = __ldg(rb + jc);
+                    rr.c = __ldg(rc + jc);
+                    pay = k.payload(jc, rr);
+                    hit = clip_tile(g, trig, rr, t, ua, ub);
+                }
+                const unsigned hmask = __ballot_sync(kFull, hit);
+                const unsigned emask = ~amask;
+                const int n_hit = __popc(hmask);
+                const int n_take = min(n_hit, __popc(emask));
+                if (hit) s_map[__popc(hmask & lt_mask)] = lane;
+                __syncwarp();
+                const int er = __popc(emask & lt_mask);
+                const bool take = !active && er < n_take;
+                const int src = take ? s_map[er] : lane;
+                pos = n_take < n_hit ? s_map[n_take] : 32;
+                __syncwarp();
+                RayRec rx;
+                rx.a.x = __shfl_sync(kFull, rr.a.x, src);
+                rx.a.y = __shfl_sync(kFull, rr.a.y, src);
+                rx.a.z = __shfl_sync(kFull, rr.a.z, src);
+                rx.a.w = __shfl_sync(kFull, rr.a.w, src);
+                rx.b.x = __shfl_sync(kFull, rr.b.x, src);
+                rx.b.y = __shfl_sync(kFull, rr.b.y, src);
+                rx.b.z = __shfl_sync(kFull, rr.b.z, src);
+                rx.b.w = __shfl_sync(kFull, rr.b.w, src);
+                rx.c.x = __shfl_sync(kFull, rr.c.x, src);
+                rx.c.y = __shfl_sync(kFull, rr.c.y, src);
+                rx.c.z = __shfl_sync(kFull, rr.c.z, src);
+                rx.c.w = __shfl_sync(kFull, rr.c.w, src);
+                const float uax = __shfl_sync(kFull, ua, src);
+                const float ubx = __shfl_sync(kFull, ub, src);
+                const long long jx = __shfl_sync(kFull, (long long)jc, src);
+                const float payx = __shfl_sync(kFull, pay, src);
+                if (take) {
+                    w.init(g, trig, t, rx, uax, ubx);
+                    j = jx;
+                    acc = payx;
+                    active = true;
+                }
+                amask = __ballot_sync(kFull, active);
+            }
+        }
+        if (amask == 0) {
+            if (!more) break;
+            continue;
+        }
+#pragma unroll
+        for (int r = 0; r < kStepsPerCheck; ++r)
+            if (active && !w.step(g, trig, t, piece)) {
+                k.end(j, acc);
+                active = false;
+            }
+    }
 }
 
 }  // namespace cylct

@@ -74,7 +74,8 @@ def test_set_pose_equals_fresh_plan(lib):
         gu.project(plan, x)
         plan.cyl_plan_set_pose((s2.alpha, s2.beta, s2.gamma, s2.tx, s2.ty, s2.tz))
         got = gu.project(plan, x)
-    np.testing.assert_array_equal(got, ref)
+    # same rays and tiles; only the order of the per-tile atomic sums may differ
+    np.testing.assert_allclose(got, ref, rtol=1e-6, atol=1e-7)
 
 
 def test_row_sums_match_oracle(lib, orc):
