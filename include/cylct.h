@@ -153,6 +153,102 @@ int cyl_sart_solve(cyl_plan *plan, const void *sino, cyl_dtype sino_dtype, const
                    const float *w, const cyl_sart_params *params, void *x_out,
                    cyl_dtype x_dtype, void *stream);
 
+/* Batched SART: n scans (each its own plan: own pose, projection count and geometry,
+ * all on one device) reconstructed together, each exactly as cyl_sart_solve would with
+ * the same params.  A round advances every unfinished scan by one subset; each round is
+ * a tiled forward projection and a tiled back-projection with the fused Eq. 6 update over
+ * (tile, scan) blocks, and all rounds are queued as one CUDA graph (params->use_graph).
+ * Arrays (per scan i, in plan i's layout): sinos[i] of sino_dtype, x0s[i] (x0s or its
+ * entries NULL = zeros), ws[i] FP32 weights (ws or its entries NULL = none), x_outs[i] of
+ * x_dtype.  All DEVICE pointers on the plans' device; host arrays give CYL_EINVAL.
+ * Asynchronous on `stream`.  Errors: CYL_EINVAL, CYL_ENOMEM, CYL_EDEVICE. */
+int cyl_sart_solve_batch(int32_t n, cyl_plan *const *plans, const void *const *sinos,
+                         cyl_dtype sino_dtype, const void *const *x0s, const float *const *ws,
+                         const cyl_sart_params *params, void *const *x_outs, cyl_dtype x_dtype,
+                         void *stream);
+
+/* ---------------------------------------------------------------- serving
+ * A server reconstructs a stream of in-line inspection scans of registered part types
+ * (Sec. 2.4 / 3.3: series of same-type parts, each with its own pose; the grid is fixed to
+ * the part, so one warm-start volume and one weight map per part type stay resident).
+ * A scheduler thread runs continuous batching: each round advances every active scan by
+ * one SART subset with the batched kernels, and requests that arrive while others are on
+ * the GPU join at the next round as soon as their device footprint fits the HBM budget.
+ * Every scan gets exactly the arithmetic of cyl_sart_solve with the server's parameters.
+ */
+typedef struct cyl_server cyl_server;
+
+typedef struct cyl_server_cfg {
+    int32_t device;
+    int64_t hbm_budget_bytes;   /* device bytes the server may hold (parts + scans), > 0 */
+    int32_t max_active;         /* scans reconstructed together, 1 .. 1024 */
+    int32_t n_iter;             /* SART sweeps per scan */
+    int32_t subset_size;
+    double lambda;
+    int32_t weight_mode;
+    int32_t clamp_nonneg;
+    cyl_dtype storage;          /* dtype of sinograms and volumes (F32, F16 or BF16) */
+    int32_t rounds_ahead;       /* rounds queued on the GPU before the scheduler waits,
+                                   1 .. 64 (0 = 4) */
+} cyl_server_cfg;
+
+/* A request: one scan of a registered part type.  sino ([n_proj][H][W] line integrals of
+ * the server's storage dtype) and x_out ([N_h][N_theta][N_r] of the storage dtype) may be
+ * host or device memory; both must stay valid until cyl_poll reports completion.
+ * angles_rad (n_proj stage angles) is copied by cyl_submit. */
+typedef struct cyl_request {
+    int32_t part;
+    cyl_pose pose;
+    int32_t n_proj;
+    const double *angles_rad;
+    const void *sino;
+    void *x_out;
+} cyl_request;
+
+typedef struct cyl_result {
+    int32_t status;             /* CYL_OK, CYL_EPENDING, or the error the scan ended with */
+    int64_t submit_ns;          /* steady-clock times: submitted, admitted, result written */
+    int64_t admit_ns;
+    int64_t done_ns;
+} cyl_result;
+
+typedef struct cyl_server_stats {
+    int64_t submitted, completed, failed, active, queued;
+    int64_t rounds;             /* GPU rounds launched */
+    int64_t hbm_in_use;         /* bytes held by parts and admitted scans */
+} cyl_server_stats;
+
+/* Start a server and its scheduler thread.  Errors: CYL_EINVAL, CYL_EDEVICE, CYL_ENOMEM. */
+int cyl_server_create(const cyl_server_cfg *cfg, cyl_server **out);
+
+/* Register a part type: its grid, its acquisition geometry (geom->n_proj and
+ * geom->angles_rad are ignored: every request brings its own), a warm-start volume x0
+ * (storage dtype, NULL = zeros) and a weight map w (FP32, NULL = none), host or device
+ * memory, copied into resident device memory.  *part receives the part id.  Errors:
+ * CYL_EINVAL, CYL_EADMIT (the part alone exceeds the budget), CYL_ENOMEM, CYL_EDEVICE. */
+int cyl_server_add_part(cyl_server *srv, const cyl_grid *grid, const cyl_geom *geom,
+                        const void *x0, const float *w, int32_t *part);
+
+/* Queue a request; *ticket identifies it.  Never blocks on the GPU.  Errors: CYL_EINVAL,
+ * CYL_EADMIT (the scan can never fit the budget next to the resident parts),
+ * CYL_ECANCELLED (server shutting down). */
+int cyl_submit(cyl_server *srv, const cyl_request *req, uint64_t *ticket);
+
+/* Result of a ticket: CYL_OK once done (out filled, the ticket is then released),
+ * CYL_EPENDING while queued or running, CYL_ENOTFOUND for unknown or released tickets,
+ * or the scan's error. */
+int cyl_poll(cyl_server *srv, uint64_t ticket, cyl_result *out);
+
+/* Like cyl_poll, but waits up to timeout_ms for completion; CYL_ETIMEOUT if it is still
+ * pending then. */
+int cyl_wait(cyl_server *srv, uint64_t ticket, int64_t timeout_ms, cyl_result *out);
+
+int cyl_server_get_stats(cyl_server *srv, cyl_server_stats *out);
+
+/* Stop the scheduler (queued requests end with CYL_ECANCELLED, running ones finish),
+ * release all device memory and free the server.  NULL is accepted. */
+int cyl_server_destroy(cyl_server *srv);
+
 /* Segments (pieces of positive length between consecutive crossings, i.e. the
  * non-zero entries of each row of A counted with multiplicity) of each projection
  * p0 .. p0+np-1.  counts_out: device int64[np].  Used to state algorithmic bytes. */

@@ -65,7 +65,26 @@ struct UpdateArgs {
     int clamp;
 };
 
+// One scan of a batched solve (static for the whole solve).
+struct BatchScan {
+    ScanDev sd;
+    const void *sino;       // [N_p][H][W] of the batch's sinogram dtype
+    const void *x_proj;     // volume the projector reads (batch's projector dtype)
+    UpdateArgs upd;         // fused update (16-bit dtype of the batch)
+    float *q[2];            // two projection accumulators of subset_size x H x W
+    int64_t q_len;
+};
+
+// One unit of work of a round: subset [p0, p0 + np) of scan `scan`, accumulating into
+// that scan's projection buffer q[buf].
+struct BatchItem {
+    int scan, p0, np, buf;
+};
+
 // Kernel launchers (kernels.cu).  All return cudaError_t of the launch.
+cudaError_t launch_batch_round(const BatchScan *scans, const BatchItem *items, const int *n_items,
+                               int max_items, int round, int max_tiles, int smem_fp, int smem_bp,
+                               cyl_dtype xt, cyl_dtype st_, cyl_dtype x16t, cudaStream_t st);
 cudaError_t launch_rays(const GridDev &g, const ProjGeom *geo, int n_proj, float4 *ra,
                         float4 *rb, float4 *rc, cudaStream_t st);
 // q[v][pix] += sum over tiles of the tile's part of A x, views p0 .. p0+np-1 (q must be

@@ -90,31 +90,47 @@ struct FpK {
     }
 };
 
-// One CTA per (tile, view): stage the tile's voxels in shared memory, walk every ray of
-// the view that crosses the tile, add its partial line integral to q.
+// One CTA per (tile, views): stage the tile's voxels in shared memory once, then walk
+// every ray of views p0 .. p0+np-1 that crosses the tile, adding its partial line
+// integral to q (q holds np views).
 template <class T>
-__global__ void __launch_bounds__(kTileThreads)
-k_fp_tile(ScanDev sd, int p0, const T *__restrict__ x, float *__restrict__ q)
+__device__ __forceinline__ void fp_tile_body(const ScanDev &sd, int tile, int p0, int np,
+                                             const T *__restrict__ x, float *__restrict__ q,
+                                             float4 *smem4, WalkShared &ws)
 {
-    extern __shared__ float4 smem4[];
-    __shared__ WalkShared ws;
     const GridDev &g = sd.g;
-    const int tile = blockIdx.x, v = blockIdx.y, p = p0 + v;
-    const int4 bb = sd.bbox[(int64_t)p * sd.td.n_tiles + tile];
-    if (bb.x > bb.z || bb.y > bb.w) return;
     float2 *s_trig = reinterpret_cast<float2 *>(smem4);
     float *s_x = reinterpret_cast<float *>(s_trig + ((g.n_t + 1) & ~1));
     const Tile t = tile_of(sd.td, g, tile);
     const TileSpan s = span_of(g, t);
     stage_trig(sd, s_trig);
     for (int i = threadIdx.x; i < s.n; i += blockDim.x) s_x[i] = to_f32<T>(__ldg(x + tile_global(g, t, s, i)));
-    if (threadIdx.x == 0) ws.chunk = 0;
-    __syncthreads();
     const int64_t npix = (int64_t)g.det_w * g.det_h;
-    const int64_t r0 = (int64_t)p * npix;
-    FpK k{s_x, q + (int64_t)v * npix};
-    tile_walk_all(g, s_trig, t, sd.ray_a + r0, sd.ray_b + r0, sd.ray_c + r0, bb, k, &ws.chunk,
-                  ws.map[threadIdx.x >> 5]);
+    for (int v = 0; v < np; ++v) {
+        const int p = p0 + v;
+        const int4 bb = sd.bbox[(int64_t)p * sd.td.n_tiles + tile];
+        if (threadIdx.x == 0) ws.chunk = 0;
+        __syncthreads();
+        if (!(bb.x > bb.z || bb.y > bb.w)) {
+            const int64_t r0 = (int64_t)p * npix;
+            FpK k{s_x, q + (int64_t)v * npix};
+            tile_walk_all(g, s_trig, t, sd.ray_a + r0, sd.ray_b + r0, sd.ray_c + r0, bb, k,
+                          &ws.chunk, ws.map[threadIdx.x >> 5]);
+        }
+        __syncthreads();
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(kTileThreads)
+k_fp_tile(ScanDev sd, int p0, const T *__restrict__ x, float *__restrict__ q)
+{
+    extern __shared__ float4 smem4[];
+    __shared__ WalkShared ws;
+    const int tile = blockIdx.x, v = blockIdx.y;
+    const int4 bb = sd.bbox[(int64_t)(p0 + v) * sd.td.n_tiles + tile];
+    if (bb.x > bb.z || bb.y > bb.w) return;
+    fp_tile_body(sd, tile, p0 + v, 1, x, q + (int64_t)v * sd.g.det_w * sd.g.det_h, smem4, ws);
 }
 
 // ----------------------------------------------------------------- back-projection
@@ -162,14 +178,13 @@ __device__ __forceinline__ void sart_update(const UpdateArgs &u, int64_t m, floa
 // shared memory (y = SART residual (p - q) / L, or the given data in pure mode), then
 // either apply Eq. 6 to the tile's voxels (SART) or write num / den out (pure).
 template <class S, class X, bool SART>
-__global__ void __launch_bounds__(kTileThreads)
-k_bp_tile(ScanDev sd, int p0, int np, const S *__restrict__ y, const float *__restrict__ q,
-          UpdateArgs upd, float *__restrict__ num_out, float *__restrict__ den_out)
+__device__ __forceinline__ void bp_tile_body(const ScanDev &sd, int tile, int p0, int np,
+                                             const S *__restrict__ y, const float *__restrict__ q,
+                                             const UpdateArgs &upd, float *__restrict__ num_out,
+                                             float *__restrict__ den_out, float4 *smem4,
+                                             WalkShared &ws)
 {
-    extern __shared__ float4 smem4[];
-    __shared__ WalkShared ws;
     const GridDev &g = sd.g;
-    const int tile = blockIdx.x;
     float2 *s_trig = reinterpret_cast<float2 *>(smem4);
     const Tile t = tile_of(sd.td, g, tile);
     const TileSpan s = span_of(g, t);
@@ -211,6 +226,63 @@ k_bp_tile(ScanDev sd, int p0, int np, const S *__restrict__ y, const float *__re
             if (den_out) den_out[m] = s_den[i];
         }
     }
+}
+
+template <class S, class X, bool SART>
+__global__ void __launch_bounds__(kTileThreads)
+k_bp_tile(ScanDev sd, int p0, int np, const S *__restrict__ y, const float *__restrict__ q,
+          UpdateArgs upd, float *__restrict__ num_out, float *__restrict__ den_out)
+{
+    extern __shared__ float4 smem4[];
+    __shared__ WalkShared ws;
+    bp_tile_body<S, X, SART>(sd, blockIdx.x, p0, np, y, q, upd, num_out, den_out, smem4, ws);
+}
+
+// ------------------------------------------------------------------ batched solve
+
+// Round r of a batched solve works on items[r * max_items .. + n_items[r]): for each, one
+// subset of one scan.  Blocks are (tile, item); tiles beyond a scan's tile count and
+// items beyond the round's count exit at once.  The forward kernel also clears the
+// scan's other projection buffer, which the next round accumulates into.
+template <class T>
+__global__ void __launch_bounds__(kTileThreads)
+k_fp_batch(const BatchScan *__restrict__ scans, const BatchItem *__restrict__ items,
+           const int *__restrict__ n_items, int max_items, int round)
+{
+    extern __shared__ float4 smem4[];
+    __shared__ WalkShared ws;
+    const int k = blockIdx.y;
+    if (k >= n_items[round]) return;
+    const BatchItem it = items[(int64_t)round * max_items + k];
+    const BatchScan &sc = scans[it.scan];
+    const int tile = blockIdx.x;
+    if (tile >= sc.sd.td.n_tiles) return;
+    {   // clear the next round's buffer: tile t zeroes its share
+        float *qc = sc.q[it.buf ^ 1];
+        const int64_t n = sc.q_len;
+        const int64_t a = n * tile / sc.sd.td.n_tiles, b = n * (tile + 1) / sc.sd.td.n_tiles;
+        for (int64_t i = a + threadIdx.x; i < b; i += blockDim.x) qc[i] = 0.f;
+    }
+    fp_tile_body(sc.sd, tile, it.p0, it.np, static_cast<const T *>(sc.x_proj), sc.q[it.buf], smem4, ws);
+}
+
+template <class S, class X>
+__global__ void __launch_bounds__(kTileThreads)
+k_bp_batch(const BatchScan *__restrict__ scans, const BatchItem *__restrict__ items,
+           const int *__restrict__ n_items, int max_items, int round)
+{
+    extern __shared__ float4 smem4[];
+    __shared__ WalkShared ws;
+    const int k = blockIdx.y;
+    if (k >= n_items[round]) return;
+    const BatchItem it = items[(int64_t)round * max_items + k];
+    const BatchScan &sc = scans[it.scan];
+    const int tile = blockIdx.x;
+    if (tile >= sc.sd.td.n_tiles) return;
+    const int64_t npix = (int64_t)sc.sd.g.det_w * sc.sd.g.det_h;
+    const S *y = static_cast<const S *>(sc.sino) + (int64_t)it.p0 * npix;
+    bp_tile_body<S, X, true>(sc.sd, tile, it.p0, it.np, y, sc.q[it.buf], sc.upd, nullptr, nullptr,
+                             smem4, ws);
 }
 
 // ------------------------------------------------------------ counts, row sums
@@ -342,6 +414,17 @@ cudaError_t set_kernel_attributes()
     CYL_SET_BP(__nv_bfloat16)
 #undef CYL_SET_BP
     set((const void *)k_count_tile);
+    set((const void *)k_fp_batch<float>);
+    set((const void *)k_fp_batch<__half>);
+    set((const void *)k_fp_batch<__nv_bfloat16>);
+#define CYL_SET_BB(S)                                  \
+    set((const void *)k_bp_batch<S, float>);           \
+    set((const void *)k_bp_batch<S, __half>);          \
+    set((const void *)k_bp_batch<S, __nv_bfloat16>);
+    CYL_SET_BB(float)
+    CYL_SET_BB(__half)
+    CYL_SET_BB(__nv_bfloat16)
+#undef CYL_SET_BB
     return e;
 }
 
@@ -382,6 +465,27 @@ cudaError_t launch_bp_tiles(const ScanDev &sd, int p0, int np, const void *sino,
             using X = std::remove_pointer_t<decltype(tx)>;
             k_bp_tile<S, X, true><<<sd.td.n_tiles, kTileThreads, sd.td.smem_bp, st>>>(
                 sd, p0, np, (const S *)sino, q, *upd, nullptr, nullptr);
+            return cudaGetLastError();
+        });
+    });
+}
+
+cudaError_t launch_batch_round(const BatchScan *scans, const BatchItem *items, const int *n_items,
+                               int max_items, int round, int max_tiles, int smem_fp, int smem_bp,
+                               cyl_dtype xt, cyl_dtype st_, cyl_dtype x16t, cudaStream_t st)
+{
+    const dim3 grid(max_tiles, max_items);
+    cudaError_t e = dispatch1(xt, [&](auto *tx) {
+        using T = std::remove_pointer_t<decltype(tx)>;
+        k_fp_batch<T><<<grid, kTileThreads, smem_fp, st>>>(scans, items, n_items, max_items, round);
+        return cudaGetLastError();
+    });
+    if (e != cudaSuccess) return e;
+    return dispatch1(st_, [&](auto *ts) {
+        using S = std::remove_pointer_t<decltype(ts)>;
+        return dispatch1(x16t, [&](auto *tx) {
+            using X = std::remove_pointer_t<decltype(tx)>;
+            k_bp_batch<S, X><<<grid, kTileThreads, smem_bp, st>>>(scans, items, n_items, max_items, round);
             return cudaGetLastError();
         });
     });

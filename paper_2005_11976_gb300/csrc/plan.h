@@ -18,6 +18,10 @@ void build_grid(const cyl_grid &grid, const cyl_geom &geom, GridDev &g, std::vec
 void build_views(const cyl_grid &grid, const cyl_geom &geom, const cyl_pose &pose,
                  const TileDev &td, std::vector<ProjGeom> &geo, std::vector<int4> &bbox);
 
+// batch.cu: per round, the (scan, subset) items of a batched solve
+void batch_rounds(const std::vector<int> &n_proj, int subset, int n_iter,
+                  std::vector<BatchItem> &items, std::vector<int> &n_items, int &rounds);
+
 // Buffers and settings of one SART solve.
 struct SolveState {
     const void *sino = nullptr;

@@ -62,6 +62,32 @@ class cyl_sart_params(ctypes.Structure):
                 ("use_graph", ctypes.c_int32)]
 
 
+class cyl_server_cfg(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_int64),
+                ("max_active", ctypes.c_int32), ("n_iter", ctypes.c_int32),
+                ("subset_size", ctypes.c_int32), ("lambda_", ctypes.c_double),
+                ("weight_mode", ctypes.c_int32), ("clamp_nonneg", ctypes.c_int32),
+                ("storage", ctypes.c_int), ("rounds_ahead", ctypes.c_int32)]
+
+
+class cyl_request(ctypes.Structure):
+    _fields_ = [("part", ctypes.c_int32), ("pose", cyl_pose), ("n_proj", ctypes.c_int32),
+                ("angles_rad", ctypes.POINTER(ctypes.c_double)), ("sino", ctypes.c_void_p),
+                ("x_out", ctypes.c_void_p)]
+
+
+class cyl_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("submit_ns", ctypes.c_int64),
+                ("admit_ns", ctypes.c_int64), ("done_ns", ctypes.c_int64)]
+
+
+class cyl_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("failed", ctypes.c_int64), ("active", ctypes.c_int64),
+                ("queued", ctypes.c_int64), ("rounds", ctypes.c_int64),
+                ("hbm_in_use", ctypes.c_int64)]
+
+
 _VP = ctypes.c_void_p
 _I32 = ctypes.c_int32
 _I64 = ctypes.c_int64
@@ -83,6 +109,16 @@ SIGNATURES = {
     "cyl_sart_solve": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP,
                                       ctypes.POINTER(cyl_sart_params), _VP, ctypes.c_int, _VP]),
     "cyl_count_segments": (ctypes.c_int, [_VP, _I32, _I32, _VP, _VP]),
+    "cyl_sart_solve_batch": (ctypes.c_int, [_I32, _VP, _VP, ctypes.c_int, _VP, _VP,
+                                            ctypes.POINTER(cyl_sart_params), _VP, ctypes.c_int, _VP]),
+    "cyl_server_create": (ctypes.c_int, [ctypes.POINTER(cyl_server_cfg), ctypes.POINTER(_VP)]),
+    "cyl_server_add_part": (ctypes.c_int, [_VP, ctypes.POINTER(cyl_grid), ctypes.POINTER(cyl_geom),
+                                           _VP, _VP, ctypes.POINTER(_I32)]),
+    "cyl_submit": (ctypes.c_int, [_VP, ctypes.POINTER(cyl_request), ctypes.POINTER(ctypes.c_uint64)]),
+    "cyl_poll": (ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.POINTER(cyl_result)]),
+    "cyl_wait": (ctypes.c_int, [_VP, ctypes.c_uint64, _I64, ctypes.POINTER(cyl_result)]),
+    "cyl_server_get_stats": (ctypes.c_int, [_VP, ctypes.POINTER(cyl_server_stats)]),
+    "cyl_server_destroy": (ctypes.c_int, [_VP]),
     "cyl_plan_set_timing": (ctypes.c_int, [_VP, ctypes.c_int]),
     "cyl_plan_kernel_time": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                             ctypes.POINTER(_I64)]),
@@ -240,6 +276,90 @@ class Plan:
         return ms.value, n.value
 
 
+def _ptr_array(items):
+    arr = (ctypes.c_void_p * len(items))(*[ptr(a) for a in items])
+    return arr
+
+
+def cyl_sart_solve_batch(plans, sinos, sino_dtype, x0s, ws, params, x_outs, x_dtype, stream=None):
+    """Batched SART over Plan objects; x0s / ws may be None or lists with None entries."""
+    n = len(plans)
+    hp = _ptr_array([p.h.value for p in plans])
+    hs = _ptr_array(sinos)
+    hx0 = _ptr_array(x0s) if x0s is not None else None
+    hw = _ptr_array(ws) if ws is not None else None
+    ho = _ptr_array(x_outs)
+    _check(load().cyl_sart_solve_batch(n, hp, hs, sino_dtype, hx0, hw, ctypes.byref(params), ho,
+                                       x_dtype, stream_ptr(stream)), "cyl_sart_solve_batch")
+
+
 def cyl_log_transform(counts, in_dtype, i0, p_out, out_dtype, n, stream=None):
     _check(load().cyl_log_transform(ptr(counts), in_dtype, float(i0), ptr(p_out), out_dtype, n,
                                     stream_ptr(stream)), "cyl_log_transform")
+
+
+class Server:
+    """Owns a cyl_server; methods map one to one onto the serving entry points."""
+
+    def __init__(self, hbm_budget_bytes, max_active=64, n_iter=10, subset_size=1, lam=0.5,
+                 weight_mode=1, clamp_nonneg=False, storage=CYL_F32, rounds_ahead=4, device=0):
+        lib = load()
+        self.cfg = cyl_server_cfg(device, int(hbm_budget_bytes), max_active, n_iter, subset_size,
+                                  lam, weight_mode, int(clamp_nonneg), storage, rounds_ahead)
+        h = _VP()
+        _check(lib.cyl_server_create(ctypes.byref(self.cfg), ctypes.byref(h)), "cyl_server_create")
+        self.h = h
+        self._keep = {}
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            load().cyl_server_destroy(self.h)
+            self.h = None
+        self._keep = {}
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def cyl_server_add_part(self, scan, x0=None, w=None) -> int:
+        grid, geom, pose, ang = structs_from_scan(scan)
+        part = _I32()
+        _check(load().cyl_server_add_part(self.h, ctypes.byref(grid), ctypes.byref(geom), ptr(x0),
+                                          ptr(w), ctypes.byref(part)), "cyl_server_add_part")
+        return part.value
+
+    def cyl_submit(self, part, pose, angles, sino, x_out) -> int:
+        ang = np.ascontiguousarray(angles, dtype=np.float64)
+        req = cyl_request(part, cyl_pose(*[float(v) for v in pose]), len(ang),
+                          ang.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ptr(sino), ptr(x_out))
+        t = ctypes.c_uint64()
+        _check(load().cyl_submit(self.h, ctypes.byref(req), ctypes.byref(t)), "cyl_submit")
+        self._keep[t.value] = (sino, x_out)       # the caller's buffers stay referenced
+        return t.value
+
+    def cyl_poll(self, ticket):
+        r = cyl_result()
+        rc = load().cyl_poll(self.h, ticket, ctypes.byref(r))
+        if rc != CYL_EPENDING:
+            self._keep.pop(ticket, None)
+        return rc, r
+
+    def cyl_wait(self, ticket, timeout_ms=600000):
+        r = cyl_result()
+        rc = load().cyl_wait(self.h, ticket, int(timeout_ms), ctypes.byref(r))
+        if rc not in (CYL_EPENDING, CYL_ETIMEOUT):
+            self._keep.pop(ticket, None)
+        return rc, r
+
+    def stats(self) -> dict:
+        s = cyl_server_stats()
+        _check(load().cyl_server_get_stats(self.h, ctypes.byref(s)), "cyl_server_get_stats")
+        return {k: getattr(s, k) for k, _ in cyl_server_stats._fields_}

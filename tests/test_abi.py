@@ -84,3 +84,18 @@ def test_binding_fails_loudly_without_library(tmp_path):
             cylct.load(str(tmp_path / "missing.so"))
         finally:
             cylct._lib = saved
+
+
+def test_server_config_validation_without_gpu(lib):
+    bad = [dict(hbm_budget_bytes=0), dict(max_active=0), dict(max_active=5000), dict(n_iter=-1),
+           dict(subset_size=0), dict(weight_mode=3), dict(storage=9), dict(rounds_ahead=99)]
+    for b in bad:
+        cfg = dict(device=0, hbm_budget_bytes=1 << 30, max_active=8, n_iter=2, subset_size=1,
+                   lambda_=0.5, weight_mode=1, clamp_nonneg=0, storage=0, rounds_ahead=4)
+        cfg.update(b)
+        c = cylct.cyl_server_cfg(**cfg)
+        h = ctypes.c_void_p()
+        assert lib.cyl_server_create(ctypes.byref(c), ctypes.byref(h)) == cylct.CYL_EINVAL, b
+    assert lib.cyl_server_destroy(None) == cylct.CYL_OK
+    assert lib.cyl_poll(None, 1, None) == cylct.CYL_EINVAL
+    assert lib.cyl_sart_solve_batch(-1, None, None, 0, None, None, None, None, 0, None) == cylct.CYL_EINVAL
