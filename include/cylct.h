@@ -131,6 +131,22 @@ int cyl_row_sums(cyl_plan *plan, int32_t p0, int32_t np, float *L_out, void *str
 int cyl_project(cyl_plan *plan, const void *vol, cyl_dtype vol_dtype, int32_t p0,
                 int32_t np, void *sino_out, cyl_dtype sino_dtype, void *stream);
 
+/* Allocation-free forward projection.  The paper has no counterpart: this entry point
+ * serves callers that must not allocate device memory while they run, such as a host
+ * framework that owns all device memory through its own caching allocator, or an in-line
+ * inspection loop that cannot afford an allocation (and the synchronisation it may bring)
+ * between two parts.  Same arguments and result as cyl_project, but the FP32 accumulator
+ * is a fixed array in the library's static device memory (CYL_NOALLOC_MAX_ELEMS floats,
+ * 16 MiB, held on every GPU that loads the library until the process exits), so the call
+ * makes no allocation at all.  np * H * W above CYL_NOALLOC_MAX_ELEMS gives CYL_EINVAL.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.  Every call
+ * shares the one array (it is cleared at the start of each call): calls that overlap on
+ * the GPU, from any stream or thread, race and corrupt each other's results. */
+#define CYL_NOALLOC_MAX_ELEMS (4 * 1024 * 1024)
+int cyl_project_noalloc(cyl_plan *plan, const void *vol, cyl_dtype vol_dtype, int32_t p0,
+                        int32_t np, void *sino_out, cyl_dtype sino_dtype, void *stream);
+
 /* Matched back-projection out = A^T y over projections p0 .. p0+np-1 (the transpose of
  * exactly the t_jl cyl_project uses; Sec. 2.2 back-projection).  sino: device [np][H][W]
  * of sino_dtype.  vol_out: device float volume, OVERWRITTEN with A^T y.  colsum_out:

@@ -105,6 +105,7 @@ SIGNATURES = {
                                          _I64, _VP]),
     "cyl_row_sums": (ctypes.c_int, [_VP, _I32, _I32, _VP, _VP]),
     "cyl_project": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _I32, _I32, _VP, ctypes.c_int, _VP]),
+    "cyl_project_noalloc": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _I32, _I32, _VP, ctypes.c_int, _VP]),
     "cyl_backproject": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _I32, _I32, _VP, _VP, _VP]),
     "cyl_sart_solve": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP,
                                       ctypes.POINTER(cyl_sart_params), _VP, ctypes.c_int, _VP]),
@@ -252,6 +253,10 @@ class Plan:
     def cyl_project(self, vol, vol_dtype, p0, np_, sino_out, sino_dtype, stream=None):
         _check(load().cyl_project(self.h, ptr(vol), vol_dtype, p0, np_, ptr(sino_out), sino_dtype,
                                   stream_ptr(stream)), "cyl_project")
+
+    def cyl_project_noalloc(self, vol, vol_dtype, p0, np_, sino_out, sino_dtype, stream=None):
+        _check(load().cyl_project_noalloc(self.h, ptr(vol), vol_dtype, p0, np_, ptr(sino_out),
+                                          sino_dtype, stream_ptr(stream)), "cyl_project_noalloc")
 
     def cyl_backproject(self, sino, sino_dtype, p0, np_, vol_out, colsum_out=None, stream=None):
         _check(load().cyl_backproject(self.h, ptr(sino), sino_dtype, p0, np_, ptr(vol_out),
