@@ -34,6 +34,9 @@ sys.path.insert(0, ROOT)
 METRIC = "SART iters/sec and GRays/s at stated rel err; batched-serve vs plain scans/s, p99"
 UNIT = "SART iters/s"
 N_ITER = 20
+# DRAM bytes (read + write) per launch of each kernel at the medium workload, from one ncu
+# capture of the current kernels (profiles/); empty until such a capture exists.
+TRAFFIC: dict = {}
 LAMBDA = 0.5
 I0 = 1.0e4
 
@@ -304,26 +307,34 @@ def main():
 
     # --- roofline of the dominant kernel (segment-touch algorithmic bytes)
     hbm, peak_kind = peaks()
-    kinds = ["forward projection (tiled, k_fp_tile)",
-             "back-projection + fused SART update (tiled, k_bp_tile)"]
+    kinds = ["forward projection (k_fp_ray)",
+             "back-projection into (num, den) (k_bp_ray)",
+             "SART voxel update (k_update_nd)"]
     roof = None
-    if not args.graph and k_n[0] and k_n[1]:
-        S = float(seg.sum())
-        # segment-touch model: forward = one volume value per segment + the view's
-        # projections; back + update = one residual per segment + volume read/write + weights
-        fwd_bytes = (S * 4 + scan.n_proj * n_pix * 4) / scan.n_proj
-        bp_bytes = (S * 4 + scan.n_proj * n_pix * 4) / scan.n_proj + n_vox * (2 * 4 + 4)
-        per = [fwd_bytes, bp_bytes]
-        avg_ms = [k_ms[k] / k_n[k] for k in range(2)]
-        dom = int(np.argmax(k_ms[:2]))
-        achieved = per[dom] / (avg_ms[dom] / 1e3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None, "kernel": kinds[dom],
-                "peak_source": peak_kind,
+    if not args.graph and all(k_n):
+        S = float(seg.sum()) / scan.n_proj           # segments per view (= per launch)
+        ray_rec = 48                                 # three float4 per ray
+        # segment-touch model per launch (one view):
+        #   forward: one volume value per segment, the ray records, the projections written,
+        #            and the spare (num, den) accumulator cleared for the next subset
+        #   back:    one 8-byte (num, den) update per segment, the ray records, y and q read
+        #   update:  (num, den), x read and written, the weight map read
+        per = [S * 4 + n_pix * (ray_rec + 4) + n_vox * 8,
+               S * 8 + n_pix * (ray_rec + 4 + 4),
+               n_vox * (8 + 4 + 4 + 4)]
+        avg_ms = [k_ms[k] / k_n[k] for k in range(3)]
+        dom = int(np.argmax(k_ms))
+        ach = [per[k] / (avg_ms[k] / 1e3) / 1e9 for k in range(3)]
+        roof = {"bound": "hbm", "achieved": ach[dom], "peak": hbm, "unit": "GB/s",
+                "frac": ach[dom] / hbm, "traffic": TRAFFIC.get(kinds[dom].split("(")[-1][:-1]),
+                "kernel": kinds[dom], "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": per[dom],
-                "kernel_ms_avg": {kinds[k]: avg_ms[k] for k in range(2)},
-                "kernel_share": {kinds[k]: k_ms[k] / sum(k_ms[:2]) for k in range(2)},
-                "segments_per_view": S / scan.n_proj}
+                "units_per_launch": "one view: %d rays, %.4g segments" % (n_pix, S),
+                "kernel_ms_avg": {kinds[k]: avg_ms[k] for k in range(3)},
+                "kernel_gbs": {kinds[k]: ach[k] for k in range(3)},
+                "kernel_frac": {kinds[k]: ach[k] / hbm for k in range(3)},
+                "kernel_share": {kinds[k]: k_ms[k] / sum(k_ms) for k in range(3)},
+                "segments_per_view": S}
 
     # --- CPU oracle on a bounded sample, and a live parity check on that sample
     cpu = None

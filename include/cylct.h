@@ -278,6 +278,12 @@ int cyl_count_segments(cyl_plan *plan, int32_t p0, int32_t np, int64_t *counts_o
 int cyl_plan_set_timing(cyl_plan *plan, int enable);
 int cyl_plan_kernel_time(cyl_plan *plan, int kind, double *ms_total, int64_t *launches);
 
+/* Autotuner: times the projector and the back-projector of view 0 with each ray cut
+ * into 1, 2, 4 or 8 pieces (one thread per piece) and keeps the fastest setting of each
+ * for this plan.  Synchronises `stream`.  cyl_plan_get_pieces reports the settings. */
+int cyl_plan_tune(cyl_plan *plan, void *stream);
+int cyl_plan_get_pieces(const cyl_plan *plan, int32_t *fp_pieces, int32_t *bp_pieces);
+
 /* Sizes of a plan: voxels, rays per projection, projections, and the device bytes the
  * plan holds. */
 int cyl_plan_sizes(const cyl_plan *plan, int64_t *n_vox, int64_t *n_pix, int32_t *n_proj,

@@ -193,7 +193,7 @@ extern "C" int cyl_project(cyl_plan *plan, const void *vol, cyl_dtype vol_dtype,
         q = plan->d_q;
     }
     CYL_CUDA(cudaMemsetAsync(q, 0, sizeof(float) * n, st));
-    CYL_CUDA(launch_fp_tiles(plan->scan_dev(), p0, np, vol, vol_dtype, q, st));
+    CYL_CUDA(launch_fp_rays(plan->scan_dev(), plan->p_fp, p0, np, vol, vol_dtype, q, nullptr, 0, st));
     if (sino_dtype != CYL_F32) CYL_CUDA(launch_convert(q, CYL_F32, sino_out, sino_dtype, (int64_t)n, st));
     return CYL_OK;
 }
@@ -206,8 +206,11 @@ extern "C" int cyl_backproject(cyl_plan *plan, const void *sino, cyl_dtype sino_
     if (!valid_dtype(sino_dtype)) return set_error(CYL_EINVAL, "bad dtype");
     if (!vol_out || (np > 0 && !sino)) return set_error(CYL_EINVAL, "null array");
     DeviceGuard dg(plan->device);
-    CYL_CUDA(launch_bp_tiles(plan->scan_dev(), p0, np, sino, sino_dtype, nullptr, nullptr, vol_out,
-                             colsum_out, (cudaStream_t)stream));
+    cudaStream_t st = (cudaStream_t)stream;
+    CYL_CUDA(cudaMemsetAsync(vol_out, 0, sizeof(float) * plan->n_vox, st));
+    if (colsum_out) CYL_CUDA(cudaMemsetAsync(colsum_out, 0, sizeof(float) * plan->n_vox, st));
+    CYL_CUDA(launch_bp_rays(plan->scan_dev(), plan->p_bp, p0, np, sino, sino_dtype, nullptr, nullptr,
+                            vol_out, colsum_out, st));
     return CYL_OK;
 }
 
@@ -221,7 +224,30 @@ extern "C" int cyl_count_segments(cyl_plan *plan, int32_t p0, int32_t np, int64_
     DeviceGuard dg(plan->device);
     cudaStream_t st = (cudaStream_t)stream;
     CYL_CUDA(cudaMemsetAsync(counts_out, 0, sizeof(int64_t) * np, st));
-    CYL_CUDA(launch_count(plan->scan_dev(), p0, np, reinterpret_cast<unsigned long long *>(counts_out), st));
+    CYL_CUDA(launch_count_rays(plan->scan_dev(), p0, np, reinterpret_cast<unsigned long long *>(counts_out), st));
+    return CYL_OK;
+}
+
+extern "C" int cyl_plan_tune(cyl_plan *plan, void *stream)
+{
+    if (!plan) return set_error(CYL_EINVAL, "plan is null");
+    DeviceGuard dg(plan->device);
+    std::lock_guard<std::mutex> lock(plan->mu);
+    cudaStream_t user = (cudaStream_t)stream;
+    CYL_CUDA(cudaEventRecord(plan->ev_in, user));
+    CYL_CUDA(cudaStreamWaitEvent(plan->ws, plan->ev_in, 0));
+    int rc = plan->tune(plan->ws);
+    if (rc) return rc;
+    CYL_CUDA(cudaEventRecord(plan->ev_out, plan->ws));
+    CYL_CUDA(cudaStreamWaitEvent(user, plan->ev_out, 0));
+    return CYL_OK;
+}
+
+extern "C" int cyl_plan_get_pieces(const cyl_plan *plan, int32_t *fp, int32_t *bp)
+{
+    if (!plan) return set_error(CYL_EINVAL, "plan is null");
+    if (fp) *fp = plan->p_fp;
+    if (bp) *bp = plan->p_bp;
     return CYL_OK;
 }
 

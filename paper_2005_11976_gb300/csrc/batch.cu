@@ -1,10 +1,11 @@
 // Batched SART: many scans (own pose, own projection count) reconstructed together.
 //
 // Every scan runs exactly the subsets of its own cyl_sart_solve (Eq. 6, n_iter sweeps in
-// index order); a round advances each unfinished scan by one subset.  A round is two
-// kernels over (tile, scan) blocks: the tiled forward projection of the scans' current
-// subsets, then the tiled back-projection with the fused update.  The rounds are queued
-// once into a CUDA graph and launched as a single graph.
+// index order); a round advances each unfinished scan by one subset.  A round is three
+// kernels over (ray piece, scan) blocks: the forward projection of the scans' current
+// subsets, the back-projection into each scan's (numerator, denominator) accumulator, and
+// the voxel update.  The rounds are queued once into a CUDA graph and launched as a
+// single graph.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -116,7 +117,9 @@ extern "C" int cyl_sart_solve_batch(int32_t n, cyl_plan *const *plans, const voi
     }
 
     const size_t xb = dtype_size(x_dtype);
-    int max_tiles = 0, smem_fp = 0, smem_bp = 0, rc;
+    int max_nt = 0, rc;
+    int64_t max_rays = 0, max_vox = 0;
+    const int P = plans[0]->p_fp;
     std::vector<BatchScan> scans(n);
     std::vector<int> n_proj(n);
     for (int i = 0; i < n; ++i) {
@@ -125,6 +128,7 @@ extern "C" int cyl_sart_solve_batch(int32_t n, cyl_plan *const *plans, const voi
         const size_t qlen = (size_t)subset * pl->n_pix;
         if ((rc = pl->ensure((void **)&pl->d_q, pl->q_cap, 2 * sizeof(float) * qlen))) return rc;
         BT_CUDA(cudaMemsetAsync(pl->d_q, 0, 2 * sizeof(float) * qlen, bs));
+        for (int k = 0; k < 2; ++k) BT_CUDA(cudaMemsetAsync(pl->d_nd[k], 0, sizeof(float2) * pl->n_vox, bs));
         const void *x0 = x0s ? x0s[i] : nullptr;
         const float *w = ws ? ws[i] : nullptr;
         void *xo = x_outs[i];
@@ -137,6 +141,12 @@ extern "C" int cyl_sart_solve_batch(int32_t n, cyl_plan *const *plans, const voi
         sc.q[0] = pl->d_q;
         sc.q[1] = pl->d_q + qlen;
         sc.q_len = (int64_t)qlen;
+        sc.nd[0] = pl->d_nd[0];
+        sc.nd[1] = pl->d_nd[1];
+        sc.nd_len = pl->n_vox;
+        max_rays = std::max(max_rays, (int64_t)qlen);
+        max_vox = std::max(max_vox, pl->n_vox);
+        max_nt = std::max(max_nt, pl->g.n_t);
         UpdateArgs &u = sc.upd;
         u.x32 = nullptr;
         u.x16 = nullptr;
@@ -158,9 +168,6 @@ extern "C" int cyl_sart_solve_batch(int32_t n, cyl_plan *const *plans, const voi
         u.lambda = (float)prm->lambda;
         u.clamp = prm->clamp_nonneg ? 1 : 0;
         if (w) BT_CUDA(launch_weight_scale(w, pl->n_vox, prm->weight_mode, (float)prm->lambda, pl->d_wscale, bs));
-        max_tiles = std::max(max_tiles, pl->td.n_tiles);
-        smem_fp = std::max(smem_fp, pl->td.smem_fp);
-        smem_bp = std::max(smem_bp, pl->td.smem_bp);
         n_proj[i] = pl->geom.n_proj;
     }
     std::vector<BatchItem> items;
@@ -187,8 +194,8 @@ extern "C" int cyl_sart_solve_batch(int32_t n, cyl_plan *const *plans, const voi
             BT_CUDA(cudaStreamBeginCapture(bs, cudaStreamCaptureModeThreadLocal));
             cudaError_t ce = cudaSuccess;
             for (int r = 0; r < rounds && ce == cudaSuccess; ++r)
-                ce = launch_batch_round(d_scans, d_items, d_n, n, r, max_tiles, smem_fp, smem_bp,
-                                        x_dtype, sino_dtype, x16t, bs);
+                ce = launch_batch_round_rays(d_scans, d_items, d_n, n, r, max_rays, max_vox, max_nt,
+                                             P, x_dtype, sino_dtype, x16t, bs);
             cudaError_t ee = cudaStreamEndCapture(bs, &graph);
             if (ce != cudaSuccess) {
                 if (graph) cudaGraphDestroy(graph);
@@ -203,8 +210,8 @@ extern "C" int cyl_sart_solve_batch(int32_t n, cyl_plan *const *plans, const voi
             if (ce != cudaSuccess) return cuda_error(ce, "cudaGraphLaunch");
         } else {
             for (int r = 0; r < rounds; ++r)
-                BT_CUDA(launch_batch_round(d_scans, d_items, d_n, n, r, max_tiles, smem_fp, smem_bp,
-                                           x_dtype, sino_dtype, x16t, bs));
+                BT_CUDA(launch_batch_round_rays(d_scans, d_items, d_n, n, r, max_rays, max_vox, max_nt,
+                                                P, x_dtype, sino_dtype, x16t, bs));
         }
         BT_CUDA(cudaFreeAsync(d_blob, bs));
     }

@@ -73,6 +73,8 @@ struct BatchScan {
     UpdateArgs upd;         // fused update (16-bit dtype of the batch)
     float *q[2];            // two projection accumulators of subset_size x H x W
     int64_t q_len;
+    float2 *nd[2];          // two (numerator, column sum) accumulators of N voxels
+    int64_t nd_len;
 };
 
 // One unit of work of a round: subset [p0, p0 + np) of scan `scan`, accumulating into
@@ -101,6 +103,21 @@ cudaError_t launch_row_sums(const ScanDev &sd, int p0, int np, float *L, cudaStr
 cudaError_t launch_count(const ScanDev &sd, int p0, int np, unsigned long long *counts,
                          cudaStream_t st);
 cudaError_t set_kernel_attributes();
+
+// Ray-piece kernels (rays.cu).  P = pieces per ray (1, 2, 4 or 8).
+cudaError_t launch_fp_rays(const ScanDev &sd, int P, int p0, int np, const void *x, cyl_dtype xt,
+                           float *q, float2 *zero_buf, int64_t zero_len, cudaStream_t st);
+// q != null: SART residual (y - q) / L into nd; q == null: pure A^T y into nd, or into
+// num / den (den may be null) when nd is null.
+cudaError_t launch_bp_rays(const ScanDev &sd, int P, int p0, int np, const void *y, cyl_dtype yt,
+                           const float *q, float2 *nd, float *num, float *den, cudaStream_t st);
+cudaError_t launch_update_nd(int64_t n_vox, const float2 *nd, const UpdateArgs &u, cudaStream_t st);
+cudaError_t launch_count_rays(const ScanDev &sd, int p0, int np, unsigned long long *counts,
+                              cudaStream_t st);
+cudaError_t launch_batch_round_rays(const BatchScan *scans, const BatchItem *items, const int *n_items,
+                                    int max_items, int round, int64_t max_rays, int64_t max_vox,
+                                    int max_nt, int P, cyl_dtype xt, cyl_dtype yt, cyl_dtype x16t,
+                                    cudaStream_t st);
 cudaError_t launch_log(const void *in, cyl_dtype it, double i0, void *out, cyl_dtype ot,
                        int64_t n, cudaStream_t st);
 cudaError_t launch_convert(const void *in, cyl_dtype it, void *out, cyl_dtype ot,

@@ -67,7 +67,7 @@ extern "C" int cyl_project_noalloc(cyl_plan *plan, const void *vol, cyl_dtype vo
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(float) * (size_t)n, st);
-    if (e == cudaSuccess) e = launch_fp_tiles(plan->scan_dev(), p0, np, vol, vol_dtype, acc, st);
+    if (e == cudaSuccess) e = launch_fp_rays(plan->scan_dev(), plan->p_fp, p0, np, vol, vol_dtype, acc, nullptr, 0, st);
     if (e == cudaSuccess) e = launch_convert(acc, CYL_F32, sino_out, sino_dtype, n, st);
     return e == cudaSuccess ? CYL_OK : cuda_error(e, "cyl_project_noalloc");
 }

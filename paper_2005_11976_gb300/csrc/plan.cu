@@ -53,6 +53,8 @@ int cyl_plan::init(const cyl_grid &gr, const cyl_geom &ge, const cyl_pose &po, i
     if ((rc = alloc(&d_bbox, sizeof(int4) * (size_t)geom.n_proj * td.n_tiles))) return rc;
     for (int k = 0; k < 3; ++k)
         if ((rc = alloc(&d_ray[k], sizeof(float4) * n_rays))) return rc;
+    for (int k = 0; k < 2; ++k)
+        if ((rc = alloc(&d_nd[k], sizeof(float2) * n_vox))) return rc;
     if ((rc = alloc(&d_wscale, 2 * sizeof(float)))) return rc;
     PL_CUDA(cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking));
     PL_CUDA(cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming));
@@ -83,6 +85,13 @@ int cyl_plan::upload_pose(const cyl_pose &po, cudaStream_t st)
     return CYL_OK;
 }
 
+void cyl_plan::drop_graphs()
+{
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (gexec_odd) cudaGraphExecDestroy(gexec_odd);
+    gexec = gexec_odd = nullptr;
+}
+
 int cyl_plan::ensure(void **p, size_t &cap, size_t nbytes)
 {
     if (*p && cap >= nbytes) return CYL_OK;
@@ -94,10 +103,7 @@ int cyl_plan::ensure(void **p, size_t &cap, size_t nbytes)
         bytes -= cap;
         *p = nullptr;
         cap = 0;
-        if (gexec) {                 // a captured graph may point at the old buffer
-            cudaGraphExecDestroy(gexec);
-            gexec = nullptr;
-        }
+        drop_graphs();               // a captured graph may point at the old buffer
     }
     int rc = alloc(p, nbytes);
     if (!rc) cap = nbytes;
@@ -120,7 +126,7 @@ cudaEvent_t *cyl_plan::next_events(int n)
 cyl_plan::~cyl_plan()
 {
     if (ws) cudaStreamSynchronize(ws);
-    if (gexec) cudaGraphExecDestroy(gexec);
+    drop_graphs();
     for (cudaEvent_t e : events) cudaEventDestroy(e);
     if (ev_in) cudaEventDestroy(ev_in);
     if (ev_out) cudaEventDestroy(ev_out);
@@ -131,10 +137,12 @@ cyl_plan::~cyl_plan()
     for (void *p : allocs) cudaFree(p);
 }
 
-// One sweep: for every subset, zero q, forward-project the subset (tiles), then
-// back-project its residuals with the fused update.  Timed runs put an event before the
-// forward projection, between the two kernels and after the back-projection.
-int cyl_plan::queue_sweep(const SolveState &s, cudaStream_t st, bool timed)
+// One sweep.  Subset k of the sweep uses accumulator b = (parity + k) & 1: zero its
+// projections, forward-project (the kernel also clears accumulator b ^ 1, which the
+// previous subset's update has consumed), back-project the residuals into accumulator b,
+// then apply Eq. 6.  Timed runs record an event before the forward projection, between
+// the kernels and after the update.
+int cyl_plan::queue_sweep(const SolveState &s, cudaStream_t st, bool timed, int parity)
 {
     const ScanDev sd = scan_dev();
     UpdateArgs upd;
@@ -146,17 +154,21 @@ int cyl_plan::queue_sweep(const SolveState &s, cudaStream_t st, bool timed)
     upd.wscale = s.w ? d_wscale : nullptr;
     upd.lambda = (float)s.lambda;
     upd.clamp = s.clamp;
-    for (int p0 = 0; p0 < geom.n_proj; p0 += s.subset) {
+    int k = 0;
+    for (int p0 = 0; p0 < geom.n_proj; p0 += s.subset, ++k) {
         const int np = std::min(s.subset, geom.n_proj - p0);
+        const int b = (parity + k) & 1;
         const void *sino_p = static_cast<const char *>(s.sino) + (size_t)p0 * n_pix * dtype_size(s.sino_t);
-        cudaEvent_t *ev = timed ? next_events(3) : nullptr;
+        cudaEvent_t *ev = timed ? next_events(4) : nullptr;
         if (timed && !ev) return set_error(CYL_EDEVICE, "event creation failed");
         if (ev) PL_CUDA(cudaEventRecord(ev[0], st));
         PL_CUDA(cudaMemsetAsync(d_q, 0, sizeof(float) * (size_t)np * n_pix, st));
-        PL_CUDA(launch_fp_tiles(sd, p0, np, s.x_proj, s.x_proj_t, d_q, st));
+        PL_CUDA(launch_fp_rays(sd, p_fp, p0, np, s.x_proj, s.x_proj_t, d_q, d_nd[b ^ 1], n_vox, st));
         if (ev) PL_CUDA(cudaEventRecord(ev[1], st));
-        PL_CUDA(launch_bp_tiles(sd, p0, np, sino_p, s.sino_t, d_q, &upd, nullptr, nullptr, st));
+        PL_CUDA(launch_bp_rays(sd, p_bp, p0, np, sino_p, s.sino_t, d_q, d_nd[b], nullptr, nullptr, st));
         if (ev) PL_CUDA(cudaEventRecord(ev[2], st));
+        PL_CUDA(launch_update_nd(n_vox, d_nd[b], upd, st));
+        if (ev) PL_CUDA(cudaEventRecord(ev[3], st));
     }
     return CYL_OK;
 }
@@ -169,6 +181,7 @@ int cyl_plan::solve(const void *sino, cyl_dtype sino_t, const void *x0, const fl
     const size_t xb = dtype_size(x_t), sb = dtype_size(sino_t);
     const size_t sino_bytes = (size_t)geom.n_proj * n_pix * sb;
     const int subset = std::min(prm.subset_size, geom.n_proj);
+    const int n_sub = (geom.n_proj + subset - 1) / subset;
     int rc;
     if ((rc = ensure((void **)&d_q, q_cap, sizeof(float) * (size_t)n_pix * subset))) return rc;
 
@@ -226,38 +239,41 @@ int cyl_plan::solve(const void *sino, cyl_dtype sino_t, const void *x0, const fl
         }
     }
     if (d_w) PL_CUDA(launch_weight_scale(d_w, n_vox, prm.weight_mode, (float)prm.lambda, d_wscale, ws));
+    for (int k = 0; k < 2; ++k) PL_CUDA(cudaMemsetAsync(d_nd[k], 0, sizeof(float2) * n_vox, ws));
 
     if (timing) {
         ev_used = 0;
         for (int it = 0; it < prm.n_iter; ++it)
-            if ((rc = queue_sweep(s, ws, true))) return rc;
+            if ((rc = queue_sweep(s, ws, true, (it * n_sub) & 1))) return rc;
     } else if (prm.use_graph && prm.n_iter > 0) {
-        if (!gexec || !(gkey == s)) {
-            if (gexec) {
-                cudaGraphExecDestroy(gexec);
-                gexec = nullptr;
-            }
-            cudaGraph_t graph = nullptr;
-            PL_CUDA(cudaStreamBeginCapture(ws, cudaStreamCaptureModeThreadLocal));
-            rc = queue_sweep(s, ws, false);
-            cudaError_t ce = cudaStreamEndCapture(ws, &graph);
-            if (rc) {
-                if (graph) cudaGraphDestroy(graph);
-                return rc;
-            }
-            if (ce != cudaSuccess) return cuda_error(ce, "cudaStreamEndCapture");
-            ce = cudaGraphInstantiate(&gexec, graph, 0);
-            cudaGraphDestroy(graph);
-            if (ce != cudaSuccess) {
-                gexec = nullptr;
-                return cuda_error(ce, "cudaGraphInstantiate");
+        // one captured sweep per start parity; with an odd number of subsets the sweeps
+        // alternate between the two
+        const bool two = (n_sub & 1) && prm.n_iter > 1;
+        if (!gexec || (two && !gexec_odd) || !(gkey == s)) {
+            drop_graphs();
+            for (int par = 0; par < (two ? 2 : 1); ++par) {
+                cudaGraph_t graph = nullptr;
+                PL_CUDA(cudaStreamBeginCapture(ws, cudaStreamCaptureModeThreadLocal));
+                rc = queue_sweep(s, ws, false, par);
+                cudaError_t ce = cudaStreamEndCapture(ws, &graph);
+                if (rc) {
+                    if (graph) cudaGraphDestroy(graph);
+                    return rc;
+                }
+                if (ce != cudaSuccess) return cuda_error(ce, "cudaStreamEndCapture");
+                cudaGraphExec_t ex = nullptr;
+                ce = cudaGraphInstantiate(&ex, graph, 0);
+                cudaGraphDestroy(graph);
+                if (ce != cudaSuccess) return cuda_error(ce, "cudaGraphInstantiate");
+                (par ? gexec_odd : gexec) = ex;
             }
             gkey = s;
         }
-        for (int it = 0; it < prm.n_iter; ++it) PL_CUDA(cudaGraphLaunch(gexec, ws));
+        for (int it = 0; it < prm.n_iter; ++it)
+            PL_CUDA(cudaGraphLaunch(((it * n_sub) & 1) ? gexec_odd : gexec, ws));
     } else {
         for (int it = 0; it < prm.n_iter; ++it)
-            if ((rc = queue_sweep(s, ws, false))) return rc;
+            if ((rc = queue_sweep(s, ws, false, (it * n_sub) & 1))) return rc;
     }
 
     if (kxo == kHost) PL_CUDA(cudaMemcpyAsync(x_out, d_xo, xb * n_vox, cudaMemcpyDeviceToHost, ws));
@@ -269,13 +285,55 @@ int cyl_plan::solve(const void *sino, cyl_dtype sino_t, const void *x0, const fl
             kernel_ms[k] = 0.0;
             kernel_launches[k] = 0;
         }
-        for (size_t base = 0; base + 3 <= ev_used; base += 3)
-            for (int k = 0; k < 2; ++k) {
+        for (size_t base = 0; base + 4 <= ev_used; base += 4)
+            for (int k = 0; k < 3; ++k) {
                 float ms = 0.f;
                 PL_CUDA(cudaEventElapsedTime(&ms, events[base + k], events[base + k + 1]));
                 kernel_ms[k] += ms;
                 kernel_launches[k] += 1;
             }
     }
+    return CYL_OK;
+}
+
+// Autotuner: time the projector and the back-projector of view 0 for 1, 2, 4 and 8
+// pieces per ray and keep the fastest of each (the walk's cost does not depend on the
+// volume's values, so a zero volume and zero data serve).
+int cyl_plan::tune(cudaStream_t st)
+{
+    int rc;
+    if ((rc = ensure((void **)&d_q, q_cap, sizeof(float) * (size_t)n_pix))) return rc;
+    if ((rc = ensure((void **)&d_x32, x32_cap, sizeof(float) * n_vox))) return rc;
+    PL_CUDA(cudaMemsetAsync(d_x32, 0, sizeof(float) * n_vox, st));
+    PL_CUDA(cudaMemsetAsync(d_q, 0, sizeof(float) * n_pix, st));
+    const ScanDev sd = scan_dev();
+    cudaEvent_t e[2];
+    PL_CUDA(cudaEventCreate(&e[0]));
+    PL_CUDA(cudaEventCreate(&e[1]));
+    const int opts[4] = {1, 2, 4, 8};
+    float best_fp = 1e30f, best_bp = 1e30f;
+    for (int P : opts) {
+        for (int kind = 0; kind < 2; ++kind) {
+            float ms_min = 1e30f;
+            for (int rep = 0; rep < 3; ++rep) {
+                PL_CUDA(cudaEventRecord(e[0], st));
+                if (kind == 0)
+                    PL_CUDA(launch_fp_rays(sd, P, 0, 1, d_x32, CYL_F32, d_q, nullptr, 0, st));
+                else
+                    PL_CUDA(launch_bp_rays(sd, P, 0, 1, d_q, CYL_F32, d_q, d_nd[0], nullptr, nullptr, st));
+                PL_CUDA(cudaEventRecord(e[1], st));
+                PL_CUDA(cudaEventSynchronize(e[1]));
+                float ms = 0.f;
+                PL_CUDA(cudaEventElapsedTime(&ms, e[0], e[1]));
+                ms_min = std::min(ms_min, ms);
+            }
+            if (kind == 0 && ms_min < best_fp) { best_fp = ms_min; p_fp = P; }
+            if (kind == 1 && ms_min < best_bp) { best_bp = ms_min; p_bp = P; }
+        }
+    }
+    cudaEventDestroy(e[0]);
+    cudaEventDestroy(e[1]);
+    PL_CUDA(cudaMemsetAsync(d_nd[0], 0, sizeof(float2) * n_vox, st));
+    drop_graphs();
     return CYL_OK;
 }

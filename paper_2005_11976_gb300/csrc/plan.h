@@ -66,6 +66,8 @@ struct cyl_plan {
     float *d_wscale = nullptr;
     float *d_q = nullptr;          // forward projections of one subset (FP32)
     size_t q_cap = 0;
+    float2 *d_nd[2] = {nullptr, nullptr};   // (numerator, column sum) accumulators, per voxel
+    int p_fp = 4, p_bp = 4;        // pieces per ray of the projector / back-projector
     float *d_x32 = nullptr;
     size_t x32_cap = 0;
     void *d_stage[4] = {nullptr, nullptr, nullptr, nullptr};  // sino, x0, w, x_out
@@ -82,7 +84,8 @@ struct cyl_plan {
     std::vector<cudaEvent_t> events;
     size_t ev_used = 0;
 
-    cudaGraphExec_t gexec = nullptr;
+    // captured sweeps, one per parity of the subset counter at the sweep's start
+    cudaGraphExec_t gexec = nullptr, gexec_odd = nullptr;
     cylct::SolveState gkey{};
 
     std::mutex mu;
@@ -119,7 +122,10 @@ struct cyl_plan {
     // Grow-only scratch buffer.
     int ensure(void **p, size_t &cap, size_t nbytes);
     cudaEvent_t *next_events(int n);
-    int queue_sweep(const cylct::SolveState &s, cudaStream_t st, bool timed);
+    // Queue one sweep; `parity` is the subset counter's parity at its first subset.
+    int queue_sweep(const cylct::SolveState &s, cudaStream_t st, bool timed, int parity);
+    void drop_graphs();
+    int tune(cudaStream_t st);
     int solve(const void *sino, cyl_dtype sino_t, const void *x0, const float *w,
               const cyl_sart_params &prm, void *x_out, cyl_dtype x_t, cudaStream_t user);
     ~cyl_plan();

@@ -212,6 +212,9 @@ int cyl_server::admit(const std::shared_ptr<Scan> &s)
     }
     if (cudaMemsetAsync(pl->d_q, 0, 2 * sizeof(float) * subset * pl->n_pix, st) != cudaSuccess)
         return set_error(CYL_EDEVICE, "projection buffers");
+    for (int k = 0; k < 2; ++k)
+        if (cudaMemsetAsync(pl->d_nd[k], 0, sizeof(float2) * pl->n_vox, st) != cudaSuccess)
+            return set_error(CYL_EDEVICE, "back-projection accumulators");
     if (cudaEventCreateWithFlags(&s->done_ev, cudaEventDisableTiming) != cudaSuccess)
         return set_error(CYL_EDEVICE, "event");
     s->n_sub = (n_proj + subset - 1) / subset;
@@ -263,7 +266,8 @@ int cyl_server::run_round()
     std::vector<BatchScan> scans;
     std::vector<BatchItem> items;
     std::vector<std::shared_ptr<Scan>> members;
-    int max_tiles = 0, smem_fp = 0, smem_bp = 0;
+    int max_nt = 0, P = 0;
+    int64_t max_rays = 0, max_vox = 0;
     for (auto &s : active) {
         if (s->state != 1 || s->rounds_done >= s->rounds_total) continue;
         cyl_plan *pl = s->plan;
@@ -278,6 +282,9 @@ int cyl_server::run_round()
         sc.q[0] = pl->d_q;
         sc.q[1] = pl->d_q + (size_t)subset * pl->n_pix;
         sc.q_len = (int64_t)subset * pl->n_pix;
+        sc.nd[0] = pl->d_nd[0];
+        sc.nd[1] = pl->d_nd[1];
+        sc.nd_len = pl->n_vox;
         sc.upd.x32 = cfg.storage == CYL_F32 ? static_cast<float *>(s->d_x) : s->d_x32;
         sc.upd.x16 = cfg.storage == CYL_F32 ? nullptr : s->d_x;
         sc.upd.x16_t = cfg.storage;
@@ -289,9 +296,10 @@ int cyl_server::run_round()
         items.push_back(BatchItem{(int)scans.size(), p0, std::min(subset, s->req.n_proj - p0), r & 1});
         scans.push_back(sc);
         members.push_back(s);
-        max_tiles = std::max(max_tiles, pl->td.n_tiles);
-        smem_fp = std::max(smem_fp, pl->td.smem_fp);
-        smem_bp = std::max(smem_bp, pl->td.smem_bp);
+        max_rays = std::max(max_rays, sc.q_len);
+        max_vox = std::max(max_vox, pl->n_vox);
+        max_nt = std::max(max_nt, pl->g.n_t);
+        if (!P) P = pl->p_fp;
     }
     if (scans.empty()) return CYL_OK;
     const int n = (int)scans.size();
@@ -308,9 +316,9 @@ int cyl_server::run_round()
     if (cudaMemcpyAsync(d, h, slot_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
         return set_error(CYL_EDEVICE, "round descriptors");
     if (cudaEventRecord(slot_ev[slot], st) != cudaSuccess) return set_error(CYL_EDEVICE, "event");
-    cudaError_t e = launch_batch_round(reinterpret_cast<BatchScan *>(d), reinterpret_cast<BatchItem *>(d + b_scans),
-                                       reinterpret_cast<int *>(d + b_scans + b_items), n, 0, max_tiles,
-                                       smem_fp, smem_bp, cfg.storage, cfg.storage, cfg.storage, st);
+    cudaError_t e = launch_batch_round_rays(reinterpret_cast<BatchScan *>(d), reinterpret_cast<BatchItem *>(d + b_scans),
+                                            reinterpret_cast<int *>(d + b_scans + b_items), n, 0, max_rays,
+                                            max_vox, max_nt, P, cfg.storage, cfg.storage, cfg.storage, st);
     if (e != cudaSuccess) return cuda_error(e, "round launch");
     ++stats.rounds;
     for (auto &s : members) {

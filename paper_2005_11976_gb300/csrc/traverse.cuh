@@ -348,7 +348,7 @@ struct Walker {
 //   void end(int64_t j, float acc)              per ray, after its last piece
 // s_chunk: a shared int the caller zeroed (chunk counter of this view), s_map: 32 ints
 // of shared memory per warp.
-template <class K>
+template <class K, class W = Walker>
 __device__ __forceinline__ void tile_walk_all(const GridDev &g, const float2 *__restrict__ trig,
                                               const Tile &t, const float4 *__restrict__ ra,
                                               const float4 *__restrict__ rb,
@@ -362,7 +362,7 @@ __device__ __forceinline__ void tile_walk_all(const GridDev &g, const float2 *__
     const int n_chunks = (nc + 31) >> 5;
     int chunk = 0, pos = 32;                // current chunk of 32 candidates, next offset
     bool active = false, more = true;
-    Walker w;
+    W w;
     int64_t j = 0;
     float acc = 0.f;
     auto piece = [&](int idx, float len) { k.piece(idx, len, acc); };

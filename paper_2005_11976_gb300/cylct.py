@@ -120,6 +120,8 @@ SIGNATURES = {
     "cyl_wait": (ctypes.c_int, [_VP, ctypes.c_uint64, _I64, ctypes.POINTER(cyl_result)]),
     "cyl_server_get_stats": (ctypes.c_int, [_VP, ctypes.POINTER(cyl_server_stats)]),
     "cyl_server_destroy": (ctypes.c_int, [_VP]),
+    "cyl_plan_tune": (ctypes.c_int, [_VP, _VP]),
+    "cyl_plan_get_pieces": (ctypes.c_int, [_VP, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     "cyl_plan_set_timing": (ctypes.c_int, [_VP, ctypes.c_int]),
     "cyl_plan_kernel_time": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                             ctypes.POINTER(_I64)]),
@@ -270,6 +272,14 @@ class Plan:
     def cyl_count_segments(self, p0, np_, counts_out, stream=None):
         _check(load().cyl_count_segments(self.h, p0, np_, ptr(counts_out), stream_ptr(stream)),
                "cyl_count_segments")
+
+    def cyl_plan_tune(self, stream=None):
+        _check(load().cyl_plan_tune(self.h, stream_ptr(stream)), "cyl_plan_tune")
+
+    def cyl_plan_get_pieces(self):
+        a, b = _I32(), _I32()
+        _check(load().cyl_plan_get_pieces(self.h, ctypes.byref(a), ctypes.byref(b)), "cyl_plan_get_pieces")
+        return a.value, b.value
 
     def cyl_plan_set_timing(self, enable: bool):
         _check(load().cyl_plan_set_timing(self.h, int(enable)), "cyl_plan_set_timing")
