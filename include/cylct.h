@@ -27,7 +27,10 @@
  * owns plans, their geometry tables and scratch, and servers.
  *
  * Streams: `stream` is a cudaStream_t passed as void*; NULL means the legacy default
- * stream.  Calls are asynchronous on that stream unless stated otherwise.
+ * stream.  Calls are asynchronous on that stream unless stated otherwise.  A plan's
+ * kernels run on the plan's own work stream, ordered after the work queued on `stream`
+ * before the call and before the work queued on it after the call, so the calls of one
+ * plan never overlap on the GPU whatever streams they are given.
  *
  * Errors: every int-returning call returns CYL_OK (0) or a negative CYL_E* code; no call
  * throws, prints, or aborts the process.  Arguments are validated on the host before any
@@ -56,8 +59,10 @@ extern "C" {
 typedef enum { CYL_F32 = 0, CYL_F16 = 1, CYL_BF16 = 2 } cyl_dtype;
 
 /* Cylindrical grid about the part's axis (Sec. 2, Eq. 2). */
+#define CYL_MAX_N_THETA 6144     /* the wedge (cos, sin) table is staged in 48 KB of shared memory */
 typedef struct cyl_grid {
-    int32_t n_h, n_theta, n_r;   /* slabs, wedges, shells; each >= 1 */
+    int32_t n_h, n_theta, n_r;   /* slabs, wedges, shells; each >= 1; n_h <= 65535,
+                                    n_theta <= CYL_MAX_N_THETA, n_r <= 65534 */
     double radius_mm, height_mm; /* grid cylinder: r <= radius, |h| <= height / 2 */
 } cyl_grid;
 
@@ -141,8 +146,9 @@ int cyl_project(cyl_plan *plan, const void *vol, cyl_dtype vol_dtype, int32_t p0
  * makes no allocation at all.  np * H * W above CYL_NOALLOC_MAX_ELEMS gives CYL_EINVAL.
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
  * with that device current; make that first call before any stream capture.  Every call
- * shares the one array (it is cleared at the start of each call): calls that overlap on
- * the GPU, from any stream or thread, race and corrupt each other's results. */
+ * shares the one array (each call overwrites it): calls of different plans that overlap
+ * on the GPU, from any stream or thread, race and corrupt each other's results (calls of
+ * one plan run in order on the plan's own work stream). */
 #define CYL_NOALLOC_MAX_ELEMS (4 * 1024 * 1024)
 int cyl_project_noalloc(cyl_plan *plan, const void *vol, cyl_dtype vol_dtype, int32_t p0,
                         int32_t np, void *sino_out, cyl_dtype sino_dtype, void *stream);
@@ -169,15 +175,18 @@ int cyl_sart_solve(cyl_plan *plan, const void *sino, cyl_dtype sino_dtype, const
                    const float *w, const cyl_sart_params *params, void *x_out,
                    cyl_dtype x_dtype, void *stream);
 
-/* Batched SART: n scans (each its own plan: own pose, projection count and geometry,
- * all on one device) reconstructed together, each exactly as cyl_sart_solve would with
- * the same params.  A round advances every unfinished scan by one subset; each round is
- * a tiled forward projection and a tiled back-projection with the fused Eq. 6 update over
- * (tile, scan) blocks, and all rounds are queued as one CUDA graph (params->use_graph).
+/* Batched SART: n scans (0 <= n <= CYL_MAX_BATCH; each its own plan: own pose,
+ * projection count and geometry, all on one device) reconstructed together, each exactly
+ * as cyl_sart_solve would with the same params.  A round advances every unfinished scan
+ * by one subset: one forward projection and one back-projection launch take the ray
+ * pieces of all the round's scans from a shared work counter, then the Eq. 6 update runs
+ * per scan; all rounds are queued as one CUDA graph (params->use_graph).  The plans'
+ * piece settings are those of plans[0].
  * Arrays (per scan i, in plan i's layout): sinos[i] of sino_dtype, x0s[i] (x0s or its
  * entries NULL = zeros), ws[i] FP32 weights (ws or its entries NULL = none), x_outs[i] of
  * x_dtype.  All DEVICE pointers on the plans' device; host arrays give CYL_EINVAL.
  * Asynchronous on `stream`.  Errors: CYL_EINVAL, CYL_ENOMEM, CYL_EDEVICE. */
+#define CYL_MAX_BATCH 4096
 int cyl_sart_solve_batch(int32_t n, cyl_plan *const *plans, const void *const *sinos,
                          cyl_dtype sino_dtype, const void *const *x0s, const float *const *ws,
                          const cyl_sart_params *params, void *const *x_outs, cyl_dtype x_dtype,
@@ -278,10 +287,16 @@ int cyl_count_segments(cyl_plan *plan, int32_t p0, int32_t np, int64_t *counts_o
 int cyl_plan_set_timing(cyl_plan *plan, int enable);
 int cyl_plan_kernel_time(cyl_plan *plan, int kind, double *ms_total, int64_t *launches);
 
-/* Autotuner: times the projector and the back-projector of view 0 with each ray cut
- * into 1, 2, 4 or 8 pieces (one thread per piece) and keeps the fastest setting of each
- * for this plan.  Synchronises `stream`.  cyl_plan_get_pieces reports the settings. */
+/* Work split of the projector and the back-projector: at set-up (plan creation and
+ * cyl_plan_set_pose) each ray is walked once and cut into 16 pieces holding equal numbers
+ * of steps; a launch runs P pieces per ray (P in 1, 2, 4, 8, 16; each piece one thread),
+ * merging adjacent pieces for P < 16.  Defaults: 8 for the projector, 4 for the
+ * back-projector.
+ * cyl_plan_tune times one view (view 0) with each P and keeps the fastest for this plan;
+ * synchronises `stream`.  cyl_plan_set_pieces fixes P (0 restores the default);
+ * cyl_plan_get_pieces reports the P in use. */
 int cyl_plan_tune(cyl_plan *plan, void *stream);
+int cyl_plan_set_pieces(cyl_plan *plan, int32_t fp_pieces, int32_t bp_pieces);
 int cyl_plan_get_pieces(const cyl_plan *plan, int32_t *fp_pieces, int32_t *bp_pieces);
 
 /* Sizes of a plan: voxels, rays per projection, projections, and the device bytes the

@@ -175,6 +175,25 @@ extern "C" int cyl_row_sums(cyl_plan *plan, int32_t p0, int32_t np, float *L_out
     return e == cudaSuccess ? CYL_OK : cuda_error(e, "row sums");
 }
 
+// Plan kernels run on the plan's work stream, ordered after the caller's stream and
+// before its later work: the plan's scratch and work counters serve one launch at a time.
+namespace {
+struct OnPlanStream {
+    cyl_plan *pl;
+    cudaStream_t user;
+    cudaError_t begin()
+    {
+        cudaError_t e = cudaEventRecord(pl->ev_in, user);
+        return e == cudaSuccess ? cudaStreamWaitEvent(pl->ws, pl->ev_in, 0) : e;
+    }
+    cudaError_t end()
+    {
+        cudaError_t e = cudaEventRecord(pl->ev_out, pl->ws);
+        return e == cudaSuccess ? cudaStreamWaitEvent(user, pl->ev_out, 0) : e;
+    }
+};
+}  // namespace
+
 extern "C" int cyl_project(cyl_plan *plan, const void *vol, cyl_dtype vol_dtype, int32_t p0,
                            int32_t np, void *sino_out, cyl_dtype sino_dtype, void *stream)
 {
@@ -185,16 +204,18 @@ extern "C" int cyl_project(cyl_plan *plan, const void *vol, cyl_dtype vol_dtype,
     if (!vol || !sino_out) return set_error(CYL_EINVAL, "null array");
     DeviceGuard dg(plan->device);
     std::lock_guard<std::mutex> lock(plan->mu);
-    cudaStream_t st = (cudaStream_t)stream;
     const size_t n = (size_t)np * plan->n_pix;
     float *q = static_cast<float *>(sino_out);
     if (sino_dtype != CYL_F32) {
         if ((rc = plan->ensure((void **)&plan->d_q, plan->q_cap, sizeof(float) * n))) return rc;
         q = plan->d_q;
     }
-    CYL_CUDA(cudaMemsetAsync(q, 0, sizeof(float) * n, st));
-    CYL_CUDA(launch_fp_rays(plan->scan_dev(), plan->p_fp, p0, np, vol, vol_dtype, q, nullptr, 0, st));
-    if (sino_dtype != CYL_F32) CYL_CUDA(launch_convert(q, CYL_F32, sino_out, sino_dtype, (int64_t)n, st));
+    OnPlanStream ps{plan, (cudaStream_t)stream};
+    CYL_CUDA(ps.begin());
+    CYL_CUDA(launch_fp_rays(plan->scan_dev(), plan->p_fp, p0, np, vol, vol_dtype, q, nullptr, 0, plan->ws));
+    if (sino_dtype != CYL_F32)
+        CYL_CUDA(launch_convert(q, CYL_F32, sino_out, sino_dtype, (int64_t)n, plan->ws));
+    CYL_CUDA(ps.end());
     return CYL_OK;
 }
 
@@ -206,11 +227,14 @@ extern "C" int cyl_backproject(cyl_plan *plan, const void *sino, cyl_dtype sino_
     if (!valid_dtype(sino_dtype)) return set_error(CYL_EINVAL, "bad dtype");
     if (!vol_out || (np > 0 && !sino)) return set_error(CYL_EINVAL, "null array");
     DeviceGuard dg(plan->device);
-    cudaStream_t st = (cudaStream_t)stream;
-    CYL_CUDA(cudaMemsetAsync(vol_out, 0, sizeof(float) * plan->n_vox, st));
-    if (colsum_out) CYL_CUDA(cudaMemsetAsync(colsum_out, 0, sizeof(float) * plan->n_vox, st));
+    std::lock_guard<std::mutex> lock(plan->mu);
+    OnPlanStream ps{plan, (cudaStream_t)stream};
+    CYL_CUDA(ps.begin());
+    CYL_CUDA(cudaMemsetAsync(vol_out, 0, sizeof(float) * plan->n_vox, plan->ws));
+    if (colsum_out) CYL_CUDA(cudaMemsetAsync(colsum_out, 0, sizeof(float) * plan->n_vox, plan->ws));
     CYL_CUDA(launch_bp_rays(plan->scan_dev(), plan->p_bp, p0, np, sino, sino_dtype, nullptr, nullptr,
-                            vol_out, colsum_out, st));
+                            vol_out, colsum_out, plan->ws));
+    CYL_CUDA(ps.end());
     return CYL_OK;
 }
 
@@ -222,9 +246,13 @@ extern "C" int cyl_count_segments(cyl_plan *plan, int32_t p0, int32_t np, int64_
     if (np == 0) return CYL_OK;
     if (!counts_out) return set_error(CYL_EINVAL, "counts_out is null");
     DeviceGuard dg(plan->device);
-    cudaStream_t st = (cudaStream_t)stream;
-    CYL_CUDA(cudaMemsetAsync(counts_out, 0, sizeof(int64_t) * np, st));
-    CYL_CUDA(launch_count_rays(plan->scan_dev(), p0, np, reinterpret_cast<unsigned long long *>(counts_out), st));
+    std::lock_guard<std::mutex> lock(plan->mu);
+    OnPlanStream ps{plan, (cudaStream_t)stream};
+    CYL_CUDA(ps.begin());
+    CYL_CUDA(cudaMemsetAsync(counts_out, 0, sizeof(int64_t) * np, plan->ws));
+    CYL_CUDA(launch_count_rays(plan->scan_dev(), p0, np, reinterpret_cast<unsigned long long *>(counts_out),
+                               plan->ws));
+    CYL_CUDA(ps.end());
     return CYL_OK;
 }
 
@@ -246,8 +274,20 @@ extern "C" int cyl_plan_tune(cyl_plan *plan, void *stream)
 extern "C" int cyl_plan_get_pieces(const cyl_plan *plan, int32_t *fp, int32_t *bp)
 {
     if (!plan) return set_error(CYL_EINVAL, "plan is null");
-    if (fp) *fp = plan->p_fp;
-    if (bp) *bp = plan->p_bp;
+    if (fp) *fp = plan->p_fp > 0 ? plan->p_fp : default_pieces(0);
+    if (bp) *bp = plan->p_bp > 0 ? plan->p_bp : default_pieces(1);
+    return CYL_OK;
+}
+
+extern "C" int cyl_plan_set_pieces(cyl_plan *plan, int32_t fp, int32_t bp)
+{
+    if (!plan) return set_error(CYL_EINVAL, "plan is null");
+    if ((fp != 0 && !valid_pieces(fp)) || (bp != 0 && !valid_pieces(bp)))
+        return set_error(CYL_EINVAL, "pieces must be 0, 1, 2, 4, 8 or 16");
+    std::lock_guard<std::mutex> lock(plan->mu);
+    plan->p_fp = fp;
+    plan->p_bp = bp;
+    plan->drop_graphs();
     return CYL_OK;
 }
 

@@ -2,10 +2,10 @@
 //
 // Every scan runs exactly the subsets of its own cyl_sart_solve (Eq. 6, n_iter sweeps in
 // index order); a round advances each unfinished scan by one subset.  A round is three
-// kernels over (ray piece, scan) blocks: the forward projection of the scans' current
-// subsets, the back-projection into each scan's (numerator, denominator) accumulator, and
-// the voxel update.  The rounds are queued once into a CUDA graph and launched as a
-// single graph.
+// kernels: the forward projection of the scans' current subsets and the back-projection
+// into each scan's (numerator, column sum) accumulator, both persistent grids that take
+// ray pieces of all the round's scans from one work counter, and the voxel update.  The
+// rounds are queued once into a CUDA graph and launched as a single graph.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -75,6 +75,7 @@ extern "C" int cyl_sart_solve_batch(int32_t n, cyl_plan *const *plans, const voi
 {
     if (n < 0 || (n > 0 && (!plans || !sinos || !x_outs)) || !prm)
         return set_error(CYL_EINVAL, "bad batch arguments");
+    if (n > CYL_MAX_BATCH) return set_error(CYL_EINVAL, "more than CYL_MAX_BATCH scans");
     if (n == 0) return CYL_OK;
     if (sino_dtype < CYL_F32 || sino_dtype > CYL_BF16 || x_dtype < CYL_F32 || x_dtype > CYL_BF16)
         return set_error(CYL_EINVAL, "bad dtype");
@@ -117,8 +118,8 @@ extern "C" int cyl_sart_solve_batch(int32_t n, cyl_plan *const *plans, const voi
     }
 
     const size_t xb = dtype_size(x_dtype);
-    int max_nt = 0, rc;
-    int64_t max_rays = 0, max_vox = 0;
+    int rc;
+    int64_t max_vox = 0;
     const int P = plans[0]->p_fp;
     std::vector<BatchScan> scans(n);
     std::vector<int> n_proj(n);
@@ -127,7 +128,6 @@ extern "C" int cyl_sart_solve_batch(int32_t n, cyl_plan *const *plans, const voi
         const int subset = std::min(prm->subset_size, pl->geom.n_proj);
         const size_t qlen = (size_t)subset * pl->n_pix;
         if ((rc = pl->ensure((void **)&pl->d_q, pl->q_cap, 2 * sizeof(float) * qlen))) return rc;
-        BT_CUDA(cudaMemsetAsync(pl->d_q, 0, 2 * sizeof(float) * qlen, bs));
         for (int k = 0; k < 2; ++k) BT_CUDA(cudaMemsetAsync(pl->d_nd[k], 0, sizeof(float2) * pl->n_vox, bs));
         const void *x0 = x0s ? x0s[i] : nullptr;
         const float *w = ws ? ws[i] : nullptr;
@@ -144,9 +144,7 @@ extern "C" int cyl_sart_solve_batch(int32_t n, cyl_plan *const *plans, const voi
         sc.nd[0] = pl->d_nd[0];
         sc.nd[1] = pl->d_nd[1];
         sc.nd_len = pl->n_vox;
-        max_rays = std::max(max_rays, (int64_t)qlen);
         max_vox = std::max(max_vox, pl->n_vox);
-        max_nt = std::max(max_nt, pl->g.n_t);
         UpdateArgs &u = sc.upd;
         u.x32 = nullptr;
         u.x16 = nullptr;
@@ -179,11 +177,14 @@ extern "C" int cyl_sart_solve_batch(int32_t n, cyl_plan *const *plans, const voi
         void *d_blob = nullptr;
         const size_t b_scans = sizeof(BatchScan) * n, b_items = sizeof(BatchItem) * items.size(),
                      b_n = sizeof(int) * n_items.size();
-        BT_CUDA(cudaMallocAsync(&d_blob, b_scans + b_items + b_n + 64, bs));
+        const size_t b_sched = sizeof(int) * kSched;
+        BT_CUDA(cudaMallocAsync(&d_blob, b_sched + b_scans + b_items + b_n + 64, bs));
         char *base = static_cast<char *>(d_blob);
-        BatchScan *d_scans = reinterpret_cast<BatchScan *>(base);
-        BatchItem *d_items = reinterpret_cast<BatchItem *>(base + ((b_scans + 15) & ~size_t(15)));
+        int *d_sched = reinterpret_cast<int *>(base);
+        BatchScan *d_scans = reinterpret_cast<BatchScan *>(base + ((b_sched + 15) & ~size_t(15)));
+        BatchItem *d_items = reinterpret_cast<BatchItem *>(reinterpret_cast<char *>(d_scans) + ((b_scans + 15) & ~size_t(15)));
         int *d_n = reinterpret_cast<int *>(reinterpret_cast<char *>(d_items) + ((b_items + 15) & ~size_t(15)));
+        BT_CUDA(cudaMemsetAsync(d_sched, 0, b_sched, bs));
         BT_CUDA(cudaMemcpyAsync(d_scans, scans.data(), b_scans, cudaMemcpyHostToDevice, bs));
         BT_CUDA(cudaMemcpyAsync(d_items, items.data(), b_items, cudaMemcpyHostToDevice, bs));
         BT_CUDA(cudaMemcpyAsync(d_n, n_items.data(), b_n, cudaMemcpyHostToDevice, bs));
@@ -194,8 +195,8 @@ extern "C" int cyl_sart_solve_batch(int32_t n, cyl_plan *const *plans, const voi
             BT_CUDA(cudaStreamBeginCapture(bs, cudaStreamCaptureModeThreadLocal));
             cudaError_t ce = cudaSuccess;
             for (int r = 0; r < rounds && ce == cudaSuccess; ++r)
-                ce = launch_batch_round_rays(d_scans, d_items, d_n, n, r, max_rays, max_vox, max_nt,
-                                             P, x_dtype, sino_dtype, x16t, bs);
+                ce = launch_batch_round(d_scans, d_items, d_n, n, r, max_vox, P, d_sched, x_dtype,
+                                        sino_dtype, x16t, bs);
             cudaError_t ee = cudaStreamEndCapture(bs, &graph);
             if (ce != cudaSuccess) {
                 if (graph) cudaGraphDestroy(graph);
@@ -210,8 +211,8 @@ extern "C" int cyl_sart_solve_batch(int32_t n, cyl_plan *const *plans, const voi
             if (ce != cudaSuccess) return cuda_error(ce, "cudaGraphLaunch");
         } else {
             for (int r = 0; r < rounds; ++r)
-                BT_CUDA(launch_batch_round_rays(d_scans, d_items, d_n, n, r, max_rays, max_vox, max_nt,
-                                                P, x_dtype, sino_dtype, x16t, bs));
+                BT_CUDA(launch_batch_round(d_scans, d_items, d_n, n, r, max_vox, P, d_sched, x_dtype,
+                                           sino_dtype, x16t, bs));
         }
         BT_CUDA(cudaFreeAsync(d_blob, bs));
     }

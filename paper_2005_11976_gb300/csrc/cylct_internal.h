@@ -32,28 +32,23 @@ struct GridDev {
     float dh, inv_dh, h0;   // slab spacing, first slab plane (-H/2)
 };
 
-// Volume tiling of the projector / back-projector: tt wedges x th slabs x all shells
-// per tile (ragged last tiles), n_tt x n_th tiles, tile index = slab_tile * n_tt +
-// wedge_tile.  One tile's voxels are staged in shared memory.
-struct TileDev {
-    int tt, th, n_tt, n_th, n_tiles;
-    int smem_fp, smem_bp;   // dynamic shared memory bytes of the two kernels
-};
-
 // Device tables of one scan.
 struct ScanDev {
     GridDev g;
-    TileDev td;
     const float2 *trig;     // (cos, sin) of theta_k, k < N_theta
     const float4 *ray_a;    // ray records [view][pixel], see RayRec
     const float4 *ray_b;
     const float4 *ray_c;
-    const int4 *bbox;       // candidate pixel box [view][tile]: u0, v0, u1, v1 (inclusive)
+    const uint16_t *split;  // [view][pixel][kSplit]: cuts of each ray into kSplit pieces
+                            // of equal step counts, as fractions of its chord / 65535
+    int *sched;             // two self-resetting work counters per kernel kind (kSched)
 };
 
-constexpr int kTileThreads = 256;
+constexpr int kSplit = 16;  // pieces per ray recorded at set-up (P divides it)
+constexpr int kPiecesFp = 8, kPiecesBp = 4;   // default pieces per ray of each kernel
+constexpr int kSched = 8;   // ints of scheduler state per plan
 
-// SART update of one subset, fused into the back-projection epilogue.
+// SART update of one subset (Eq. 6): x += scale * w * num / den where den > 0.
 struct UpdateArgs {
     float *x32;             // FP32 iterate (null in strict 16-bit mode)
     void *x16;              // 16-bit copy / iterate (null in FP32 mode)
@@ -77,47 +72,40 @@ struct BatchScan {
     int64_t nd_len;
 };
 
-// One unit of work of a round: subset [p0, p0 + np) of scan `scan`, accumulating into
-// that scan's projection buffer q[buf].
+// One unit of work of a round: subset [p0, p0 + np) of scan `scan`, projecting into
+// that scan's projection buffer q[buf] and back-projecting into nd[buf].
 struct BatchItem {
     int scan, p0, np, buf;
 };
 
-// Kernel launchers (kernels.cu).  All return cudaError_t of the launch.
-cudaError_t launch_batch_round(const BatchScan *scans, const BatchItem *items, const int *n_items,
-                               int max_items, int round, int max_tiles, int smem_fp, int smem_bp,
-                               cyl_dtype xt, cyl_dtype st_, cyl_dtype x16t, cudaStream_t st);
+// Kernel launchers.  All return cudaError_t of the launch.
+// kernels.cu: ray records, row sums, elementwise kernels.
 cudaError_t launch_rays(const GridDev &g, const ProjGeom *geo, int n_proj, float4 *ra,
                         float4 *rb, float4 *rc, cudaStream_t st);
-// q[v][pix] += sum over tiles of the tile's part of A x, views p0 .. p0+np-1 (q must be
-// zeroed by the caller).
-cudaError_t launch_fp_tiles(const ScanDev &sd, int p0, int np, const void *vol, cyl_dtype vt,
-                            float *q, cudaStream_t st);
-// SART mode (upd != null): residual (p - q) / L of the subset's rays back-projected into
-// shared memory per tile, then the fused update of x.  Pure mode (upd == null): A^T y
-// written to num_out and A^T 1 to den_out (if not null) for every voxel.
-cudaError_t launch_bp_tiles(const ScanDev &sd, int p0, int np, const void *sino, cyl_dtype sdt,
-                            const float *q, const UpdateArgs *upd, float *num_out,
-                            float *den_out, cudaStream_t st);
 cudaError_t launch_row_sums(const ScanDev &sd, int p0, int np, float *L, cudaStream_t st);
-cudaError_t launch_count(const ScanDev &sd, int p0, int np, unsigned long long *counts,
-                         cudaStream_t st);
-cudaError_t set_kernel_attributes();
 
-// Ray-piece kernels (rays.cu).  P = pieces per ray (1, 2, 4 or 8).
+// Ray-piece kernels (rays.cu).  P = pieces per ray: 1, 2, 4, 8 or 16 (a divisor of
+// kSplit); P <= 0 means the kernel's default (kPiecesFp, kPiecesBp).
+int valid_pieces(int P);
+int default_pieces(int kind /* 0 forward, 1 back */);
+// Cut every ray of all views into kSplit pieces of equal step counts (once per pose).
+cudaError_t launch_split(const ScanDev &sd, int n_proj, uint16_t *split, cudaStream_t st);
+// q[v][pix] = (A x)_j for views p0 .. p0+np-1 (overwritten); zero_buf (if not null) is
+// cleared on the way.
 cudaError_t launch_fp_rays(const ScanDev &sd, int P, int p0, int np, const void *x, cyl_dtype xt,
                            float *q, float2 *zero_buf, int64_t zero_len, cudaStream_t st);
 // q != null: SART residual (y - q) / L into nd; q == null: pure A^T y into nd, or into
-// num / den (den may be null) when nd is null.
+// num / den (den may be null) when nd is null.  The outputs accumulate.
 cudaError_t launch_bp_rays(const ScanDev &sd, int P, int p0, int np, const void *y, cyl_dtype yt,
                            const float *q, float2 *nd, float *num, float *den, cudaStream_t st);
 cudaError_t launch_update_nd(int64_t n_vox, const float2 *nd, const UpdateArgs &u, cudaStream_t st);
 cudaError_t launch_count_rays(const ScanDev &sd, int p0, int np, unsigned long long *counts,
                               cudaStream_t st);
-cudaError_t launch_batch_round_rays(const BatchScan *scans, const BatchItem *items, const int *n_items,
-                                    int max_items, int round, int64_t max_rays, int64_t max_vox,
-                                    int max_nt, int P, cyl_dtype xt, cyl_dtype yt, cyl_dtype x16t,
-                                    cudaStream_t st);
+// One round of a batched solve: forward projection, back-projection and update of every
+// item of the round.  sched: the batch's scheduler state (kSched ints, zero at rest).
+cudaError_t launch_batch_round(const BatchScan *scans, const BatchItem *items, const int *n_items,
+                               int max_items, int round, int64_t max_vox, int P, int *sched,
+                               cyl_dtype xt, cyl_dtype yt, cyl_dtype x16t, cudaStream_t st);
 cudaError_t launch_log(const void *in, cyl_dtype it, double i0, void *out, cyl_dtype ot,
                        int64_t n, cudaStream_t st);
 cudaError_t launch_convert(const void *in, cyl_dtype it, void *out, cyl_dtype ot,

@@ -31,6 +31,10 @@ int validate_scan(const cyl_grid *grid, const cyl_geom *geom, const cyl_pose *po
     if (!grid || !geom || !pose) return set_error(CYL_EINVAL, "null grid, geometry or pose");
     if (grid->n_h < 1 || grid->n_theta < 1 || grid->n_r < 1)
         return set_error(CYL_EINVAL, "grid divisions must be >= 1");
+    if (grid->n_r > 65534 || grid->n_h > 65535)
+        return set_error(CYL_EINVAL, "n_r must be <= 65534 and n_h <= 65535");
+    if (grid->n_theta > CYL_MAX_N_THETA)
+        return set_error(CYL_EINVAL, "n_theta must be <= 6144 (wedge table in shared memory)");
     if ((int64_t)grid->n_h * grid->n_theta * grid->n_r >= (int64_t)1 << 31)
         return set_error(CYL_EINVAL, "grid must have fewer than 2^31 voxels");
     if (!(grid->radius_mm > 0.0) || !(grid->height_mm > 0.0) || !std::isfinite(grid->radius_mm) ||
@@ -61,39 +65,6 @@ int validate_scan(const cyl_grid *grid, const cyl_geom *geom, const cyl_pose *po
     return CYL_OK;
 }
 
-// Tiles: tt wedges (all of them when N_theta <= 16, else at most a quarter turn) x th
-// slabs, sized so that the back-projection's two FP32 accumulators of a tile take about
-// 96 KB of shared memory (two CTAs per SM).  CYL_TILE="tt,th" overrides the shape.
-int choose_tiles(const cyl_grid &grid, int max_smem, TileDev &td)
-{
-    const int n_t = grid.n_theta, n_r = grid.n_r, n_h = grid.n_h;
-    const int trig = (int)sizeof(float2) * ((n_t + 1) & ~1);
-    int tt = n_t <= 16 ? n_t : std::min(16, n_t / 4);
-    int budget = 96 * 1024;
-    int th = 0;
-    if (const char *env = getenv("CYL_TILE")) {
-        int a = 0, b = 0;
-        if (sscanf(env, "%d,%d", &a, &b) == 2 && a >= 1 && b >= 1) {
-            if (n_t > 16 && a <= n_t / 4) tt = a;
-            th = std::min(b, n_h);
-        }
-    }
-    while (tt > 1 && trig + 8LL * tt * n_r > max_smem && n_t > 16) tt /= 2;
-    if (trig + 8LL * tt * n_r > max_smem)
-        return set_error(CYL_EINVAL, "grid too fine in r / theta for one tile in shared memory");
-    if (th == 0) th = (int)std::max<int64_t>(1, (budget - trig) / (8LL * tt * n_r));
-    th = std::min(th, n_h);
-    while (th > 1 && trig + 8LL * tt * th * n_r > max_smem) --th;
-    td.tt = tt;
-    td.th = th;
-    td.n_tt = (n_t + tt - 1) / tt;
-    td.n_th = (n_h + th - 1) / th;
-    td.n_tiles = td.n_tt * td.n_th;
-    td.smem_fp = trig + 4 * tt * th * n_r;
-    td.smem_bp = trig + 8 * tt * th * n_r;
-    return CYL_OK;
-}
-
 void build_grid(const cyl_grid &grid, const cyl_geom &geom, GridDev &g, std::vector<float2> &trig)
 {
     trig.resize(grid.n_theta);
@@ -119,19 +90,16 @@ void build_grid(const cyl_grid &grid, const cyl_geom &geom, GridDev &g, std::vec
     g.h0 = (float)(-0.5 * grid.height_mm);
 }
 
-void build_views(const cyl_grid &grid, const cyl_geom &geom, const cyl_pose &pose,
-                 const TileDev &td, std::vector<ProjGeom> &geo, std::vector<int4> &bbox)
+void build_views(const cyl_geom &geom, const cyl_pose &pose, std::vector<ProjGeom> &geo)
 {
     double R[3][3];
     alignment_matrix(pose, R);
     const double T[3] = {pose.tx, pose.ty, pose.tz};
     const int W = geom.det_w, H = geom.det_h;
     geo.resize(geom.n_proj);
-    bbox.resize((size_t)geom.n_proj * td.n_tiles);
     const double xd = geom.sdd_mm - geom.sod_mm;
     const double u0 = -0.5 * (W - 1) * geom.pitch_u_mm + geom.off_u_mm;
     const double v0 = -0.5 * (H - 1) * geom.pitch_v_mm + geom.off_v_mm;
-    const double dth = 2.0 * M_PI / grid.n_theta, dh = grid.height_mm / grid.n_h;
     for (int p = 0; p < geom.n_proj; ++p) {
         const double c = cos(geom.angles_rad[p]), s = sin(geom.angles_rad[p]);
         // lab -> stage: Rz(-phi); then X' = R (X - T)
@@ -149,62 +117,6 @@ void build_views(const cyl_grid &grid, const cyl_geom &geom, const cyl_pose &pos
         to_obj(d00, true, geo[p].D0);
         to_obj(du, false, geo[p].du);
         to_obj(dv, false, geo[p].dv);
-
-        // object point -> fractional detector pixel (iu, iv); false if not in front
-        auto to_pixel = [&](const double o[3], double &fu, double &fv) -> bool {
-            double st[3];
-            for (int i = 0; i < 3; ++i) st[i] = R[0][i] * o[0] + R[1][i] * o[1] + R[2][i] * o[2] + T[i];
-            const double lx = c * st[0] - s * st[1], ly = s * st[0] + c * st[1], lz = st[2];
-            const double den = lx + geom.sod_mm;
-            if (!(den > 1e-9 * geom.sod_mm)) return false;
-            fu = (geom.sdd_mm * ly / den - geom.off_u_mm) / geom.pitch_u_mm + 0.5 * (W - 1);
-            fv = (geom.sdd_mm * lz / den - geom.off_v_mm) / geom.pitch_v_mm + 0.5 * (H - 1);
-            return true;
-        };
-        for (int tile = 0; tile < td.n_tiles; ++tile) {
-            const int tt = tile % td.n_tt, ht = tile / td.n_tt;
-            const int t0 = tt * td.tt, t1 = std::min(t0 + td.tt, grid.n_theta);
-            const int s0 = ht * td.th, s1 = std::min(s0 + td.th, grid.n_h);
-            const double h_lo = -0.5 * grid.height_mm + s0 * dh, h_hi = -0.5 * grid.height_mm + s1 * dh;
-            // convex hull of the tile in the x'y' plane
-            double px[4], py[4];
-            int npt;
-            if (td.n_tt == 1) {
-                const double r = grid.radius_mm * (1.0 + 1e-9);
-                const double sq[4][2] = {{-r, -r}, {r, -r}, {r, r}, {-r, r}};
-                for (int k = 0; k < 4; ++k) { px[k] = sq[k][0]; py[k] = sq[k][1]; }
-                npt = 4;
-            } else {
-                const double ta = t0 * dth, tb = t1 * dth;
-                const double rc = grid.radius_mm / cos(0.5 * (tb - ta)) * (1.0 + 1e-9);
-                px[0] = 0.0; py[0] = 0.0;
-                px[1] = rc * cos(ta); py[1] = rc * sin(ta);
-                px[2] = rc * cos(tb); py[2] = rc * sin(tb);
-                npt = 3;
-            }
-            double umin = 1e300, umax = -1e300, vmin = 1e300, vmax = -1e300;
-            bool whole = false;
-            for (int k = 0; k < npt && !whole; ++k)
-                for (int e = 0; e < 2; ++e) {
-                    const double o[3] = {px[k], py[k], e ? h_hi : h_lo};
-                    double fu, fv;
-                    if (!to_pixel(o, fu, fv)) { whole = true; break; }
-                    umin = std::min(umin, fu); umax = std::max(umax, fu);
-                    vmin = std::min(vmin, fv); vmax = std::max(vmax, fv);
-                }
-            int4 b;
-            if (whole) {
-                b = make_int4(0, 0, W - 1, H - 1);
-            } else {
-                const double lo_u = std::max(std::floor(umin) - 1.0, 0.0);
-                const double hi_u = std::min(std::ceil(umax) + 1.0, (double)(W - 1));
-                const double lo_v = std::max(std::floor(vmin) - 1.0, 0.0);
-                const double hi_v = std::min(std::ceil(vmax) + 1.0, (double)(H - 1));
-                if (lo_u > hi_u || lo_v > hi_v) b = make_int4(1, 1, 0, 0);
-                else b = make_int4((int)lo_u, (int)lo_v, (int)hi_u, (int)hi_v);
-            }
-            bbox[(size_t)p * td.n_tiles + tile] = b;
-        }
     }
 }
 

@@ -65,9 +65,14 @@ extern "C" int cyl_project_noalloc(cyl_plan *plan, const void *vol, cyl_dtype vo
     float *acc = nullptr;
     int rc = acc_address(plan->device, &acc);
     if (rc) return rc;
-    cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(float) * (size_t)n, st);
+    // the plan's kernels run on its work stream, ordered after the caller's stream
+    std::lock_guard<std::mutex> lock(plan->mu);
+    cudaStream_t user = (cudaStream_t)stream, st = plan->ws;
+    cudaError_t e = cudaEventRecord(plan->ev_in, user);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, plan->ev_in, 0);
     if (e == cudaSuccess) e = launch_fp_rays(plan->scan_dev(), plan->p_fp, p0, np, vol, vol_dtype, acc, nullptr, 0, st);
     if (e == cudaSuccess) e = launch_convert(acc, CYL_F32, sino_out, sino_dtype, n, st);
+    if (e == cudaSuccess) e = cudaEventRecord(plan->ev_out, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(user, plan->ev_out, 0);
     return e == cudaSuccess ? CYL_OK : cuda_error(e, "cyl_project_noalloc");
 }

@@ -39,20 +39,16 @@ int cyl_plan::init(const cyl_grid &gr, const cyl_geom &ge, const cyl_pose &po, i
     geom.angles_rad = angles.data();
     n_vox = (int64_t)gr.n_h * gr.n_theta * gr.n_r;
     n_pix = (int64_t)ge.det_w * ge.det_h;
-    int maxsm = 0;
-    PL_CUDA(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    // leave room for the kernels' static shared memory (walk scratch, about 1 KB)
-    int rc = choose_tiles(grid, maxsm - 4096, td);
-    if (rc) return rc;
-    PL_CUDA(set_kernel_attributes());
+    int rc;
     std::vector<float2> trig;
     build_grid(grid, geom, g, trig);
     const size_t n_rays = (size_t)geom.n_proj * n_pix;
     if ((rc = alloc(&d_geo, sizeof(ProjGeom) * geom.n_proj))) return rc;
     if ((rc = alloc(&d_trig, sizeof(float2) * trig.size()))) return rc;
-    if ((rc = alloc(&d_bbox, sizeof(int4) * (size_t)geom.n_proj * td.n_tiles))) return rc;
     for (int k = 0; k < 3; ++k)
         if ((rc = alloc(&d_ray[k], sizeof(float4) * n_rays))) return rc;
+    if ((rc = alloc(&d_split, sizeof(uint16_t) * kSplit * n_rays))) return rc;
+    if ((rc = alloc(&d_sched, sizeof(int) * kSched))) return rc;
     for (int k = 0; k < 2; ++k)
         if ((rc = alloc(&d_nd[k], sizeof(float2) * n_vox))) return rc;
     if ((rc = alloc(&d_wscale, 2 * sizeof(float)))) return rc;
@@ -61,8 +57,8 @@ int cyl_plan::init(const cyl_grid &gr, const cyl_geom &ge, const cyl_pose &po, i
     PL_CUDA(cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming));
     PL_CUDA(cudaEventCreateWithFlags(&ev_geo, cudaEventDisableTiming));
     PL_CUDA(cudaMallocHost(&h_geo, sizeof(ProjGeom) * geom.n_proj));
-    PL_CUDA(cudaMallocHost(&h_bbox, sizeof(int4) * (size_t)geom.n_proj * td.n_tiles));
     PL_CUDA(cudaMemcpyAsync(d_trig, trig.data(), sizeof(float2) * trig.size(), cudaMemcpyHostToDevice, ws));
+    PL_CUDA(cudaMemsetAsync(d_sched, 0, sizeof(int) * kSched, ws));
     if ((rc = upload_pose(pose, ws))) return rc;
     PL_CUDA(cudaStreamSynchronize(ws));
     return CYL_OK;
@@ -71,16 +67,14 @@ int cyl_plan::init(const cyl_grid &gr, const cyl_geom &ge, const cyl_pose &po, i
 int cyl_plan::upload_pose(const cyl_pose &po, cudaStream_t st)
 {
     std::vector<ProjGeom> geo;
-    std::vector<int4> bb;
-    build_views(grid, geom, po, td, geo, bb);
+    build_views(geom, po, geo);
     // the pinned staging copies may still feed the previous upload
     PL_CUDA(cudaEventSynchronize(ev_geo));
     std::memcpy(h_geo, geo.data(), sizeof(ProjGeom) * geo.size());
-    std::memcpy(h_bbox, bb.data(), sizeof(int4) * bb.size());
     PL_CUDA(cudaMemcpyAsync(d_geo, h_geo, sizeof(ProjGeom) * geo.size(), cudaMemcpyHostToDevice, st));
-    PL_CUDA(cudaMemcpyAsync(d_bbox, h_bbox, sizeof(int4) * bb.size(), cudaMemcpyHostToDevice, st));
     PL_CUDA(cudaEventRecord(ev_geo, st));
     PL_CUDA(launch_rays(g, d_geo, geom.n_proj, d_ray[0], d_ray[1], d_ray[2], st));
+    PL_CUDA(launch_split(scan_dev(), geom.n_proj, d_split, st));
     pose = po;
     return CYL_OK;
 }
@@ -132,16 +126,15 @@ cyl_plan::~cyl_plan()
     if (ev_out) cudaEventDestroy(ev_out);
     if (ev_geo) cudaEventDestroy(ev_geo);
     if (h_geo) cudaFreeHost(h_geo);
-    if (h_bbox) cudaFreeHost(h_bbox);
     if (ws) cudaStreamDestroy(ws);
     for (void *p : allocs) cudaFree(p);
 }
 
-// One sweep.  Subset k of the sweep uses accumulator b = (parity + k) & 1: zero its
-// projections, forward-project (the kernel also clears accumulator b ^ 1, which the
-// previous subset's update has consumed), back-project the residuals into accumulator b,
-// then apply Eq. 6.  Timed runs record an event before the forward projection, between
-// the kernels and after the update.
+// One sweep.  Subset k of the sweep uses accumulator b = (parity + k) & 1: forward-
+// project (the kernel also clears accumulator b ^ 1, which the previous subset's update
+// has consumed), back-project the residuals into accumulator b, then apply Eq. 6.  Timed
+// runs record an event before the forward projection, between the kernels and after the
+// update.
 int cyl_plan::queue_sweep(const SolveState &s, cudaStream_t st, bool timed, int parity)
 {
     const ScanDev sd = scan_dev();
@@ -162,7 +155,6 @@ int cyl_plan::queue_sweep(const SolveState &s, cudaStream_t st, bool timed, int 
         cudaEvent_t *ev = timed ? next_events(4) : nullptr;
         if (timed && !ev) return set_error(CYL_EDEVICE, "event creation failed");
         if (ev) PL_CUDA(cudaEventRecord(ev[0], st));
-        PL_CUDA(cudaMemsetAsync(d_q, 0, sizeof(float) * (size_t)np * n_pix, st));
         PL_CUDA(launch_fp_rays(sd, p_fp, p0, np, s.x_proj, s.x_proj_t, d_q, d_nd[b ^ 1], n_vox, st));
         if (ev) PL_CUDA(cudaEventRecord(ev[1], st));
         PL_CUDA(launch_bp_rays(sd, p_bp, p0, np, sino_p, s.sino_t, d_q, d_nd[b], nullptr, nullptr, st));
@@ -296,7 +288,7 @@ int cyl_plan::solve(const void *sino, cyl_dtype sino_t, const void *x0, const fl
     return CYL_OK;
 }
 
-// Autotuner: time the projector and the back-projector of view 0 for 1, 2, 4 and 8
+// Autotuner: time the projector and the back-projector of view 0 for 1, 2, 4, 8 and 16
 // pieces per ray and keep the fastest of each (the walk's cost does not depend on the
 // volume's values, so a zero volume and zero data serve).
 int cyl_plan::tune(cudaStream_t st)
@@ -310,9 +302,8 @@ int cyl_plan::tune(cudaStream_t st)
     cudaEvent_t e[2];
     PL_CUDA(cudaEventCreate(&e[0]));
     PL_CUDA(cudaEventCreate(&e[1]));
-    const int opts[4] = {1, 2, 4, 8};
     float best_fp = 1e30f, best_bp = 1e30f;
-    for (int P : opts) {
+    for (int P = 1; P <= kSplit; P *= 2) {
         for (int kind = 0; kind < 2; ++kind) {
             float ms_min = 1e30f;
             for (int rep = 0; rep < 3; ++rep) {

@@ -13,10 +13,8 @@ int cuda_error(cudaError_t e, const char *what);
 
 // geometry.cu
 int validate_scan(const cyl_grid *grid, const cyl_geom *geom, const cyl_pose *pose);
-int choose_tiles(const cyl_grid &grid, int max_smem, TileDev &td);
 void build_grid(const cyl_grid &grid, const cyl_geom &geom, GridDev &g, std::vector<float2> &trig);
-void build_views(const cyl_grid &grid, const cyl_geom &geom, const cyl_pose &pose,
-                 const TileDev &td, std::vector<ProjGeom> &geo, std::vector<int4> &bbox);
+void build_views(const cyl_geom &geom, const cyl_pose &pose, std::vector<ProjGeom> &geo);
 
 // batch.cu: per round, the (scan, subset) items of a batched solve
 void batch_rounds(const std::vector<int> &n_proj, int subset, int n_iter,
@@ -55,19 +53,19 @@ struct cyl_plan {
     cyl_pose pose{};
     std::vector<double> angles;
     cylct::GridDev g{};
-    cylct::TileDev td{};
     int64_t n_vox = 0, n_pix = 0;
     size_t bytes = 0;
 
     cylct::ProjGeom *d_geo = nullptr;
     float2 *d_trig = nullptr;
     float4 *d_ray[3] = {nullptr, nullptr, nullptr};
-    int4 *d_bbox = nullptr;
+    uint16_t *d_split = nullptr;   // [view][pixel][kSplit] cuts of each ray (per pose)
+    int *d_sched = nullptr;        // work counters of the persistent kernels (kSched)
     float *d_wscale = nullptr;
     float *d_q = nullptr;          // forward projections of one subset (FP32)
     size_t q_cap = 0;
     float2 *d_nd[2] = {nullptr, nullptr};   // (numerator, column sum) accumulators, per voxel
-    int p_fp = 4, p_bp = 4;        // pieces per ray of the projector / back-projector
+    int p_fp = 0, p_bp = 0;        // pieces per ray of the projector / back-projector (0: default)
     float *d_x32 = nullptr;
     size_t x32_cap = 0;
     void *d_stage[4] = {nullptr, nullptr, nullptr, nullptr};  // sino, x0, w, x_out
@@ -76,7 +74,6 @@ struct cyl_plan {
     cudaStream_t ws = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_geo = nullptr;
     void *h_geo = nullptr;         // pinned staging of the view tables (set_pose)
-    void *h_bbox = nullptr;
 
     bool timing = false;
     double kernel_ms[3] = {0, 0, 0};
@@ -95,12 +92,12 @@ struct cyl_plan {
     {
         cylct::ScanDev sd;
         sd.g = g;
-        sd.td = td;
         sd.trig = d_trig;
         sd.ray_a = d_ray[0];
         sd.ray_b = d_ray[1];
         sd.ray_c = d_ray[2];
-        sd.bbox = d_bbox;
+        sd.split = d_split;
+        sd.sched = d_sched;
         return sd;
     }
 

@@ -1,13 +1,27 @@
-// Ray-driven kernels: each ray is cut into P pieces of equal length along the ray, and
-// each piece is walked by one thread (a warp holds the same piece of 32 adjacent rays,
-// so its lanes walk similar paths).
-//   forward:  q_j += sum over the piece of t_jl x_l          (x gathered from L2 / HBM)
-//   backward: nd_l += (t_jl y_j, t_jl)                        (one packed 2 x FP32 atomic
-//             per piece of a ray in a voxel: numerator and column sum of Eq. 6 together)
-//   update:   x_l += s w_l num_l / den_l where den_l > 0      (Eq. 6), elementwise
+// Ray-driven kernels of Eq. 6.  Every ray is cut into pieces that hold equal numbers of
+// steps (the cuts are found once per pose by walking each ray, k_split), and every piece
+// is one task for one thread.  The warps of a persistent grid take 32 tasks at a time
+// from a work counter.  The long walks of rays through the middle of the grid, where the
+// wedge crossings of a ray bunch up around its closest approach to the axis, are thereby
+// spread over many threads, and a launch ends when its work ends.  Consecutive fetches
+// are sent to kStride parts of the detector far apart (task_of), so the rays in flight
+// at any time cover the whole view and their atomics spread over the whole volume.
+//   forward:  q_j = sum over the ray of t_jl x_l.  A warp task is ray-major: the P
+//             pieces of a ray sit in P adjacent lanes, which add their sums with
+//             shuffles; one lane stores q_j (no atomics, no zeroing of q).
+//   backward: nd_l += (t_jl r_j, t_jl), one packed 2 x FP32 reduction per segment (the
+//             numerator and the column sum of Eq. 6 together), r_j = (p_j - q_j) / L_j.
+//             A warp task is piece-major: the same piece of 32 adjacent rays, whose
+//             reductions land on neighbouring voxels.
+//   update:   x_l += s w_l num_l / den_l where den_l > 0 (Eq. 6), elementwise
 // The forward kernel also clears the spare accumulator (the one the previous subset's
 // update has consumed), so no separate memset pass is needed.
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <mutex>
 #include <type_traits>
+#include <utility>
 
 #include "traverse.cuh"
 
@@ -23,52 +37,18 @@ template <> __device__ __forceinline__ float from_f32r<float>(float v) { return 
 template <> __device__ __forceinline__ __half from_f32r<__half>(float v) { return __float2half_rn(v); }
 template <> __device__ __forceinline__ __nv_bfloat16 from_f32r<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
 
-__device__ __forceinline__ void red_add2(float2 *p, float a, float b)
+// *p += (a, len) when len > 0, as one predicated packed reduction (no branch)
+__device__ __forceinline__ void red_add2_pos(float2 *p, float a, float len)
 {
-    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a), "f"(b) : "memory");
-}
-
-struct Piece {
-    int64_t r;      // ray slot in [0, n_rays)
-    int piece;
-    bool valid;
-};
-
-__device__ __forceinline__ Piece piece_of(int64_t n_rays, int P, int64_t block0 = 0)
-{
-    Piece pc;
-    const int64_t gw = ((block0 + blockIdx.x) * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    pc.piece = (int)(gw % P);
-    pc.r = (gw / P) * 32 + (threadIdx.x & 31);
-    pc.valid = pc.r < n_rays;
-    return pc;
-}
-
-__device__ __forceinline__ Tile whole_grid(const GridDev &g)
-{
-    Tile t;
-    t.t0 = 0;
-    t.t1 = g.n_t;
-    t.s0 = 0;
-    t.s1 = g.n_h;
-    t.full_circle = true;
-    return t;
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.gt.f32 q, %2, 0f00000000;\n\t"
+                 "@q red.global.add.v2.f32 [%0], {%1, %2};\n\t}"
+                 ::"l"(p), "f"(a), "f"(len) : "memory");
 }
 
 __device__ __forceinline__ void stage_trig_smem(const float2 *trig, int n_t, float2 *s)
 {
     for (int k = threadIdx.x; k < n_t; k += blockDim.x) s[k] = trig[k];
     __syncthreads();
-}
-
-// piece [ua, ub] of ray rr; false if the ray misses the grid
-__device__ __forceinline__ bool piece_interval(const RayRec &rr, int piece, int P, float &ua, float &ub)
-{
-    if (!(rr.c.y > rr.c.x)) return false;
-    const float len = (rr.c.y - rr.c.x) / (float)P;
-    ua = rr.c.x + piece * len;
-    ub = piece == P - 1 ? rr.c.y : rr.c.x + (piece + 1) * len;
-    return ub > ua;
 }
 
 __device__ __forceinline__ RayRec ray_at(const ScanDev &sd, int64_t rec)
@@ -86,56 +66,84 @@ __device__ __forceinline__ void zero_slice(float2 *buf, int64_t len, int64_t tid
     for (int64_t i = tid; i < len; i += nthreads) buf[i] = make_float2(0.f, 0.f);
 }
 
-// ------------------------------------------------------------------ device bodies
+// --------------------------------------------------------------- work scheduling
 
-template <class T>
-__device__ __forceinline__ void fp_piece(const ScanDev &sd, const float2 *s_trig, int p0, int64_t n_rays,
-                                         int P, const T *__restrict__ x, float *__restrict__ q, Piece pc)
+// sched[0] hands out warp tasks; sched[1] counts the warps that found no work left, and
+// the last of them resets both, so the pair is zero again for the next launch on the
+// stream.  Every warp of the grid calls retire() exactly once, after its last fetch.
+__device__ __forceinline__ int fetch_task(int *sched)
 {
-    if (!pc.valid) return;
-    const GridDev &g = sd.g;
-    const int64_t npix = (int64_t)g.det_w * g.det_h;
-    const RayRec rr = ray_at(sd, (int64_t)p0 * npix + pc.r);
-    float ua, ub;
-    if (!piece_interval(rr, pc.piece, P, ua, ub)) return;
-    const Tile t = whole_grid(g);
-    Walker w;
-    w.init(g, s_trig, t, rr, ua, ub);
-    float acc = 0.f;
-    auto op = [&](int idx, float len) { acc = fmaf(len, as_f32<T>(__ldg(x + idx)), acc); };
-    while (w.step(g, s_trig, t, op)) {
-    }
-    if (acc != 0.f) atomicAdd(q + pc.r, acc);
+    int v = 0;
+    if ((threadIdx.x & 31) == 0) v = atomicAdd(sched, 1);
+    return __shfl_sync(0xffffffffu, v, 0);
 }
 
-template <class S, bool SART>
-__device__ __forceinline__ void bp_piece(const ScanDev &sd, const float2 *s_trig, int p0, int64_t n_rays,
-                                         int P, const S *__restrict__ y, const float *__restrict__ q,
-                                         float2 *__restrict__ nd, float *__restrict__ num,
-                                         float *__restrict__ den, Piece pc)
+__device__ __forceinline__ void retire(int *sched)
 {
-    if (!pc.valid) return;
-    const GridDev &g = sd.g;
-    const int64_t npix = (int64_t)g.det_w * g.det_h;
-    const RayRec rr = ray_at(sd, (int64_t)p0 * npix + pc.r);
-    float ua, ub;
-    if (!piece_interval(rr, pc.piece, P, ua, ub)) return;
-    float yv;
-    if (SART) {
-        const float L = rr.c.z;
-        yv = L > 0.f ? (as_f32<S>(y[pc.r]) - q[pc.r]) / L : 0.f;
-    } else {
-        yv = as_f32<S>(y[pc.r]);
-        if (yv == 0.f && !den) return;
+    if ((threadIdx.x & 31) == 0) {
+        __threadfence();
+        const unsigned total = gridDim.x * (blockDim.x >> 5);
+        if ((unsigned)atomicAdd(sched + 1, 1) == total - 1) {
+            atomicExch(sched, 0);
+            atomicExch(sched + 1, 0);
+        }
     }
-    const Tile t = whole_grid(g);
+}
+
+// Warp task of fetch number f among n (f < task_span(n)): fetches f and f + 1 go to
+// tasks about n / kStride apart.  Returns -1 for the few fetch numbers past n.
+constexpr int kLgStride = 8, kStride = 1 << kLgStride;
+
+__device__ __forceinline__ int64_t task_span(int64_t n) { return ((n + kStride - 1) >> kLgStride) << kLgStride; }
+
+__device__ __forceinline__ int64_t task_of(int64_t f, int64_t n)
+{
+    const int64_t c = (n + kStride - 1) >> kLgStride;
+    const int64_t t = (f & (kStride - 1)) * c + (f >> kLgStride);
+    return t < n ? t : -1;
+}
+
+// Piece `piece` of P of ray rr: [ua, ub] from the recorded cuts (cut i of kSplit at
+// u_in + frac_i (u_out - u_in)); false if empty.  Neighbouring pieces compute their
+// shared cut from the same stored value, so the pieces tile the clipped interval.
+__device__ __forceinline__ bool piece_bounds(const RayRec &rr, const uint16_t *__restrict__ cuts,
+                                             int piece, int P, float &ua, float &ub)
+{
+    const float u0 = rr.c.x, u1 = rr.c.y;
+    if (!(u1 > u0)) return false;
+    const float len = u1 - u0;
+    const int stride = kSplit / P;
+    constexpr float kq = 1.f / 65535.f;
+    ua = piece == 0 ? u0 : fminf(fmaf((float)__ldg(cuts + piece * stride - 1) * kq, len, u0), u1);
+    ub = piece == P - 1 ? u1 : fminf(fmaf((float)__ldg(cuts + (piece + 1) * stride - 1) * kq, len, u0), u1);
+    return ub > ua;
+}
+
+// ------------------------------------------------------------------ piece walks
+
+template <class T>
+__device__ __forceinline__ float fp_walk(const GridDev &g, const float2 *__restrict__ trig,
+                                         const RayRec &rr, float ua, float ub, const T *__restrict__ x)
+{
     Walker w;
-    w.init(g, s_trig, t, rr, ua, ub);
+    w.init(g, trig, rr, ua, ub);
+    float acc = 0.f;
+    auto op = [&](int idx, float len) { acc = fmaf(len, as_f32<T>(__ldg(x + idx)), acc); };
+    while (w.step(g, trig, op)) {
+    }
+    return acc;
+}
+
+// yv: the ray's value (residual or data); into nd, or into num / den when nd is null
+__device__ __forceinline__ void bp_walk(const GridDev &g, const float2 *__restrict__ trig,
+                                        const RayRec &rr, float ua, float ub, float yv, float2 *nd,
+                                        float *num, float *den)
+{
+    Walker w;
+    w.init(g, trig, rr, ua, ub);
     if (nd) {
-        auto op = [&](int idx, float len) {
-            if (len > 0.f) red_add2(nd + idx, len * yv, len);
-        };
-        while (w.step(g, s_trig, t, op)) {
+        auto op = [&](int idx, float len) { red_add2_pos(nd + idx, len * yv, len); };
+        while (w.step(g, trig, op)) {
         }
     } else {
         auto op = [&](int idx, float len) {
@@ -144,9 +152,16 @@ __device__ __forceinline__ void bp_piece(const ScanDev &sd, const float2 *s_trig
                 if (den) atomicAdd(den + idx, len);
             }
         };
-        while (w.step(g, s_trig, t, op)) {
+        while (w.step(g, trig, op)) {
         }
     }
+}
+
+// sum over the P adjacent lanes of a ray (P divides 32)
+__device__ __forceinline__ float ray_sum(float v, int P)
+{
+    for (int o = P >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
 }
 
 template <class X>
@@ -162,28 +177,131 @@ __device__ __forceinline__ void update_voxel(const UpdateArgs &u, int64_t m, flo
     if (x16) x16[m] = from_f32r<X>(xv);
 }
 
-// ------------------------------------------------------------------ single scan
+// ------------------------------------------------------------------ set-up
 
-template <class T, int P>
-__global__ void __launch_bounds__(256)
-k_fp_ray(ScanDev sd, int p0, int64_t n_rays, const T *__restrict__ x, float *__restrict__ q,
-         float2 *zero_buf, int64_t zero_len)
+// Steps of a ray's walk, estimated from the crossings of each family between u_in and
+// u_out (shells from the radii at both ends and at the closest approach, wedges from the
+// angle swept, slabs from the height travelled).
+__device__ __forceinline__ float estimate_steps(const GridDev &g, const RayRec &rr)
 {
-    extern __shared__ float2 s_trig_ray[];
-    stage_trig_smem(sd.trig, sd.g.n_t, s_trig_ray);
-    zero_slice(zero_buf, zero_len, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
-               (int64_t)gridDim.x * blockDim.x);
-    fp_piece<T>(sd, s_trig_ray, p0, n_rays, P, x, q, piece_of(n_rays, P));
+    const float ex = rr.b.x, ey = rr.b.y, d2 = rr.b.w, u0 = rr.c.x, u1 = rr.c.y;
+    float n = 1.f + (u1 - u0) * fabsf(rr.b.z) * g.inv_dh;
+    if (ray_kstar(rr) >= 0) {
+        const float a = fmaf(ex, ex, ey * ey);
+        const float r0 = sqrtf(fmaf(a * u0, u0, d2)), r1 = sqrtf(fmaf(a * u1, u1, d2)), rd = sqrtf(d2);
+        n += ((u0 < 0.f && u1 > 0.f) ? (r0 - rd) + (r1 - rd) : fabsf(r1 - r0)) * g.inv_dr;
+        if (g.n_t > 1) {
+            const float x0 = fmaf(u0, ex, rr.a.x), y0 = fmaf(u0, ey, rr.a.y);
+            const float x1 = fmaf(u1, ex, rr.a.x), y1 = fmaf(u1, ey, rr.a.y);
+            n += fabsf(atan2f(x0 * y1 - y0 * x1, x0 * x1 + y0 * y1)) * g.inv_dth;
+        }
+    }
+    return n;
 }
 
-template <class S, int P, bool SART>
-__global__ void __launch_bounds__(256)
-k_bp_ray(ScanDev sd, int p0, int64_t n_rays, const S *__restrict__ y, const float *__restrict__ q,
-         float2 *nd, float *num, float *den)
+// One thread per ray of every view: walk the ray once and record kSplit - 1 cuts, cut i
+// in the middle of the segment that holds step ceil(i N / kSplit) of an estimated N.  The
+// last entry keeps the estimate (saturated), for diagnostics.
+__global__ void __launch_bounds__(256) k_split(ScanDev sd, int64_t n_rays, uint16_t *split)
 {
-    extern __shared__ float2 s_trig_ray[];
-    stage_trig_smem(sd.trig, sd.g.n_t, s_trig_ray);
-    bp_piece<S, SART>(sd, s_trig_ray, p0, n_rays, P, y, q, nd, num, den, piece_of(n_rays, P));
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_rays) return;
+    const RayRec rr = ray_at(sd, j);
+    uint16_t *out = split + j * kSplit;
+    if (!(rr.c.y > rr.c.x)) {
+        for (int i = 0; i < kSplit; ++i) out[i] = 0;
+        return;
+    }
+    const GridDev &g = sd.g;
+    const float n_est = estimate_steps(g, rr);
+    const float per = n_est / kSplit;
+    const float scale = 65535.f / (rr.c.y - rr.c.x);
+    Walker w;
+    w.init(g, sd.trig, rr, rr.c.x, rr.c.y);
+    int s = 0, next = 1;
+    auto op = [&](int, float len) {
+        ++s;
+        while (next < kSplit && (float)s >= ceilf(next * per)) {
+            const float f = (fmaf(0.5f, len, w.u) - rr.c.x) * scale;
+            out[next - 1] = (uint16_t)fminf(fmaxf(f, 0.f), 65535.f);
+            ++next;
+        }
+    };
+    while (w.step(g, sd.trig, op)) {
+    }
+    for (; next < kSplit; ++next) out[next - 1] = 65535;
+    out[kSplit - 1] = (uint16_t)fminf(n_est, 65535.f);
+}
+
+// ------------------------------------------------------------------ single scan
+
+// Rays j in [0, n_rays) are rays p0 * H * W + j of the plan; lgP = log2(P).
+template <class T>
+__global__ void __launch_bounds__(256)
+k_fp(ScanDev sd, int lgP, int p0, int64_t n_rays, const T *__restrict__ x, float *__restrict__ q,
+     float2 *zero_buf, int64_t zero_len)
+{
+    extern __shared__ float2 s_trig[];
+    stage_trig_smem(sd.trig, sd.g.n_t, s_trig);
+    zero_slice(zero_buf, zero_len, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+               (int64_t)gridDim.x * blockDim.x);
+    const int P = 1 << lgP, lane = threadIdx.x & 31;
+    const int64_t base = (int64_t)p0 * sd.g.det_w * sd.g.det_h;
+    const int64_t n_wt = ((n_rays << lgP) + 31) >> 5, span = task_span(n_wt);
+    for (;;) {
+        const int f = fetch_task(sd.sched);
+        if (f >= span) break;
+        const int64_t wt = task_of(f, n_wt);
+        if (wt < 0) continue;
+        const int64_t t = wt * 32 + lane, r = t >> lgP;
+        const int piece = (int)(t & (P - 1));
+        float acc = 0.f;
+        if (r < n_rays) {
+            const RayRec rr = ray_at(sd, base + r);
+            float ua, ub;
+            if (piece_bounds(rr, sd.split + (base + r) * kSplit, piece, P, ua, ub))
+                acc = fp_walk<T>(sd.g, s_trig, rr, ua, ub, x);
+        }
+        acc = ray_sum(acc, P);
+        if (piece == 0 && r < n_rays) q[r] = acc;
+    }
+    retire(sd.sched);
+}
+
+// y, q: the launch's rays (indexed like r); SART: residual (y - q) / L, else y
+template <class S, bool SART>
+__global__ void __launch_bounds__(256)
+k_bp(ScanDev sd, int lgP, int p0, int64_t n_rays, const S *__restrict__ y, const float *__restrict__ q,
+     float2 *nd, float *num, float *den)
+{
+    extern __shared__ float2 s_trig[];
+    stage_trig_smem(sd.trig, sd.g.n_t, s_trig);
+    const int P = 1 << lgP, lane = threadIdx.x & 31;
+    const int64_t base = (int64_t)p0 * sd.g.det_w * sd.g.det_h;
+    const int64_t n_wt = ((n_rays + 31) >> 5) << lgP, span = task_span(n_wt);
+    int *sched = sd.sched + 2;
+    for (;;) {
+        const int f = fetch_task(sched);
+        if (f >= span) break;
+        const int64_t wt = task_of(f, n_wt);
+        if (wt < 0) continue;
+        const int64_t r = (wt >> lgP) * 32 + lane;
+        const int piece = (int)(wt & (P - 1));
+        if (r >= n_rays) continue;
+        const RayRec rr = ray_at(sd, base + r);
+        float ua, ub;
+        if (!piece_bounds(rr, sd.split + (base + r) * kSplit, piece, P, ua, ub)) continue;
+        float yv;
+        if (SART) {
+            const float L = rr.c.z;
+            yv = L > 0.f ? (as_f32<S>(y[r]) - q[r]) / L : 0.f;
+        } else {
+            yv = as_f32<S>(y[r]);
+            if (yv == 0.f && !den) continue;
+        }
+        bp_walk(sd.g, s_trig, rr, ua, ub, yv, nd, num, den);
+    }
+    retire(sched);
 }
 
 template <class X>
@@ -195,79 +313,144 @@ __global__ void k_update_nd(int64_t n, const float2 *__restrict__ nd, UpdateArgs
         update_voxel<X>(u, m, __ldg(nd + m), sc);
 }
 
-struct CountRayOp {
-    unsigned int n;
-};
-
-template <int P>
+// Segments of positive length per view; a cut inside a segment is not counted twice.
 __global__ void __launch_bounds__(256)
-k_count_ray(ScanDev sd, int p0, int64_t n_rays, unsigned long long *counts)
+k_count(ScanDev sd, int p0, int64_t n_rays, unsigned long long *counts)
 {
-    extern __shared__ float2 s_trig_ray[];
-    stage_trig_smem(sd.trig, sd.g.n_t, s_trig_ray);
-    const Piece pc = piece_of(n_rays, P);
-    unsigned int n = 0;
-    int view = 0;
-    const GridDev &g = sd.g;
-    const int64_t npix = (int64_t)g.det_w * g.det_h;
-    if (pc.valid) {
-        view = (int)(pc.r / npix);
-        const RayRec rr = ray_at(sd, (int64_t)p0 * npix + pc.r);
+    extern __shared__ float2 s_trig[];
+    stage_trig_smem(sd.trig, sd.g.n_t, s_trig);
+    const int lane = threadIdx.x & 31;
+    const int64_t npix = (int64_t)sd.g.det_w * sd.g.det_h, base = p0 * npix;
+    constexpr int lgP = 4;   // kSplit pieces
+    static_assert(kSplit == 1 << lgP, "kSplit is 2^4");
+    const int64_t n_wt = ((n_rays << lgP) + 31) >> 5;
+    int *sched = sd.sched + 4;
+    for (;;) {
+        const int wt = fetch_task(sched);
+        if (wt >= n_wt) break;
+        const int64_t t = (int64_t)wt * 32 + lane, r = t >> lgP;
+        const int piece = (int)(t & (kSplit - 1));
+        if (r >= n_rays) continue;
+        const RayRec rr = ray_at(sd, base + r);
         float ua, ub;
-        if (piece_interval(rr, pc.piece, P, ua, ub)) {
-            const Tile t = whole_grid(g);
-            Walker w;
-            w.init(g, s_trig_ray, t, rr, ua, ub);
-            auto op = [&](int, float len) { n += len > 0.f; };
-            while (w.step(g, s_trig_ray, t, op)) {
-            }
-            // the cut at the start of a later piece splits one segment of the ray in two
-            if (pc.piece > 0 && n > 0) --n;
+        if (!piece_bounds(rr, sd.split + (base + r) * kSplit, piece, kSplit, ua, ub)) continue;
+        Walker w;
+        w.init(sd.g, s_trig, rr, ua, ub);
+        unsigned int n = 0;
+        auto op = [&](int, float len) { n += len > 0.f; };
+        while (w.step(sd.g, s_trig, op)) {
         }
+        if (piece > 0 && n > 0) --n;
+        if (n) atomicAdd(counts + r / npix, (unsigned long long)n);
     }
-    if (n) atomicAdd(counts + view, (unsigned long long)n);
+    retire(sched);
 }
 
 // ------------------------------------------------------------------ batched rounds
 
-// Blocks (x, item): item k of the round's items; x spans the item's ray pieces.  The
-// forward kernel also clears the scan's spare accumulators (projections and nd) for the
-// next round.
-template <class T, int P>
-__global__ void __launch_bounds__(256)
-k_fp_ray_batch(const BatchScan *__restrict__ scans, const BatchItem *__restrict__ items,
-               const int *__restrict__ n_items, int max_items, int round)
+// Warp tasks of the round's items, item-aligned (a warp task never spans two items):
+// s_pre[k] = first warp task of item k, s_pre[n] = total.  Thread 0 fills it.  An item
+// of `rays` rays has ceil(rays P / 32) ray-major warp tasks (forward) or
+// ceil(rays / 32) P piece-major ones (backward).
+template <bool PIECE_MAJOR>
+__device__ __forceinline__ int round_prefix(const BatchScan *__restrict__ scans,
+                                            const BatchItem *__restrict__ its, int n, int lgP,
+                                            int *s_pre)
 {
-    extern __shared__ float2 s_trig_ray[];
-    const int k = blockIdx.y;
-    if (k >= n_items[round]) return;
-    const BatchItem it = items[(int64_t)round * max_items + k];
-    const BatchScan &sc = scans[it.scan];
-    stage_trig_smem(sc.sd.trig, sc.sd.g.n_t, s_trig_ray);
-    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
-    zero_slice(sc.nd[it.buf ^ 1], sc.nd_len, tid, nth);
-    for (int64_t i = tid; i < sc.q_len; i += nth) sc.q[it.buf ^ 1][i] = 0.f;
-    const int64_t n_rays = (int64_t)it.np * sc.sd.g.det_w * sc.sd.g.det_h;
-    fp_piece<T>(sc.sd, s_trig_ray, it.p0, n_rays, P, static_cast<const T *>(sc.x_proj), sc.q[it.buf],
-                piece_of(n_rays, P));
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int k = 0; k < n; ++k) {
+            s_pre[k] = acc;
+            const BatchScan &sc = scans[its[k].scan];
+            const int64_t rays = (int64_t)its[k].np * sc.sd.g.det_w * sc.sd.g.det_h;
+            acc += PIECE_MAJOR ? (int)(((rays + 31) >> 5) << lgP) : (int)(((rays << lgP) + 31) >> 5);
+        }
+        s_pre[n] = acc;
+    }
+    __syncthreads();
+    return s_pre[n];
 }
 
-template <class S, int P>
-__global__ void __launch_bounds__(256)
-k_bp_ray_batch(const BatchScan *__restrict__ scans, const BatchItem *__restrict__ items,
-               const int *__restrict__ n_items, int max_items, int round)
+// the item whose warp tasks hold wt (s_pre ascending, n >= 1)
+__device__ __forceinline__ int item_of(const int *s_pre, int n, int wt)
 {
-    extern __shared__ float2 s_trig_ray[];
-    const int k = blockIdx.y;
-    if (k >= n_items[round]) return;
-    const BatchItem it = items[(int64_t)round * max_items + k];
-    const BatchScan &sc = scans[it.scan];
-    stage_trig_smem(sc.sd.trig, sc.sd.g.n_t, s_trig_ray);
-    const int64_t npix = (int64_t)sc.sd.g.det_w * sc.sd.g.det_h;
-    const int64_t n_rays = (int64_t)it.np * npix;
-    const S *y = static_cast<const S *>(sc.sino) + (int64_t)it.p0 * npix;
-    bp_piece<S, true>(sc.sd, s_trig_ray, it.p0, n_rays, P, y, sc.q[it.buf], sc.nd[it.buf], nullptr,
-                      nullptr, piece_of(n_rays, P));
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_pre[mid] <= wt) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <class T>
+__global__ void __launch_bounds__(256)
+k_fp_batch(const BatchScan *__restrict__ scans, const BatchItem *__restrict__ items,
+           const int *__restrict__ n_items, int max_items, int round, int lgP, int *sched)
+{
+    extern __shared__ int s_pre[];
+    const int n = n_items[round];
+    const BatchItem *its = items + (int64_t)round * max_items;
+    const int total = round_prefix<false>(scans, its, n, lgP, s_pre);
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
+    for (int k = 0; k < n; ++k) {   // spare accumulators of every item's scan
+        const BatchScan &sc = scans[its[k].scan];
+        zero_slice(sc.nd[its[k].buf ^ 1], sc.nd_len, tid, nth);
+    }
+    const int P = 1 << lgP, lane = threadIdx.x & 31;
+    for (;;) {
+        const int wt = fetch_task(sched);
+        if (wt >= total) break;
+        const int k = item_of(s_pre, n, wt);
+        const BatchItem it = its[k];
+        const BatchScan &sc = scans[it.scan];
+        const int64_t npix = (int64_t)sc.sd.g.det_w * sc.sd.g.det_h, n_rays = it.np * npix;
+        const int64_t base = it.p0 * npix;
+        const int64_t t = (int64_t)(wt - s_pre[k]) * 32 + lane, r = t >> lgP;
+        const int piece = (int)(t & (P - 1));
+        float acc = 0.f;
+        if (r < n_rays) {
+            const RayRec rr = ray_at(sc.sd, base + r);
+            float ua, ub;
+            if (piece_bounds(rr, sc.sd.split + (base + r) * kSplit, piece, P, ua, ub))
+                acc = fp_walk<T>(sc.sd.g, sc.sd.trig, rr, ua, ub, static_cast<const T *>(sc.x_proj));
+        }
+        acc = ray_sum(acc, P);
+        if (piece == 0 && r < n_rays) sc.q[it.buf][r] = acc;
+    }
+    retire(sched);
+}
+
+template <class S>
+__global__ void __launch_bounds__(256)
+k_bp_batch(const BatchScan *__restrict__ scans, const BatchItem *__restrict__ items,
+           const int *__restrict__ n_items, int max_items, int round, int lgP, int *sched)
+{
+    extern __shared__ int s_pre[];
+    const int n = n_items[round];
+    const BatchItem *its = items + (int64_t)round * max_items;
+    const int total = round_prefix<true>(scans, its, n, lgP, s_pre);
+    const int P = 1 << lgP, lane = threadIdx.x & 31;
+    for (;;) {
+        const int wt = fetch_task(sched + 2);
+        if (wt >= total) break;
+        const int k = item_of(s_pre, n, wt);
+        const BatchItem it = its[k];
+        const BatchScan &sc = scans[it.scan];
+        const int64_t npix = (int64_t)sc.sd.g.det_w * sc.sd.g.det_h, n_rays = it.np * npix;
+        const int64_t base = it.p0 * npix;
+        const int wl = wt - s_pre[k];
+        const int64_t r = (int64_t)(wl >> lgP) * 32 + lane;
+        const int piece = wl & (P - 1);
+        if (r >= n_rays) continue;
+        const RayRec rr = ray_at(sc.sd, base + r);
+        float ua, ub;
+        if (!piece_bounds(rr, sc.sd.split + (base + r) * kSplit, piece, P, ua, ub)) continue;
+        const float L = rr.c.z;
+        const S *y = static_cast<const S *>(sc.sino) + base;
+        const float yv = L > 0.f ? (as_f32<S>(y[r]) - sc.q[it.buf][r]) / L : 0.f;
+        bp_walk(sc.sd.g, sc.sd.trig, rr, ua, ub, yv, sc.nd[it.buf], nullptr, nullptr);
+    }
+    retire(sched + 2);
 }
 
 template <class X>
@@ -298,24 +481,6 @@ static cudaError_t dispatch_t(cyl_dtype t, F &&f)
     return cudaErrorInvalidValue;
 }
 
-template <class F>
-static cudaError_t dispatch_p(int P, F &&f)
-{
-    switch (P) {
-    case 1: return f(std::integral_constant<int, 1>());
-    case 2: return f(std::integral_constant<int, 2>());
-    case 4: return f(std::integral_constant<int, 4>());
-    case 8: return f(std::integral_constant<int, 8>());
-    }
-    return cudaErrorInvalidValue;
-}
-
-static inline unsigned ray_blocks(int64_t n_rays, int P)
-{
-    const int64_t warps = ((n_rays + 31) / 32) * P;
-    return (unsigned)((warps * 32 + 255) / 256);
-}
-
 static inline size_t trig_smem(int n_t) { return sizeof(float2) * (size_t)n_t; }
 
 static inline int update_blocks(int64_t n)
@@ -324,18 +489,63 @@ static inline int update_blocks(int64_t n)
     return (int)(b < 152 * 8 ? (b > 0 ? b : 1) : 152 * 8);
 }
 
+// log2 of P (P <= 0: the kernel's default); -1 unless P is a power of two dividing kSplit
+static int log2_pieces(int P, int dflt)
+{
+    if (P <= 0) P = dflt;
+    int l = 0;
+    while ((1 << l) < P) ++l;
+    return (1 << l) == P && P <= kSplit ? l : -1;
+}
+
+// Blocks of a persistent grid: every SM filled with as many 256-thread blocks of
+// `kernel` (with `smem` bytes of dynamic shared memory) as fit; looked up once.
+static unsigned persistent_blocks(const void *kernel, size_t smem)
+{
+    static std::mutex mu;
+    static std::map<std::pair<const void *, std::pair<int, size_t>>, unsigned> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const auto key = std::make_pair(kernel, std::make_pair(dev, smem));
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int n_sm = 0, per_sm = 0;
+    if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, smem) != cudaSuccess ||
+        n_sm < 1 || per_sm < 1) {
+        cudaGetLastError();
+        return 152;
+    }
+    const unsigned b = (unsigned)(n_sm * per_sm);
+    cache[key] = b;
+    return b;
+}
+
+int valid_pieces(int P) { return log2_pieces(P, kSplit) >= 0; }
+int default_pieces(int kind) { return kind == 0 ? kPiecesFp : kPiecesBp; }
+
+cudaError_t launch_split(const ScanDev &sd, int n_proj, uint16_t *split, cudaStream_t st)
+{
+    const int64_t n_rays = (int64_t)n_proj * sd.g.det_w * sd.g.det_h;
+    if (n_rays <= 0) return cudaSuccess;
+    k_split<<<(unsigned)((n_rays + 255) / 256), 256, 0, st>>>(sd, n_rays, split);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fp_rays(const ScanDev &sd, int P, int p0, int np, const void *x, cyl_dtype xt,
                            float *q, float2 *zero_buf, int64_t zero_len, cudaStream_t st)
 {
     if (np <= 0) return cudaSuccess;
+    const int lgP = log2_pieces(P, kPiecesFp);
+    if (lgP < 0) return cudaErrorInvalidValue;
     const int64_t n_rays = (int64_t)np * sd.g.det_w * sd.g.det_h;
+    const size_t smem = trig_smem(sd.g.n_t);
     return dispatch_t(xt, [&](auto *tx) {
         using T = std::remove_pointer_t<decltype(tx)>;
-        return dispatch_p(P, [&](auto pc) {
-            k_fp_ray<T, decltype(pc)::value><<<ray_blocks(n_rays, pc), 256, trig_smem(sd.g.n_t), st>>>(
-                sd, p0, n_rays, (const T *)x, q, zero_buf, zero_len);
-            return cudaGetLastError();
-        });
+        const unsigned blocks = persistent_blocks((const void *)k_fp<T>, smem);
+        k_fp<T><<<blocks, 256, smem, st>>>(sd, lgP, p0, n_rays, (const T *)x, q, zero_buf, zero_len);
+        return cudaGetLastError();
     });
 }
 
@@ -343,18 +553,20 @@ cudaError_t launch_bp_rays(const ScanDev &sd, int P, int p0, int np, const void 
                            const float *q, float2 *nd, float *num, float *den, cudaStream_t st)
 {
     if (np <= 0) return cudaSuccess;
+    const int lgP = log2_pieces(P, kPiecesBp);
+    if (lgP < 0) return cudaErrorInvalidValue;
     const int64_t n_rays = (int64_t)np * sd.g.det_w * sd.g.det_h;
+    const size_t smem = trig_smem(sd.g.n_t);
     return dispatch_t(yt, [&](auto *ty) {
         using S = std::remove_pointer_t<decltype(ty)>;
-        return dispatch_p(P, [&](auto pc) {
-            if (q)
-                k_bp_ray<S, decltype(pc)::value, true><<<ray_blocks(n_rays, pc), 256, trig_smem(sd.g.n_t), st>>>(
-                    sd, p0, n_rays, (const S *)y, q, nd, num, den);
-            else
-                k_bp_ray<S, decltype(pc)::value, false><<<ray_blocks(n_rays, pc), 256, trig_smem(sd.g.n_t), st>>>(
-                    sd, p0, n_rays, (const S *)y, q, nd, num, den);
-            return cudaGetLastError();
-        });
+        if (q) {
+            const unsigned blocks = persistent_blocks((const void *)k_bp<S, true>, smem);
+            k_bp<S, true><<<blocks, 256, smem, st>>>(sd, lgP, p0, n_rays, (const S *)y, q, nd, num, den);
+        } else {
+            const unsigned blocks = persistent_blocks((const void *)k_bp<S, false>, smem);
+            k_bp<S, false><<<blocks, 256, smem, st>>>(sd, lgP, p0, n_rays, (const S *)y, q, nd, num, den);
+        }
+        return cudaGetLastError();
     });
 }
 
@@ -372,32 +584,30 @@ cudaError_t launch_count_rays(const ScanDev &sd, int p0, int np, unsigned long l
 {
     if (np <= 0) return cudaSuccess;
     const int64_t n_rays = (int64_t)np * sd.g.det_w * sd.g.det_h;
-    k_count_ray<4><<<ray_blocks(n_rays, 4), 256, trig_smem(sd.g.n_t), st>>>(sd, p0, n_rays, counts);
+    const size_t smem = trig_smem(sd.g.n_t);
+    k_count<<<persistent_blocks((const void *)k_count, smem), 256, smem, st>>>(sd, p0, n_rays, counts);
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch_round_rays(const BatchScan *scans, const BatchItem *items, const int *n_items,
-                                    int max_items, int round, int64_t max_rays, int64_t max_vox,
-                                    int max_nt, int P, cyl_dtype xt, cyl_dtype yt, cyl_dtype x16t,
-                                    cudaStream_t st)
+cudaError_t launch_batch_round(const BatchScan *scans, const BatchItem *items, const int *n_items,
+                               int max_items, int round, int64_t max_vox, int P, int *sched,
+                               cyl_dtype xt, cyl_dtype yt, cyl_dtype x16t, cudaStream_t st)
 {
-    const dim3 grid_r(ray_blocks(max_rays, P), max_items);
+    const int lgPf = log2_pieces(P, kPiecesFp), lgPb = log2_pieces(P, kPiecesBp);
+    if (lgPf < 0 || lgPb < 0 || max_items < 1) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(int) * ((size_t)max_items + 1);
     cudaError_t e = dispatch_t(xt, [&](auto *tx) {
         using T = std::remove_pointer_t<decltype(tx)>;
-        return dispatch_p(P, [&](auto pc) {
-            k_fp_ray_batch<T, decltype(pc)::value><<<grid_r, 256, trig_smem(max_nt), st>>>(
-                scans, items, n_items, max_items, round);
-            return cudaGetLastError();
-        });
+        const unsigned blocks = persistent_blocks((const void *)k_fp_batch<T>, smem);
+        k_fp_batch<T><<<blocks, 256, smem, st>>>(scans, items, n_items, max_items, round, lgPf, sched);
+        return cudaGetLastError();
     });
     if (e != cudaSuccess) return e;
     e = dispatch_t(yt, [&](auto *ty) {
         using S = std::remove_pointer_t<decltype(ty)>;
-        return dispatch_p(P, [&](auto pc) {
-            k_bp_ray_batch<S, decltype(pc)::value><<<grid_r, 256, trig_smem(max_nt), st>>>(
-                scans, items, n_items, max_items, round);
-            return cudaGetLastError();
-        });
+        const unsigned blocks = persistent_blocks((const void *)k_bp_batch<S>, smem);
+        k_bp_batch<S><<<blocks, 256, smem, st>>>(scans, items, n_items, max_items, round, lgPb, sched);
+        return cudaGetLastError();
     });
     if (e != cudaSuccess) return e;
     const dim3 grid_u((unsigned)std::min(update_blocks(max_vox), 512), max_items);

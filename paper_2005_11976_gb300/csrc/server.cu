@@ -51,7 +51,6 @@ constexpr int64_t kWaitLimitNs = 120LL * 1000 * 1000 * 1000;   // one round, at 
 struct Part {
     cyl_grid grid{};
     cyl_geom geom{};
-    TileDev td{};               // tiling of the part's grid (sizes the per-view tables)
     void *d_x0 = nullptr;       // warm start, storage dtype
     float *d_w = nullptr;       // weights or null
     float *d_wscale = nullptr;  // lambda / max(w) (or lambda)
@@ -124,6 +123,7 @@ struct cyl_server {
     std::vector<cudaEvent_t> slot_ev;
     size_t slot_bytes = 0;
     int next_slot = 0;
+    int *d_sched = nullptr;            // work counters of the round kernels (kSched)
 
     size_t scan_footprint(const Part &pt, int n_proj) const;
     int admit(const std::shared_ptr<Scan> &s);
@@ -143,7 +143,9 @@ size_t cyl_server::scan_footprint(const Part &pt, int n_proj) const
                + (size_t)n_proj * npix * sb                       // sinogram
                + (size_t)pt.n_vox * sb                             // iterate / output
                + 2 * (size_t)subset * npix * sizeof(float)         // projection buffers
-               + (size_t)n_proj * (sizeof(ProjGeom) + (size_t)pt.td.n_tiles * sizeof(int4))
+               + 2 * (size_t)pt.n_vox * sizeof(float2)            // (num, den) accumulators
+               + (size_t)n_proj * npix * kSplit * sizeof(uint16_t)  // ray cuts
+               + (size_t)n_proj * sizeof(ProjGeom)
                + 64 * 1024;                                        // small tables
     if (cfg.storage != CYL_F32) b += (size_t)pt.n_vox * sizeof(float);
     return b;
@@ -210,8 +212,6 @@ int cyl_server::admit(const std::shared_ptr<Scan> &s)
         if (launch_convert(s->d_x, cfg.storage, s->d_x32, CYL_F32, pl->n_vox, st) != cudaSuccess)
             return set_error(CYL_EDEVICE, "iterate conversion");
     }
-    if (cudaMemsetAsync(pl->d_q, 0, 2 * sizeof(float) * subset * pl->n_pix, st) != cudaSuccess)
-        return set_error(CYL_EDEVICE, "projection buffers");
     for (int k = 0; k < 2; ++k)
         if (cudaMemsetAsync(pl->d_nd[k], 0, sizeof(float2) * pl->n_vox, st) != cudaSuccess)
             return set_error(CYL_EDEVICE, "back-projection accumulators");
@@ -266,8 +266,8 @@ int cyl_server::run_round()
     std::vector<BatchScan> scans;
     std::vector<BatchItem> items;
     std::vector<std::shared_ptr<Scan>> members;
-    int max_nt = 0, P = 0;
-    int64_t max_rays = 0, max_vox = 0;
+    int P = 0;
+    int64_t max_vox = 0;
     for (auto &s : active) {
         if (s->state != 1 || s->rounds_done >= s->rounds_total) continue;
         cyl_plan *pl = s->plan;
@@ -296,9 +296,7 @@ int cyl_server::run_round()
         items.push_back(BatchItem{(int)scans.size(), p0, std::min(subset, s->req.n_proj - p0), r & 1});
         scans.push_back(sc);
         members.push_back(s);
-        max_rays = std::max(max_rays, sc.q_len);
         max_vox = std::max(max_vox, pl->n_vox);
-        max_nt = std::max(max_nt, pl->g.n_t);
         if (!P) P = pl->p_fp;
     }
     if (scans.empty()) return CYL_OK;
@@ -316,9 +314,9 @@ int cyl_server::run_round()
     if (cudaMemcpyAsync(d, h, slot_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
         return set_error(CYL_EDEVICE, "round descriptors");
     if (cudaEventRecord(slot_ev[slot], st) != cudaSuccess) return set_error(CYL_EDEVICE, "event");
-    cudaError_t e = launch_batch_round_rays(reinterpret_cast<BatchScan *>(d), reinterpret_cast<BatchItem *>(d + b_scans),
-                                            reinterpret_cast<int *>(d + b_scans + b_items), n, 0, max_rays,
-                                            max_vox, max_nt, P, cfg.storage, cfg.storage, cfg.storage, st);
+    cudaError_t e = launch_batch_round(reinterpret_cast<BatchScan *>(d), reinterpret_cast<BatchItem *>(d + b_scans),
+                                       reinterpret_cast<int *>(d + b_scans + b_items), n, 0, max_vox, P,
+                                       d_sched, cfg.storage, cfg.storage, cfg.storage, st);
     if (e != cudaSuccess) return cuda_error(e, "round launch");
     ++stats.rounds;
     for (auto &s : members) {
@@ -457,7 +455,9 @@ extern "C" int cyl_server_create(const cyl_server_cfg *cfg, cyl_server **out)
         s->d_slot.push_back(d);
         s->slot_ev.push_back(e);
     }
-    if (!rc && set_kernel_attributes() != cudaSuccess) rc = set_error(CYL_EDEVICE, "kernel attributes");
+    if (!rc && (cudaMalloc(&s->d_sched, sizeof(int) * kSched) != cudaSuccess ||
+                cudaMemset(s->d_sched, 0, sizeof(int) * kSched) != cudaSuccess))
+        rc = set_error(CYL_ENOMEM, "scheduler state");
     if (rc) {
         cyl_server_destroy(s);
         if (prev >= 0) cudaSetDevice(prev);
@@ -485,11 +485,6 @@ extern "C" int cyl_server_add_part(cyl_server *srv, const cyl_grid *grid, const 
     pt.grid = *grid;
     pt.geom = g1;
     pt.geom.angles_rad = nullptr;
-    {
-        int maxsm = 0;
-        cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, srv->cfg.device);
-        if ((rc = choose_tiles(*grid, maxsm - 4096, pt.td))) return rc;
-    }
     pt.n_vox = (int64_t)grid->n_h * grid->n_theta * grid->n_r;
     const size_t sb = dtype_size(srv->cfg.storage);
     pt.bytes = (size_t)pt.n_vox * sb + (w ? (size_t)pt.n_vox * sizeof(float) : 0) + 2 * sizeof(float);
@@ -638,6 +633,7 @@ extern "C" int cyl_server_destroy(cyl_server *srv)
         if (srv->d_slot[k]) cudaFree(srv->d_slot[k]);
         if (srv->slot_ev[k]) cudaEventDestroy(srv->slot_ev[k]);
     }
+    if (srv->d_sched) cudaFree(srv->d_sched);
     if (srv->st) cudaStreamDestroy(srv->st);
     if (prev >= 0) cudaSetDevice(prev);
     delete srv;

@@ -122,6 +122,7 @@ SIGNATURES = {
     "cyl_server_destroy": (ctypes.c_int, [_VP]),
     "cyl_plan_tune": (ctypes.c_int, [_VP, _VP]),
     "cyl_plan_get_pieces": (ctypes.c_int, [_VP, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
+    "cyl_plan_set_pieces": (ctypes.c_int, [_VP, _I32, _I32]),
     "cyl_plan_set_timing": (ctypes.c_int, [_VP, ctypes.c_int]),
     "cyl_plan_kernel_time": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                             ctypes.POINTER(_I64)]),
@@ -280,6 +281,9 @@ class Plan:
         a, b = _I32(), _I32()
         _check(load().cyl_plan_get_pieces(self.h, ctypes.byref(a), ctypes.byref(b)), "cyl_plan_get_pieces")
         return a.value, b.value
+
+    def cyl_plan_set_pieces(self, fp: int = 0, bp: int = 0):
+        _check(load().cyl_plan_set_pieces(self.h, int(fp), int(bp)), "cyl_plan_set_pieces")
 
     def cyl_plan_set_timing(self, enable: bool):
         _check(load().cyl_plan_set_timing(self.h, int(enable)), "cyl_plan_set_timing")

@@ -276,6 +276,41 @@ def test_sart_16bit_storage(lib, orc, x_dt, strict):
     assert err <= (STRICT_BOUND[x_dt] if strict else TOL_16), err
 
 
+@pytest.mark.parametrize("pieces", [1, 2, 4, 8, 16])
+def test_pieces_per_ray_do_not_change_results(lib, orc, pieces):
+    # cutting each ray into P pieces walked by different threads changes only the
+    # summation order: projections and back-projections stay within the FP32 bound, per
+    # voxel against the size of its terms
+    s = tilted_scan()
+    rng = np.random.default_rng(7)
+    x = rng.uniform(0.0, 0.05, size=s.vol_shape)
+    y = rng.standard_normal(s.sino_shape)
+    o = osetup(orc, s)
+    ref_q, ref_b = orc.project(o, x), orc.backproject(o, y)
+    with cylct.Plan(s) as plan:
+        plan.cyl_plan_set_pieces(pieces, pieces)
+        assert plan.cyl_plan_get_pieces() == (pieces, pieces)
+        got_q = gu.project(plan, x)
+        got_b = gu.backproject(plan, y)
+        plan.cyl_plan_set_pieces(0, 0)
+        assert plan.cyl_plan_get_pieces() == (8, 4)
+    assert per_projection_rel(got_q, ref_q) <= TOL_FP32
+    abs_ref = orc.backproject(o, np.abs(y))
+    assert np.max(np.abs(got_b - ref_b)) <= TOL_FP32 * np.max(abs_ref)
+
+
+def test_tune_and_piece_settings(lib):
+    s = tilted_scan()
+    with cylct.Plan(s) as plan:
+        plan.cyl_plan_tune()
+        fp, bp = plan.cyl_plan_get_pieces()
+        assert fp in (1, 2, 4, 8, 16) and bp in (1, 2, 4, 8, 16)
+        with pytest.raises(cylct.CylError) as e:
+            plan.cyl_plan_set_pieces(3, 3)
+        assert e.value.code == cylct.CYL_EINVAL
+        assert plan.cyl_plan_get_pieces() == (fp, bp)
+
+
 # ------------------------------------------------- medium workload, sampled
 
 def test_medium_single_view_projection_and_subset(lib, orc):
