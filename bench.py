@@ -35,10 +35,15 @@ METRIC = "SART iters/sec and GRays/s at stated rel err; batched-serve vs plain s
 UNIT = "SART iters/s"
 N_ITER = 20
 # DRAM bytes (read + write) per launch of each kernel at the medium workload, from one ncu
-# capture of the current kernels (profiles/); empty until such a capture exists.
-TRAFFIC: dict = {}
+# capture of the current kernels (profiles/sart_medium_kernels.md).
+TRAFFIC: dict = {"k_fp": 73.0e6, "k_bp": 83.2e6, "k_update_nd": 145.4e6}
 LAMBDA = 0.5
 I0 = 1.0e4
+CONFIG_MEDIUM = {
+    "workload": "medium plain SART: grid (128,512,128) R25 H50, 180 views over 360 deg, 256x256 det "
+                "0.8 mm, SOD 200 SDD 800, 20 sweeps lambda 0.5, warm start, ROI weights 4x, Poisson I0 1e4",
+    "l2": "flushed (256 MB write) before every timed step",
+}
 
 
 def peaks():
@@ -128,22 +133,27 @@ def oracle_sample(scan, x_warm, counts_view, w, view: int):
     return time.perf_counter() - t0, x1, o
 
 
+def oracle_view_counts(scan, x_part, view: int):
+    """Seeded Poisson counts of one view, from the oracle's own projection of the part
+    (every input of an oracle run comes from the oracle or from synth)."""
+    import dataclasses
+    import oracle
+    from paper_2005_11976_gb300 import synth
+    s1 = dataclasses.replace(scan, angles=scan.angles[view:view + 1])
+    p_clean = oracle.project(oracle.Setup(**s1.fields()), x_part)
+    return synth.poisson_counts(p_clean, I0, np.random.default_rng(5))
+
+
 def run_reference(args):
     """The FP64 CPU oracle as it stands, timed on this host's cores."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     import oracle
-    from paper_2005_11976_gb300 import synth
     oracle.build()
     scan, x_part, x_warm, w, _ = workload(0)
-    rng = np.random.default_rng(5)
-    # counts for one view from the oracle's own projection of the part
     view = 37
-    import dataclasses
-    s1 = dataclasses.replace(scan, angles=scan.angles[view:view + 1])
-    p_clean = oracle.project(oracle.Setup(**s1.fields()), x_part)
-    counts = synth.poisson_counts(p_clean, I0, rng)
+    counts = oracle_view_counts(scan, x_part, view)
     times = []
     for k in range(args.warmup + args.steps):
         dt, _, _ = oracle_sample(scan, x_warm, counts, w, view)
@@ -152,15 +162,14 @@ def run_reference(args):
     t_subset = sum(times) / len(times)
     value = 1.0 / (t_subset * scan.n_proj)
     cores = oracle.num_threads()
+    sample = f"one SART subset (view {view} of {scan.n_proj}) of the medium workload per step, scaled x{scan.n_proj}"
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t_subset * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "medium plain SART (128,512,128) grid, 180 views 256x256, 20 sweeps",
-                   "sample": "one SART subset (view 37) per step, scaled x180 views"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": "one SART subset (1 of 180 views) of the medium workload per step"},
+        "config": dict(CONFIG_MEDIUM, sample=sample),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -188,20 +197,15 @@ def main():
         return run_serving(args)
 
     import torch
-    import torch.distributed as dist
     from paper_2005_11976_gb300 import build as cbuild
-    from paper_2005_11976_gb300 import cylct, synth
+    from paper_2005_11976_gb300 import cylct, replicas, synth
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank, world, local = replicas.dist_env()
     torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    replicas.init("nccl", torch.device("cuda", local))
     if rank == 0 or not os.path.exists(cylct.LIB_PATH):
         cbuild.build()
-    if world > 1:
-        dist.barrier()
+    replicas.barrier()
     lib = cylct.load()
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
@@ -236,6 +240,14 @@ def main():
         step(stream)
     torch.cuda.synchronize()
 
+    # set-up cost of a pose: ray records and equal-step cuts of all views
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    plan.cyl_plan_set_pose(pose, stream)
+    ev1.record(stream)
+    ev1.synchronize()
+    set_pose_ms = ev0.elapsed_time(ev1)
+
     # segments per view (algorithmic bytes of the projector)
     seg = torch.zeros(scan.n_proj, dtype=torch.int64, device=dev)
     plan.cyl_count_segments(0, scan.n_proj, seg, stream)
@@ -243,8 +255,7 @@ def main():
     seg = seg.cpu().numpy()
 
     clocks = ClockSampler(local)
-    if world > 1:
-        dist.barrier()
+    replicas.barrier()
     torch.cuda.synchronize()
     clocks.start()
     t_wall0 = time.perf_counter()
@@ -266,17 +277,11 @@ def main():
                 k_ms[k] += ms
                 k_n[k] += n
     torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
+    replicas.barrier()
     t_wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    sweeps = world * args.steps * N_ITER
-    value = sweeps / (total_ms / 1e3)
+    total_ms = replicas.max_over_ranks(float(sum(step_ms)), dev)
+    value = replicas.whole_job_rate(args.steps * N_ITER, world, total_ms / 1e3)
     rays_per_sweep = 2 * scan.n_proj * n_pix         # forward + back-projected rays
     grays = world * args.steps * N_ITER * rays_per_sweep / (total_ms / 1e3) / 1e9
 
@@ -296,19 +301,21 @@ def main():
 
         e2e_step(stream)
         torch.cuda.synchronize()
+        replicas.barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
             e2e_step(stream)
         torch.cuda.synchronize()
-        e2e_t = time.perf_counter() - t0
-        e2e = {"value": world * args.steps * N_ITER / e2e_t, "unit": UNIT,
+        e2e_t = replicas.max_over_ranks(time.perf_counter() - t0, dev)
+        replicas.barrier()
+        e2e = {"value": replicas.whole_job_rate(args.steps * N_ITER, world, e2e_t), "unit": UNIT,
                "h2d_bytes_per_step": int(counts.numel() * 4),
                "d2h_bytes_per_step": int(n_vox * 4)}
 
     # --- roofline of the dominant kernel (segment-touch algorithmic bytes)
     hbm, peak_kind = peaks()
-    kinds = ["forward projection (k_fp_ray)",
-             "back-projection into (num, den) (k_bp_ray)",
+    kinds = ["forward projection (k_fp)",
+             "back-projection into (num, den) (k_bp)",
              "SART voxel update (k_update_nd)"]
     roof = None
     if not args.graph and all(k_n):
@@ -344,17 +351,17 @@ def main():
         import oracle
         oracle.build()
         view = 37
-        dt, x1_or, o = oracle_sample(scan, x_warm, counts[view:view + 1].cpu().numpy().astype(np.float64),
-                                     w, view)
+        counts_v = oracle_view_counts(scan, x_part, view)
+        dt, x1_or, o = oracle_sample(scan, x_warm, counts_v, w, view)
         cpu = {"value": 1.0 / (dt * scan.n_proj), "unit": UNIT, "cores": oracle.num_threads(),
                "kind": "oracle",
                "sample": f"one SART subset (view {view} of {scan.n_proj}) of the medium workload, "
                          f"{dt:.2f} s, scaled x{scan.n_proj}"}
         s1 = dataclasses.replace(scan, angles=scan.angles[view:view + 1])
         with cylct.Plan(s1, device=local) as p1:
-            pv = torch.empty((1,) + scan.sino_shape[1:], dtype=torch.float32, device=dev)
-            cylct.cyl_log_transform(counts[view:view + 1].contiguous(), cylct.CYL_F32, I0, pv,
-                                    cylct.CYL_F32, n_pix, stream)
+            cv = torch.from_numpy(counts_v.astype(np.float32)).to(dev)
+            pv = torch.empty_like(cv)
+            cylct.cyl_log_transform(cv, cylct.CYL_F32, I0, pv, cylct.CYL_F32, n_pix, stream)
             xg = torch.empty_like(x_out)
             p1.cyl_sart_solve(pv, cylct.CYL_F32, x0, wd, cylct.sart_params(n_iter=1, lam=LAMBDA),
                               xg, cylct.CYL_F32, stream)
@@ -362,18 +369,16 @@ def main():
             xg = xg.cpu().numpy().astype(np.float64)
         parity = float(np.linalg.norm(xg - x1_or) / np.linalg.norm(x1_or))
 
-    n_launch = args.steps * (1 + N_ITER * scan.n_proj * 2 + 2)   # rays, (fp, bp) per view, log, wscale
+    # per step: ray records + cuts (set_pose), log, weight max + scale, and per subset the
+    # projector, the back-projector and the update
+    n_launch = args.steps * (2 + 1 + 2 + N_ITER * scan.n_proj * 3)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "medium plain SART: grid (128,512,128) R25 H50, 180 views over 360 deg, "
-                               "256x256 det 0.8 mm, SOD 200 SDD 800, 20 sweeps lambda 0.5, warm start, "
-                               "ROI weights 4x, Poisson I0 1e4",
-                   "l2": "flushed (256 MB write) before every timed step",
-                   "launch": "graph" if args.graph else "eager, CUDA events per kernel",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
-        "grays_per_s": grays, "rel_err_vs_oracle_one_subset": parity,
+        "config": dict(CONFIG_MEDIUM, launch="graph" if args.graph else "eager, CUDA events per kernel",
+                       parallelism="replicas" if world > 1 else "single GPU"),
+        "grays_per_s": grays, "rel_err_vs_oracle_one_subset": parity, "set_pose_ms": set_pose_ms,
         "rel_err_bound": "<=1e-5 rel L2 per projection and per iterate (tests)",
         "wall_s_timed": t_wall, "clocks": clk, "gpu_launches": n_launch,
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
@@ -382,6 +387,7 @@ def main():
         print(json.dumps(line), flush=True)
     plan.close()
     if world > 1:
+        import torch.distributed as dist
         dist.destroy_process_group()
     return 0
 

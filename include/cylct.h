@@ -3,7 +3,7 @@
  *
  * Method: Goethals, Heyndrickx, Boone, "Fast tomographic inspection of cylindrical
  * objects" (J. Nondestructive Evaluation).  Cone-beam X-ray CT reconstructed by SART
- * (Eq. 6) on a cylindrical (N_h, N_theta, N_r) grid attached to the part's own axis
+ * (Eq. 7) on a cylindrical (N_h, N_theta, N_r) grid attached to the part's own axis
  * (Sec. 2, Eq. 1-2), with an initial volume and a weight map (Sec. 2.2, Sec. 3.3).
  *
  * Conventions (the paper leaves them open; every entry point uses these):
@@ -19,7 +19,7 @@
  *     theta_k = 2 pi k / N_theta, slabs h_k = -H/2 + k H / N_h.
  *   - Volumes are [N_h][N_theta][N_r] (r fastest), voxel l = (ih N_theta + it) N_r + ir.
  *     Sinograms are [N_p][H][W] (u fastest).  mu in 1/mm, lengths in mm.
- *   - System matrix (Sec. 2.2, Eq. 5): t_jl = exact length of ray j (source -> pixel
+ *   - System matrix (Sec. 2.2, Eq. 6): t_jl = exact length of ray j (source -> pixel
  *     centre) inside voxel l.
  *
  * Memory and ownership: the caller owns every array argument.  Unless an entry point
@@ -80,7 +80,7 @@ typedef struct cyl_pose {
     double tx, ty, tz;           /* mm */
 } cyl_pose;
 
-/* SART parameters (Eq. 6). */
+/* SART parameters (Eq. 7). */
 typedef struct cyl_sart_params {
     int32_t n_iter;        /* full sweeps over all projections; >= 0 */
     int32_t subset_size;   /* consecutive projections per subset (OS); >= 1 */
@@ -119,18 +119,18 @@ int cyl_plan_destroy(cyl_plan *plan);
  * CYL_EDEVICE. */
 int cyl_plan_set_pose(cyl_plan *plan, const cyl_pose *pose, void *stream);
 
-/* Eq. 5, left side: p = -ln(max(I, 1) / I0) for n detector values.  counts: device
+/* Eq. 6, left side: p = -ln(max(I, 1) / I0) for n detector values.  counts: device
  * array of `in` type; p_out: device array of `out` type; n >= 0.  In-place (counts ==
  * p_out, same dtype) is allowed. */
 int cyl_log_transform(const void *counts, cyl_dtype in, double i0, void *p_out,
                       cyl_dtype out, int64_t n, void *stream);
 
-/* Row sums L_j = sum_l t_jl (the denominator of Eq. 6's row normalisation) of the rays
+/* Row sums L_j = sum_l t_jl (the denominator of Eq. 7's row normalisation) of the rays
  * of projections p0 .. p0+np-1, as the FP64 chord of each ray through the grid cylinder
  * rounded to FP32.  L_out: device float[np][H][W]. */
 int cyl_row_sums(cyl_plan *plan, int32_t p0, int32_t np, float *L_out, void *stream);
 
-/* Forward projection q = A x (Eq. 5 right side) for projections p0 .. p0+np-1.
+/* Forward projection q = A x (Eq. 6 right side) for projections p0 .. p0+np-1.
  * vol: device [N_h][N_theta][N_r] of vol_dtype.  sino_out: device [np][H][W] of
  * sino_dtype (FP32 accumulation, rounded once on store). */
 int cyl_project(cyl_plan *plan, const void *vol, cyl_dtype vol_dtype, int32_t p0,
@@ -156,11 +156,11 @@ int cyl_project_noalloc(cyl_plan *plan, const void *vol, cyl_dtype vol_dtype, in
 /* Matched back-projection out = A^T y over projections p0 .. p0+np-1 (the transpose of
  * exactly the t_jl cyl_project uses; Sec. 2.2 back-projection).  sino: device [np][H][W]
  * of sino_dtype.  vol_out: device float volume, OVERWRITTEN with A^T y.  colsum_out:
- * NULL or device float volume, overwritten with A^T 1 (Eq. 6's column sums). */
+ * NULL or device float volume, overwritten with A^T 1 (Eq. 7's column sums). */
 int cyl_backproject(cyl_plan *plan, const void *sino, cyl_dtype sino_dtype, int32_t p0,
                     int32_t np, float *vol_out, float *colsum_out, void *stream);
 
-/* SART (Eq. 6) over all projections: x0 (warm start, Sec. 2.2 / 3.3 "initial volume";
+/* SART (Eq. 7) over all projections: x0 (warm start, Sec. 2.2 / 3.3 "initial volume";
  * NULL = zeros), weight map w (weighted back-projection, Sec. 2.2; NULL = none; FP32),
  * n_iter sweeps of ordered subsets in index order; the result goes to x_out.
  *   sino:  [N_p][H][W] line integrals of sino_dtype;
@@ -179,7 +179,7 @@ int cyl_sart_solve(cyl_plan *plan, const void *sino, cyl_dtype sino_dtype, const
  * projection count and geometry, all on one device) reconstructed together, each exactly
  * as cyl_sart_solve would with the same params.  A round advances every unfinished scan
  * by one subset: one forward projection and one back-projection launch take the ray
- * pieces of all the round's scans from a shared work counter, then the Eq. 6 update runs
+ * pieces of all the round's scans from a shared work counter, then the Eq. 7 update runs
  * per scan; all rounds are queued as one CUDA graph (params->use_graph).  The plans'
  * piece settings are those of plans[0].
  * Arrays (per scan i, in plan i's layout): sinos[i] of sino_dtype, x0s[i] (x0s or its

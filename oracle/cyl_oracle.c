@@ -8,9 +8,9 @@
  *   - every crossing of a ray with a radial shell, an azimuthal wedge plane and an axial
  *     slab plane is collected, the list is SORTED, and each piece between consecutive
  *     crossings is assigned to the voxel containing its midpoint (definition of t_jl,
- *     Sec. 2.2 below Eq. 5: the intersection length of ray j with voxel l);
+ *     Sec. 2.2 below Eq. 6: the intersection length of ray j with voxel l);
  *   - projection, back-projection and row sums are plain sums over those rows;
- *   - SART follows Eq. 6 literally: residual over the subset, divided by the row sum,
+ *   - SART follows Eq. 7 literally: residual over the subset, divided by the row sum,
  *     back-projected, divided by the column sum over the subset, scaled by lambda.
  * The CUDA path walks crossings incrementally instead of sorting, so the two share no
  * algorithm beyond the geometry both take from the paper.
@@ -349,7 +349,7 @@ int orc_backproject(const orc_setup *s, const double *y, int p0, int np, double 
     return err ? -1 : 0;
 }
 
-/* Eq. 6, one subset at a time:
+/* Eq. 7, one subset at a time:
  *   mu_m += lambda * w_hat_m * [sum_{j in OS} t_jm (p_j - sum_l t_jl mu_l) / sum_l t_jl]
  *                              / [sum_{j in OS} t_jm]. */
 int orc_sart(const orc_setup *s, const double *p, const double *x0, const double *w,

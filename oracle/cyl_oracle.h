@@ -11,8 +11,8 @@
  *   - cylindrical coordinates r, theta, h about the z' axis (Eq. 2, theta read as atan2
  *     in [0, 2 pi));
  *   - the linear model p_j = sum_l t_jl mu_l with t_jl the exact length of ray j inside
- *     voxel l (Sec. 2.2, Eq. 5);
- *   - the SART update of Eq. 6 over ordered subsets of projections.
+ *     voxel l (Sec. 2.2, Eq. 6);
+ *   - the SART update of Eq. 7 over ordered subsets of projections.
  *
  * Conventions the paper leaves open (the same ones the CUDA path documents):
  *   source at (-SOD, 0, 0); detector plane x = SDD - SOD, u along +y, v along +z;
@@ -73,14 +73,14 @@ int orc_row_sums(const orc_setup *s, int p0, int np, double *L);
  * crossings (a voxel entered twice counts twice). */
 int orc_row_nnz(const orc_setup *s, int p0, int np, long *nnz);
 
-/* SART of Eq. 6.  x0 may be NULL (zeros), w may be NULL (all ones).
+/* SART of Eq. 7.  x0 may be NULL (zeros), w may be NULL (all ones).
  * weight_mode 1: w_hat = w / max(w); 0: w_hat = w.  Subsets are runs of subset_size
  * consecutive projections in index order; one iteration is one sweep over all of them. */
 int orc_sart(const orc_setup *s, const double *p, const double *x0, const double *w,
              int n_iter, int subset_size, double lambda, int clamp_nonneg,
              int weight_mode, double *x);
 
-/* Eq. 5 log transform: p = -ln(max(I, 1) / I0), elementwise. */
+/* Eq. 6 log transform: p = -ln(max(I, 1) / I0), elementwise. */
 void orc_log_transform(const double *I, double I0, long n, double *p);
 
 int orc_num_threads(void);

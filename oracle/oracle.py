@@ -3,7 +3,7 @@
 TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the benchmark's CPU
 baseline may call it; the product path never does.  The C source follows the paper's
 definitions directly (Sec. 2 Eq. 1-2 for the pose and cylindrical coordinates, Sec. 2.2
-Eq. 5 for the intersection-length model, Eq. 6 for SART); see the header comment of
+Eq. 6 for the intersection-length model, Eq. 7 for SART); see the header comment of
 ``cyl_oracle.c``.
 """
 from __future__ import annotations
@@ -223,7 +223,7 @@ def row_nnz(s: Setup, p0: int = 0, np_: int | None = None) -> np.ndarray:
 
 def sart(s: Setup, p, x0=None, w=None, n_iter: int = 1, subset_size: int = 1,
          lam: float = 0.5, clamp_nonneg: bool = False, weight_mode: int = 1) -> np.ndarray:
-    """Eq. 6 SART; returns the final volume [N_h][N_theta][N_r]."""
+    """Eq. 7 SART; returns the final volume [N_h][N_theta][N_r]."""
     c, keep = s._c()
     p = _f64(p).reshape(-1)
     assert p.size == s.n_proj * s.n_pix

@@ -1,6 +1,6 @@
 // Batched SART: many scans (own pose, own projection count) reconstructed together.
 //
-// Every scan runs exactly the subsets of its own cyl_sart_solve (Eq. 6, n_iter sweeps in
+// Every scan runs exactly the subsets of its own cyl_sart_solve (Eq. 7, n_iter sweeps in
 // index order); a round advances each unfinished scan by one subset.  A round is three
 // kernels: the forward projection of the scans' current subsets and the back-projection
 // into each scan's (numerator, column sum) accumulator, both persistent grids that take

@@ -48,7 +48,7 @@ constexpr int kSplit = 16;  // pieces per ray recorded at set-up (P divides it)
 constexpr int kPiecesFp = 8, kPiecesBp = 4;   // default pieces per ray of each kernel
 constexpr int kSched = 8;   // ints of scheduler state per plan
 
-// SART update of one subset (Eq. 6): x += scale * w * num / den where den > 0.
+// SART update of one subset (Eq. 7): x += scale * w * num / den where den > 0.
 struct UpdateArgs {
     float *x32;             // FP32 iterate (null in strict 16-bit mode)
     void *x16;              // 16-bit copy / iterate (null in FP32 mode)

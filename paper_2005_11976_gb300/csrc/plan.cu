@@ -1,4 +1,4 @@
-// Plan set-up and the SART solve driver (Eq. 6 over ordered subsets, n_iter sweeps).
+// Plan set-up and the SART solve driver (Eq. 7 over ordered subsets, n_iter sweeps).
 #include <algorithm>
 #include <cstring>
 
@@ -132,7 +132,7 @@ cyl_plan::~cyl_plan()
 
 // One sweep.  Subset k of the sweep uses accumulator b = (parity + k) & 1: forward-
 // project (the kernel also clears accumulator b ^ 1, which the previous subset's update
-// has consumed), back-project the residuals into accumulator b, then apply Eq. 6.  Timed
+// has consumed), back-project the residuals into accumulator b, then apply Eq. 7.  Timed
 // runs record an event before the forward projection, between the kernels and after the
 // update.
 int cyl_plan::queue_sweep(const SolveState &s, cudaStream_t st, bool timed, int parity)

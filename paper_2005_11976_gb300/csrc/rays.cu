@@ -1,4 +1,4 @@
-// Ray-driven kernels of Eq. 6.  Every ray is cut into pieces that hold equal numbers of
+// Ray-driven kernels of Eq. 7.  Every ray is cut into pieces that hold equal numbers of
 // steps (the cuts are found once per pose by walking each ray, k_split), and every piece
 // is one task for one thread.  The warps of a persistent grid take 32 tasks at a time
 // from a work counter.  The long walks of rays through the middle of the grid, where the
@@ -10,10 +10,10 @@
 //             pieces of a ray sit in P adjacent lanes, which add their sums with
 //             shuffles; one lane stores q_j (no atomics, no zeroing of q).
 //   backward: nd_l += (t_jl r_j, t_jl), one packed 2 x FP32 reduction per segment (the
-//             numerator and the column sum of Eq. 6 together), r_j = (p_j - q_j) / L_j.
+//             numerator and the column sum of Eq. 7 together), r_j = (p_j - q_j) / L_j.
 //             A warp task is piece-major: the same piece of 32 adjacent rays, whose
 //             reductions land on neighbouring voxels.
-//   update:   x_l += s w_l num_l / den_l where den_l > 0 (Eq. 6), elementwise
+//   update:   x_l += s w_l num_l / den_l where den_l > 0 (Eq. 7), elementwise
 // The forward kernel also clears the spare accumulator (the one the previous subset's
 // update has consumed), so no separate memset pass is needed.
 #include <algorithm>

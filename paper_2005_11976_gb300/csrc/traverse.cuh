@@ -1,6 +1,6 @@
 // Exact ray traversal of the cylindrical grid (device code).
 //
-// t_jl of Sec. 2.2 (Eq. 5) is the length of ray j inside voxel l.  A voxel of the grid of
+// t_jl of Sec. 2.2 (Eq. 6) is the length of ray j inside voxel l.  A voxel of the grid of
 // Eq. 2 is bounded by two radial shells, two azimuthal wedge half-planes and two axial
 // slab planes, so a ray's row of the system matrix is the list of pieces between
 // consecutive crossings of those three families.  A ray walks them incrementally: it
@@ -40,7 +40,7 @@ constexpr float kTwoPiF = 6.283185307179586f;
 //   a = (P*x, P*y, uref, utan)  uref: u of slab plane kref (or 0 for a ray with e_z = 0)
 //                               utan: |u| of shell boundary kstar
 //   b = (e_x, e_y, e_z, d^2)
-//   c = (u_in, u_out, L, packed) L: chord in the grid cylinder (row sum of Eq. 6);
+//   c = (u_in, u_out, L, packed) L: chord in the grid cylinder (row sum of Eq. 7);
 //                               u_in > u_out marks a ray that misses the grid;
 //                               packed = kstar | kref << 16, kstar = 0xffff for a ray
 //                               parallel to the axis; kref: the slab plane nearest the

@@ -12,7 +12,7 @@ cylindrical grid of Sec. 2, Eq. 2), as an intersection of parameter intervals:
 * the wedge is the intersection of two half-planes for N_theta >= 3, one half-plane for
   N_theta = 2 and the whole plane for N_theta = 1.
 
-The entry t_jl (Sec. 2.2, definition below Eq. 5) is the total length of the result.
+The entry t_jl (Sec. 2.2, definition below Eq. 6) is the total length of the result.
 Ray geometry (source and pixel positions) is restated here from the stated conventions
 without calling the oracle.
 """

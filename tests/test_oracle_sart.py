@@ -1,4 +1,4 @@
-"""Pins of the oracle's SART (Eq. 6) by properties that any correct SART has."""
+"""Pins of the oracle's SART (Eq. 7) by properties that any correct SART has."""
 import dataclasses
 import math
 
@@ -34,7 +34,7 @@ def test_single_voxel_by_hand(orc):
 
 @pytest.mark.parametrize("lam", [1.0, 0.5])
 def test_one_ray_subset_moves_residual_by_lambda(orc, lam):
-    # a subset of one ray: Eq. 6 adds lam * r / L to every voxel the ray crosses, so that
+    # a subset of one ray: Eq. 7 adds lam * r / L to every voxel the ray crosses, so that
     # ray's residual is multiplied by exactly (1 - lam)
     s = one_ray_scan()
     rng = np.random.default_rng(4)
