@@ -9,10 +9,11 @@
 //   forward:  q_j = sum over the ray of t_jl x_l.  A warp task is ray-major: the P
 //             pieces of a ray sit in P adjacent lanes, which add their sums with
 //             shuffles; one lane stores q_j (no atomics, no zeroing of q).
-//   backward: nd_l += (t_jl r_j, t_jl), one packed 2 x FP32 reduction per segment (the
-//             numerator and the column sum of Eq. 7 together), r_j = (p_j - q_j) / L_j.
-//             A warp task is piece-major: the same piece of 32 adjacent rays, whose
-//             reductions land on neighbouring voxels.
+//   backward: nd_l += (t_jl r_j, t_jl), a packed 2 x FP32 reduction per segment (the
+//             numerator and the column sum of Eq. 7 together), r_j = (p_j - q_j) / L_j;
+//             two consecutive segments in the two halves of one 16-byte voxel pair go
+//             out as one 4 x FP32 reduction.  A warp task is piece-major: the same piece
+//             of 32 adjacent rays, whose reductions land on neighbouring voxels.
 //   update:   x_l += s w_l num_l / den_l where den_l > 0 (Eq. 7), elementwise
 // The forward kernel also clears the spare accumulator (the one the previous subset's
 // update has consumed), so no separate memset pass is needed.
@@ -37,12 +38,19 @@ template <> __device__ __forceinline__ float from_f32r<float>(float v) { return 
 template <> __device__ __forceinline__ __half from_f32r<__half>(float v) { return __float2half_rn(v); }
 template <> __device__ __forceinline__ __nv_bfloat16 from_f32r<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
 
-// *p += (a, len) when len > 0, as one predicated packed reduction (no branch)
-__device__ __forceinline__ void red_add2_pos(float2 *p, float a, float len)
+// Predicated packed reductions (the predicate is evaluated in PTX: no branch).
+__device__ __forceinline__ void red_add2_if(bool c, float2 *p, float a, float b)
 {
-    asm volatile("{\n\t.reg .pred q;\n\tsetp.gt.f32 q, %2, 0f00000000;\n\t"
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %3, 0;\n\t"
                  "@q red.global.add.v2.f32 [%0], {%1, %2};\n\t}"
-                 ::"l"(p), "f"(a), "f"(len) : "memory");
+                 ::"l"(p), "f"(a), "f"(b), "r"((unsigned)c) : "memory");
+}
+
+__device__ __forceinline__ void red_add4_if(bool c, float2 *p, float a, float b, float d, float e)
+{
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %5, 0;\n\t"
+                 "@q red.global.add.v4.f32 [%0], {%1, %2, %3, %4};\n\t}"
+                 ::"l"(p), "f"(a), "f"(b), "f"(d), "f"(e), "r"((unsigned)c) : "memory");
 }
 
 __device__ __forceinline__ void stage_trig_smem(const float2 *trig, int n_t, float2 *s)
@@ -70,7 +78,9 @@ __device__ __forceinline__ void zero_slice(float2 *buf, int64_t len, int64_t tid
 
 // sched[0] hands out warp tasks; sched[1] counts the warps that found no work left, and
 // the last of them resets both, so the pair is zero again for the next launch on the
-// stream.  Every warp of the grid calls retire() exactly once, after its last fetch.
+// stream.  Every warp of the grid calls retire() exactly once, after its last fetch has
+// returned, so no fetch can follow the reset; no fence is needed (the kernel's end
+// orders its memory operations before the next launch).
 __device__ __forceinline__ int fetch_task(int *sched)
 {
     int v = 0;
@@ -81,7 +91,6 @@ __device__ __forceinline__ int fetch_task(int *sched)
 __device__ __forceinline__ void retire(int *sched)
 {
     if ((threadIdx.x & 31) == 0) {
-        __threadfence();
         const unsigned total = gridDim.x * (blockDim.x >> 5);
         if ((unsigned)atomicAdd(sched + 1, 1) == total - 1) {
             atomicExch(sched, 0);
@@ -142,9 +151,25 @@ __device__ __forceinline__ void bp_walk(const GridDev &g, const float2 *__restri
     Walker w;
     w.init(g, trig, rr, ua, ub);
     if (nd) {
-        auto op = [&](int idx, float len) { red_add2_pos(nd + idx, len * yv, len); };
+        // a segment waits one step: if the next one lands in the other half of the same
+        // 16-byte voxel pair, both go out as one 4 x FP32 reduction
+        int pidx = -1;
+        float pa = 0.f, pl = 0.f;
+        auto op = [&](int idx, float len) {
+            const float a = len * yv;
+            const bool has = len > 0.f;
+            const bool pair = has && pidx >= 0 && idx != pidx && (idx >> 1) == (pidx >> 1);
+            const bool lo = (idx & 1) == 0;
+            red_add4_if(pair, nd + (idx & ~1), lo ? a : pa, lo ? len : pl, lo ? pa : a, lo ? pl : len);
+            red_add2_if(has && !pair && pidx >= 0, nd + (pidx < 0 ? 0 : pidx), pa, pl);
+            const bool take = has && !pair;
+            pidx = pair ? -1 : (take ? idx : pidx);
+            pa = take ? a : pa;
+            pl = take ? len : pl;
+        };
         while (w.step(g, trig, op)) {
         }
+        red_add2_if(pidx >= 0, nd + (pidx < 0 ? 0 : pidx), pa, pl);
     } else {
         auto op = [&](int idx, float len) {
             if (len > 0.f) {

@@ -240,9 +240,9 @@ struct Walker {
         kh_hi = (float)(g.n_h - kref);
         hstep = (ez > 0.f ? 1 : -1) * g.n_t * g.n_r;
         ur = shell_u(ks);
+        if (!wedges) kt = 0;
         ut = wedges ? wedge_u(trig, kt) : kInf;
         uh = slab_u(kh);
-        if (!wedges) kt = -1;
     }
 
     // One piece: calls op(idx, length); returns false once the ray has reached ub (or
@@ -271,7 +271,7 @@ struct Walker {
         kh = ish ? kh + hsign : kh;
         // its next crossing
         const float urn = shell_u(ks);
-        const float utn = wedge_u(trig, max(kt, 0));
+        const float utn = wedge_u(trig, kt);
         const float uhn = slab_u(kh);
         ur = isr ? urn : ur;
         ut = ist ? utn : ut;
