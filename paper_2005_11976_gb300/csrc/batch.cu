@@ -152,14 +152,15 @@ extern "C" int cyl_sart_solve_batch(int32_t n, cyl_plan *const *plans, const voi
         u.strict16 = 0;
         if (x_dtype == CYL_F32) {
             u.x32 = (float *)xo;
-        } else {
+        } else if (prm->strict_16bit) {
             u.x16 = xo;
-            u.strict16 = prm->strict_16bit ? 1 : 0;
-            if (!u.strict16) {
-                if ((rc = pl->ensure((void **)&pl->d_x32, pl->x32_cap, sizeof(float) * pl->n_vox))) return rc;
-                u.x32 = pl->d_x32;
-                BT_CUDA(launch_convert(xo, x_dtype, pl->d_x32, CYL_F32, pl->n_vox, bs));
-            }
+            u.strict16 = 1;
+        } else {
+            // FP32 iterate, read by the projector; rounded to x_dtype after the last round
+            if ((rc = pl->ensure((void **)&pl->d_x32, pl->x32_cap, sizeof(float) * pl->n_vox))) return rc;
+            u.x32 = pl->d_x32;
+            sc.x_proj = pl->d_x32;
+            BT_CUDA(launch_convert(xo, x_dtype, pl->d_x32, CYL_F32, pl->n_vox, bs));
         }
         u.w = w;
         u.wscale = w ? pl->d_wscale : nullptr;
@@ -188,14 +189,16 @@ extern "C" int cyl_sart_solve_batch(int32_t n, cyl_plan *const *plans, const voi
         BT_CUDA(cudaMemcpyAsync(d_scans, scans.data(), b_scans, cudaMemcpyHostToDevice, bs));
         BT_CUDA(cudaMemcpyAsync(d_items, items.data(), b_items, cudaMemcpyHostToDevice, bs));
         BT_CUDA(cudaMemcpyAsync(d_n, n_items.data(), b_n, cudaMemcpyHostToDevice, bs));
-        const cyl_dtype x16t = x_dtype == CYL_F32 ? CYL_F32 : x_dtype;
+        // projector and update types: the 16-bit iterate in strict mode, else FP32
+        const bool strict = x_dtype != CYL_F32 && prm->strict_16bit;
+        const cyl_dtype xt = strict ? x_dtype : CYL_F32, x16t = xt;
         if (prm->use_graph) {
             cudaGraph_t graph = nullptr;
             cudaGraphExec_t exec = nullptr;
             BT_CUDA(cudaStreamBeginCapture(bs, cudaStreamCaptureModeThreadLocal));
             cudaError_t ce = cudaSuccess;
             for (int r = 0; r < rounds && ce == cudaSuccess; ++r)
-                ce = launch_batch_round(d_scans, d_items, d_n, n, r, max_vox, P, d_sched, x_dtype,
+                ce = launch_batch_round(d_scans, d_items, d_n, n, r, max_vox, P, d_sched, xt,
                                         sino_dtype, x16t, bs);
             cudaError_t ee = cudaStreamEndCapture(bs, &graph);
             if (ce != cudaSuccess) {
@@ -211,11 +214,14 @@ extern "C" int cyl_sart_solve_batch(int32_t n, cyl_plan *const *plans, const voi
             if (ce != cudaSuccess) return cuda_error(ce, "cudaGraphLaunch");
         } else {
             for (int r = 0; r < rounds; ++r)
-                BT_CUDA(launch_batch_round(d_scans, d_items, d_n, n, r, max_vox, P, d_sched, x_dtype,
+                BT_CUDA(launch_batch_round(d_scans, d_items, d_n, n, r, max_vox, P, d_sched, xt,
                                            sino_dtype, x16t, bs));
         }
         BT_CUDA(cudaFreeAsync(d_blob, bs));
     }
+    if (x_dtype != CYL_F32 && !prm->strict_16bit)
+        for (int i = 0; i < n; ++i)
+            BT_CUDA(launch_convert(plans[i]->d_x32, CYL_F32, x_outs[i], x_dtype, plans[i]->n_vox, bs));
     BT_CUDA(cudaEventRecord(plans[0]->ev_out, bs));
     BT_CUDA(cudaStreamWaitEvent(user, plans[0]->ev_out, 0));
     for (int i = 1; i < n; ++i) BT_CUDA(cudaStreamWaitEvent(plans[i]->ws, plans[0]->ev_out, 0));

@@ -218,17 +218,21 @@ int cyl_plan::solve(const void *sino, cyl_dtype sino_t, const void *x0, const fl
         s.x32 = (float *)d_xo;
         s.x_proj = d_xo;
         s.x_proj_t = CYL_F32;
-    } else {
+    } else if (prm.strict_16bit) {
+        // the iterate itself is 16-bit: the projector reads it, every update rounds it
         s.x16 = d_xo;
         s.x16_t = x_t;
         s.x_proj = d_xo;
         s.x_proj_t = x_t;
-        s.strict16 = prm.strict_16bit ? 1 : 0;
-        if (!s.strict16) {
-            if ((rc = ensure((void **)&d_x32, x32_cap, sizeof(float) * n_vox))) return rc;
-            s.x32 = d_x32;
-            PL_CUDA(launch_convert(d_xo, x_t, d_x32, CYL_F32, n_vox, ws));
-        }
+        s.strict16 = 1;
+    } else {
+        // 16-bit storage of the warm start and the result around an FP32 iterate, which
+        // the projector reads; the result is rounded once, after the last sweep
+        if ((rc = ensure((void **)&d_x32, x32_cap, sizeof(float) * n_vox))) return rc;
+        s.x32 = d_x32;
+        s.x_proj = d_x32;
+        s.x_proj_t = CYL_F32;
+        PL_CUDA(launch_convert(d_xo, x_t, d_x32, CYL_F32, n_vox, ws));
     }
     if (d_w) PL_CUDA(launch_weight_scale(d_w, n_vox, prm.weight_mode, (float)prm.lambda, d_wscale, ws));
     for (int k = 0; k < 2; ++k) PL_CUDA(cudaMemsetAsync(d_nd[k], 0, sizeof(float2) * n_vox, ws));
@@ -268,6 +272,7 @@ int cyl_plan::solve(const void *sino, cyl_dtype sino_t, const void *x0, const fl
             if ((rc = queue_sweep(s, ws, false, (it * n_sub) & 1))) return rc;
     }
 
+    if (x_t != CYL_F32 && !s.strict16) PL_CUDA(launch_convert(d_x32, CYL_F32, d_xo, x_t, n_vox, ws));
     if (kxo == kHost) PL_CUDA(cudaMemcpyAsync(x_out, d_xo, xb * n_vox, cudaMemcpyDeviceToHost, ws));
     PL_CUDA(cudaEventRecord(ev_out, ws));
     PL_CUDA(cudaStreamWaitEvent(user, ev_out, 0));

@@ -220,6 +220,13 @@ int cyl_server::admit(const std::shared_ptr<Scan> &s)
     s->n_sub = (n_proj + subset - 1) / subset;
     s->rounds_total = cfg.n_iter * s->n_sub;
     s->rounds_done = 0;
+    if (s->rounds_total == 0) {        // no sweep: the result is the warm start
+        if (s->own_x && cudaMemcpyAsync(s->req.x_out, s->d_x, (size_t)pl->n_vox * sb,
+                                        cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            return set_error(CYL_EDEVICE, "result copy");
+        if (cudaEventRecord(s->done_ev, st) != cudaSuccess) return set_error(CYL_EDEVICE, "event");
+        s->state = 2;
+    }
     return CYL_OK;
 }
 
@@ -278,7 +285,7 @@ int cyl_server::run_round()
         BatchScan sc{};
         sc.sd = pl->scan_dev();
         sc.sino = s->d_sino;
-        sc.x_proj = s->d_x;
+        sc.x_proj = cfg.storage == CYL_F32 ? s->d_x : s->d_x32;   // the FP32 iterate
         sc.q[0] = pl->d_q;
         sc.q[1] = pl->d_q + (size_t)subset * pl->n_pix;
         sc.q_len = (int64_t)subset * pl->n_pix;
@@ -286,7 +293,7 @@ int cyl_server::run_round()
         sc.nd[1] = pl->d_nd[1];
         sc.nd_len = pl->n_vox;
         sc.upd.x32 = cfg.storage == CYL_F32 ? static_cast<float *>(s->d_x) : s->d_x32;
-        sc.upd.x16 = cfg.storage == CYL_F32 ? nullptr : s->d_x;
+        sc.upd.x16 = nullptr;               // the result is rounded once, at the end
         sc.upd.x16_t = cfg.storage;
         sc.upd.strict16 = 0;
         sc.upd.w = pt.d_w;
@@ -316,11 +323,13 @@ int cyl_server::run_round()
     if (cudaEventRecord(slot_ev[slot], st) != cudaSuccess) return set_error(CYL_EDEVICE, "event");
     cudaError_t e = launch_batch_round(reinterpret_cast<BatchScan *>(d), reinterpret_cast<BatchItem *>(d + b_scans),
                                        reinterpret_cast<int *>(d + b_scans + b_items), n, 0, max_vox, P,
-                                       d_sched, cfg.storage, cfg.storage, cfg.storage, st);
+                                       d_sched, CYL_F32, cfg.storage, CYL_F32, st);
     if (e != cudaSuccess) return cuda_error(e, "round launch");
     ++stats.rounds;
     for (auto &s : members) {
         if (++s->rounds_done == s->rounds_total) {
+            if (cfg.storage != CYL_F32)
+                launch_convert(s->d_x32, CYL_F32, s->d_x, cfg.storage, s->plan->n_vox, st);
             if (s->own_x)
                 cudaMemcpyAsync(s->req.x_out, s->d_x, (size_t)s->plan->n_vox * dtype_size(cfg.storage),
                                 cudaMemcpyDeviceToHost, st);

@@ -333,3 +333,24 @@ def test_medium_single_view_projection_and_subset(lib, orc):
     ref = orc.sart(o, p, x0=x, w=w, n_iter=1, lam=0.5)
     assert gu.rel_l2(got - x, ref - x) <= TOL_FP32 * 10
     assert gu.rel_l2(got, ref) <= TOL_FP32
+
+
+@pytest.mark.parametrize("vol_dt", [cylct.CYL_F16, cylct.CYL_BF16])
+def test_precision_size_single_view_projection(lib, orc, vol_dt):
+    # full precision-variant grid (256, 1024, 256) and 512^2 detector, volume stored in
+    # 16 bits; one view so the oracle finishes in seconds.  The oracle projects the same
+    # rounded volume, so the bound is the FP32 one.
+    import torch
+    full = synth.precision_scan(synth.rng_for("precision"))
+    s = dataclasses.replace(full, angles=full.angles[101:102])
+    az = synth.insert_azimuths(synth.rng_for("precision"))
+    x = synth.part_phantom(s, az)
+    tdt = torch.float16 if vol_dt == cylct.CYL_F16 else torch.bfloat16
+    x16 = torch.from_numpy(x.astype(np.float32)).to(tdt)
+    ref = orc.project(osetup(orc, s), x16.float().numpy().astype(np.float64))
+    with cylct.Plan(s) as plan:
+        out = torch.empty(s.sino_shape, dtype=torch.float32, device="cuda")
+        plan.cyl_project(x16.cuda(), vol_dt, 0, 1, out, cylct.CYL_F32)
+        got = gu.to_np(out)
+    assert gu.rel_l2(got, ref) <= TOL_FP32
+

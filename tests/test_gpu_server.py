@@ -135,3 +135,17 @@ def test_bf16_storage(lib):
         solo = alone(s, gu.to_np(sinos[k]), x0, parts[part][2], cylct.CYL_BF16)
         assert gu.rel_l2(gu.to_np(outs[k]), solo) <= 2.5e-3, k
     srv.close()
+
+
+def test_zero_sweeps_return_the_warm_start(lib):
+    srv = cylct.Server(8 << 30, n_iter=0, lam=0.5)
+    x0 = np.random.default_rng(2).uniform(0.0, 0.05, size=PART_A.vol_shape)
+    pid = srv.cyl_server_add_part(PART_A, gu.to_dev(x0), None)
+    s = request_scan(PART_A, 3, (0.1, 0.02, 0.3, 0.1, 0.0, -0.1), 0.0)
+    out = np.zeros(s.vol_shape, np.float32)
+    t = srv.cyl_submit(pid, (s.alpha, s.beta, s.gamma, s.tx, s.ty, s.tz), s.angles,
+                       np.ones(s.sino_shape, np.float32), out)
+    assert srv.cyl_wait(t, 60000)[0] == cylct.CYL_OK
+    assert np.array_equal(out, x0.astype(np.float32))
+    srv.close()
+
