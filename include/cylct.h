@@ -281,9 +281,12 @@ int cyl_count_segments(cyl_plan *plan, int32_t p0, int32_t np, int64_t *counts_o
                        void *stream);
 
 /* Per-kernel device time of the plan's last cyl_sart_solve run with timing enabled.
- * kind: 0 forward projection, 1 back-projection, 2 update.  Timing adds a CUDA event
- * pair around every launch of that solve (eager launches, no graph).  ms_total and
- * launches receive the sum of event durations and the number of launches. */
+ * kind: 0 forward projection, 1 back-projection, 2 update.  Timing records a CUDA event
+ * between every two launches of a sweep.  With params->use_graph (and one captured
+ * graph: an even number of subsets, or one sweep) the events are captured into the
+ * sweep's graph and the times are those of the solve's last sweep; otherwise the
+ * launches are eager and the times cover every sweep.  ms_total and launches receive
+ * the sum of event durations and the number of launches timed. */
 int cyl_plan_set_timing(cyl_plan *plan, int enable);
 int cyl_plan_kernel_time(cyl_plan *plan, int kind, double *ms_total, int64_t *launches);
 

@@ -83,7 +83,8 @@ void cyl_plan::drop_graphs()
 {
     if (gexec) cudaGraphExecDestroy(gexec);
     if (gexec_odd) cudaGraphExecDestroy(gexec_odd);
-    gexec = gexec_odd = nullptr;
+    if (gexec_timed) cudaGraphExecDestroy(gexec_timed);
+    gexec = gexec_odd = gexec_timed = nullptr;
 }
 
 int cyl_plan::ensure(void **p, size_t &cap, size_t nbytes)
@@ -147,6 +148,10 @@ int cyl_plan::queue_sweep(const SolveState &s, cudaStream_t st, bool timed, int 
     upd.wscale = s.w ? d_wscale : nullptr;
     upd.lambda = (float)s.lambda;
     upd.clamp = s.clamp;
+    // timing events captured into a graph must be external records to be timed
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (timed) PL_CUDA(cudaStreamIsCapturing(st, &cap));
+    const unsigned rec_flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
     int k = 0;
     for (int p0 = 0; p0 < geom.n_proj; p0 += s.subset, ++k) {
         const int np = std::min(s.subset, geom.n_proj - p0);
@@ -154,13 +159,13 @@ int cyl_plan::queue_sweep(const SolveState &s, cudaStream_t st, bool timed, int 
         const void *sino_p = static_cast<const char *>(s.sino) + (size_t)p0 * n_pix * dtype_size(s.sino_t);
         cudaEvent_t *ev = timed ? next_events(4) : nullptr;
         if (timed && !ev) return set_error(CYL_EDEVICE, "event creation failed");
-        if (ev) PL_CUDA(cudaEventRecord(ev[0], st));
+        if (ev) PL_CUDA(cudaEventRecordWithFlags(ev[0], st, rec_flags));
         PL_CUDA(launch_fp_rays(sd, p_fp, p0, np, s.x_proj, s.x_proj_t, d_q, d_nd[b ^ 1], n_vox, st));
-        if (ev) PL_CUDA(cudaEventRecord(ev[1], st));
+        if (ev) PL_CUDA(cudaEventRecordWithFlags(ev[1], st, rec_flags));
         PL_CUDA(launch_bp_rays(sd, p_bp, p0, np, sino_p, s.sino_t, d_q, d_nd[b], nullptr, nullptr, st));
-        if (ev) PL_CUDA(cudaEventRecord(ev[2], st));
+        if (ev) PL_CUDA(cudaEventRecordWithFlags(ev[2], st, rec_flags));
         PL_CUDA(launch_update_nd(n_vox, d_nd[b], upd, st));
-        if (ev) PL_CUDA(cudaEventRecord(ev[3], st));
+        if (ev) PL_CUDA(cudaEventRecordWithFlags(ev[3], st, rec_flags));
     }
     return CYL_OK;
 }
@@ -237,7 +242,32 @@ int cyl_plan::solve(const void *sino, cyl_dtype sino_t, const void *x0, const fl
     if (d_w) PL_CUDA(launch_weight_scale(d_w, n_vox, prm.weight_mode, (float)prm.lambda, d_wscale, ws));
     for (int k = 0; k < 2; ++k) PL_CUDA(cudaMemsetAsync(d_nd[k], 0, sizeof(float2) * n_vox, ws));
 
-    if (timing) {
+    const bool one_graph = !(n_sub & 1) || prm.n_iter == 1;
+    if (timing && prm.use_graph && prm.n_iter > 0 && one_graph) {
+        // one captured sweep with its timing events: every launch re-records them, so
+        // after the solve they hold the kernel times of the last sweep
+        if (!gexec_timed || !(gkey_timed == s)) {
+            if (gexec_timed) cudaGraphExecDestroy(gexec_timed);
+            gexec_timed = nullptr;
+            ev_used = 0;
+            cudaGraph_t graph = nullptr;
+            PL_CUDA(cudaStreamBeginCapture(ws, cudaStreamCaptureModeThreadLocal));
+            rc = queue_sweep(s, ws, true, 0);
+            cudaError_t ce = cudaStreamEndCapture(ws, &graph);
+            if (rc) {
+                if (graph) cudaGraphDestroy(graph);
+                return rc;
+            }
+            if (ce != cudaSuccess) return cuda_error(ce, "cudaStreamEndCapture");
+            ce = cudaGraphInstantiate(&gexec_timed, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ce != cudaSuccess) return cuda_error(ce, "cudaGraphInstantiate");
+            gkey_timed = s;
+            ev_timed = ev_used;
+        }
+        ev_used = ev_timed;
+        for (int it = 0; it < prm.n_iter; ++it) PL_CUDA(cudaGraphLaunch(gexec_timed, ws));
+    } else if (timing) {
         ev_used = 0;
         for (int it = 0; it < prm.n_iter; ++it)
             if ((rc = queue_sweep(s, ws, true, (it * n_sub) & 1))) return rc;

@@ -84,6 +84,10 @@ struct cyl_plan {
     // captured sweeps, one per parity of the subset counter at the sweep's start
     cudaGraphExec_t gexec = nullptr, gexec_odd = nullptr;
     cylct::SolveState gkey{};
+    // captured sweep with timing events (timing mode with graphs)
+    cudaGraphExec_t gexec_timed = nullptr;
+    cylct::SolveState gkey_timed{};
+    size_t ev_timed = 0;           // events captured in gexec_timed (events[0 .. ev_timed))
 
     std::mutex mu;
     std::vector<void *> allocs;
