@@ -36,7 +36,7 @@ UNIT = "SART iters/s"
 N_ITER = 20
 # DRAM bytes (read + write) per launch of each kernel at the medium workload, from one ncu
 # capture of the current kernels (profiles/sart_medium_kernels.md).
-TRAFFIC: dict = {"k_fp": 73.0e6, "k_bp": 83.2e6, "k_update_nd": 145.4e6}
+TRAFFIC: dict = {"k_fp": 73.3e6, "k_bp": 82.9e6, "k_update_nd": 145.8e6}
 LAMBDA = 0.5
 I0 = 1.0e4
 CONFIG_MEDIUM = {
