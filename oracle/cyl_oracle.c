@@ -83,6 +83,18 @@ void orc_ray(const orc_setup *s, int p, int iu, int iv, double S[3], double D[3]
 {
     double src[3] = {-s->sod, 0.0, 0.0};
     double pix[3];
+    if (s->frames) {
+        /* general trajectory: the projection's own source and detector, no stage turn */
+        const double *f = s->frames + 12 * (long)p;
+        int k;
+        for (k = 0; k < 3; ++k) {
+            src[k] = f[k];
+            pix[k] = f[3 + k] + iu * f[6 + k] + iv * f[9 + k];
+        }
+        lab_to_object(s, 0.0, src, S);
+        lab_to_object(s, 0.0, pix, D);
+        return;
+    }
     pix[0] = s->sdd - s->sod;
     pix[1] = (iu - 0.5 * (s->det_w - 1)) * s->pitch_u + s->off_u;
     pix[2] = (iv - 0.5 * (s->det_h - 1)) * s->pitch_v + s->off_v;

@@ -40,6 +40,9 @@ typedef struct {
     const double *angles;       /* n_proj stage angles phi_p, radians */
     double alpha, beta, gamma;  /* zxz Euler angles, radians */
     double tx, ty, tz;          /* object position T in stage coordinates, mm */
+    const double *frames;       /* NULL (circular scan), or n_proj x 12 lab-frame source S,
+                                   pixel (0, 0) centre D0 and pixel steps du, dv, mm: a
+                                   general trajectory, no stage rotation */
 } orc_setup;
 
 /* Alignment matrix R of X' = R X + T, row-major: the transpose of the object's

@@ -49,6 +49,7 @@ class _COrcSetup(ctypes.Structure):
         ("angles", ctypes.POINTER(ctypes.c_double)),
         ("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("gamma", ctypes.c_double),
         ("tx", ctypes.c_double), ("ty", ctypes.c_double), ("tz", ctypes.c_double),
+        ("frames", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -86,7 +87,9 @@ def load():
 
 @dataclasses.dataclass
 class Setup:
-    """Grid, circular cone-beam geometry and pose of one scan (lengths in mm)."""
+    """Grid, cone-beam geometry and pose of one scan (lengths in mm).  ``frames``, when
+    given, is an (n_proj, 12) array of lab-frame source, pixel (0, 0) centre and pixel
+    steps du, dv per projection (a general trajectory: the circular fields are unused)."""
     n_h: int
     n_theta: int
     n_r: int
@@ -107,10 +110,11 @@ class Setup:
     tx: float = 0.0
     ty: float = 0.0
     tz: float = 0.0
+    frames: np.ndarray | None = None
 
     @property
     def n_proj(self) -> int:
-        return int(len(self.angles))
+        return int(len(self.frames)) if self.frames is not None else int(len(self.angles))
 
     @property
     def n_vox(self) -> int:
@@ -121,13 +125,15 @@ class Setup:
         return self.det_w * self.det_h
 
     def _c(self):
-        ang = np.ascontiguousarray(self.angles, dtype=np.float64)
+        n = self.n_proj
+        ang = np.ascontiguousarray(self.angles if self.frames is None else np.zeros(n), dtype=np.float64)
+        fr = None if self.frames is None else np.ascontiguousarray(self.frames, dtype=np.float64).reshape(n, 12)
         c = _COrcSetup(
             self.n_h, self.n_theta, self.n_r, self.radius, self.height, self.sod, self.sdd,
-            self.n_proj, self.det_w, self.det_h, self.pitch_u, self.pitch_v, self.off_u,
+            n, self.det_w, self.det_h, self.pitch_u, self.pitch_v, self.off_u,
             self.off_v, ang.ctypes.data_as(_D), self.alpha, self.beta, self.gamma,
-            self.tx, self.ty, self.tz)
-        return c, ang  # keep the angle array alive alongside the struct
+            self.tx, self.ty, self.tz, fr.ctypes.data_as(_D) if fr is not None else None)
+        return c, (ang, fr)  # keep the arrays alive alongside the struct
 
 
 def _dptr(a):

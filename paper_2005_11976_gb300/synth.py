@@ -60,10 +60,11 @@ class Scan:
     tx: float = 0.0
     ty: float = 0.0
     tz: float = 0.0
+    frames: np.ndarray | None = None   # (n_proj, 12) general trajectory, or None (circular)
 
     @property
     def n_proj(self) -> int:
-        return int(len(self.angles))
+        return int(len(self.frames)) if self.frames is not None else int(len(self.angles))
 
     @property
     def vol_shape(self):
@@ -97,6 +98,38 @@ def full_circle(n_proj: int) -> np.ndarray:
 def limited_arc(n_proj: int, last_angle_deg: float) -> np.ndarray:
     """n_proj angles from 0 to the last scan angle inclusive (the Table 1 style of scan)."""
     return np.deg2rad(last_angle_deg) * np.arange(n_proj) / max(n_proj - 1, 1)
+
+
+def frames_from_circular(scan: Scan) -> np.ndarray:
+    """The (n_proj, 12) frames (source, pixel (0, 0) centre, pixel steps du, dv, in stage
+    coordinates) of a circular scan: the stage turn of each projection applied to the
+    fixed source and detector."""
+    out = np.zeros((scan.n_proj, 12))
+    u0 = -0.5 * (scan.det_w - 1) * scan.pitch_u + scan.off_u
+    v0 = -0.5 * (scan.det_h - 1) * scan.pitch_v + scan.off_v
+    for p, phi in enumerate(scan.angles):
+        c, s_ = math.cos(phi), math.sin(phi)
+        rot = lambda v: (c * v[0] + s_ * v[1], -s_ * v[0] + c * v[1], v[2])
+        out[p, 0:3] = rot((-scan.sod, 0.0, 0.0))
+        out[p, 3:6] = rot((scan.sdd - scan.sod, u0, v0))
+        out[p, 6:9] = rot((0.0, scan.pitch_u, 0.0))
+        out[p, 9:12] = rot((0.0, 0.0, scan.pitch_v))
+    return out
+
+
+def conveyor_frames(n_proj: int, sod: float, sdd: float, det_w: int, det_h: int, pitch: float,
+                    travel: float) -> np.ndarray:
+    """A part carried along +y on a belt through a fixed cone beam: in the part's stage
+    frame the source and the detector move along -y, over `travel` mm centred on the axis."""
+    out = np.zeros((n_proj, 12))
+    u0 = -0.5 * (det_w - 1) * pitch
+    v0 = -0.5 * (det_h - 1) * pitch
+    for p, y in enumerate(np.linspace(-0.5 * travel, 0.5 * travel, n_proj)):
+        out[p, 0:3] = (-sod, -y, 0.0)
+        out[p, 3:6] = (sdd - sod, u0 - y, v0)
+        out[p, 6:9] = (0.0, pitch, 0.0)
+        out[p, 9:12] = (0.0, 0.0, pitch)
+    return out
 
 
 # --------------------------------------------------------------------------- scans

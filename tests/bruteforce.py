@@ -47,8 +47,19 @@ def rays(scan):
     pix[..., 1] = u[None, :]
     pix[..., 2] = v[:, None]
     src = np.array([-scan.sod, 0.0, 0.0])
-    S = np.zeros((len(scan.angles), scan.det_h, scan.det_w, 3))
+    frames = getattr(scan, "frames", None)
+    n = len(frames) if frames is not None else len(scan.angles)
+    S = np.zeros((n, scan.det_h, scan.det_w, 3))
     D = np.zeros_like(S)
+    if frames is not None:
+        # general trajectory: each projection's own source and detector, in stage
+        # coordinates (no stage turn)
+        for p in range(n):
+            f = np.asarray(frames[p], dtype=np.float64)
+            pts = f[3:6][None, None, :] + iu[None, :, None] * f[6:9] + iv[:, None, None] * f[9:12]
+            S[p] = R @ (f[0:3] - T)
+            D[p] = (pts - T) @ R.T
+        return S, D
     for p, phi in enumerate(scan.angles):
         # lab -> stage (rotate by -phi) -> object: X' = R (X - T)
         S[p] = R @ (rot_z(-phi) @ src - T)

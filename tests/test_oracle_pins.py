@@ -312,3 +312,50 @@ def test_log_transform_closed_form(orc):
     np.testing.assert_allclose(orc.log_transform(I, I0), p_true, atol=1e-12)
     # counts below one are clamped to one count
     assert math.isclose(orc.log_transform(np.array([0.0]), I0)[0], math.log(I0))
+
+
+# ------------------------------------------------------ general trajectories (frames)
+
+def test_frames_of_a_circular_scan_reproduce_it(orc):
+    # the frames of a circular scan (its stage turns applied to source and detector) must
+    # give the circular scan's rays and projections exactly
+    scan = small_scan(3, 8, 3, n_proj=5)
+    fscan = dataclasses.replace(scan, frames=synth.frames_from_circular(scan))
+    o, of = osetup(orc, scan), osetup(orc, fscan)
+    for p in range(scan.n_proj):
+        for iu, iv in ((0, 0), (3, 5), (7, 7)):
+            a, b = orc.ray(o, p, iu, iv), orc.ray(of, p, iu, iv)
+            np.testing.assert_allclose(b[0], a[0], atol=1e-12)
+            np.testing.assert_allclose(b[1], a[1], atol=1e-12)
+    x = np.random.default_rng(4).uniform(0.0, 0.05, size=scan.vol_shape)
+    np.testing.assert_allclose(orc.project(of, x), orc.project(o, x), rtol=0, atol=1e-12)
+
+
+def conveyor_scan(n_proj=6, det=12, grid=(3, 8, 4)):
+    s = synth.Scan(*grid, 5.0, 6.0, 40.0, 100.0, det, det, 1.5, 1.5, np.zeros(n_proj))
+    s.frames = synth.conveyor_frames(n_proj, 40.0, 100.0, det, det, 1.5, 30.0)
+    s.alpha, s.beta, s.gamma, s.tx, s.ty, s.tz = 0.3, 0.12, 0.8, 0.4, -0.2, 0.3
+    return s
+
+
+def test_conveyor_trajectory_rays_chords_and_bruteforce(orc):
+    scan = conveyor_scan()
+    o = osetup(orc, scan)
+    S, D = bf.rays(scan)
+    for p in range(scan.n_proj):
+        for iu, iv in ((0, 0), (5, 6), (11, 11)):
+            So, Do = orc.ray(o, p, iu, iv)
+            np.testing.assert_allclose(So, S[p, iv, iu], atol=1e-12)
+            np.testing.assert_allclose(Do, D[p, iv, iu], atol=1e-12)
+    L = orc.row_sums(o)
+    hit = 0
+    for p in range(scan.n_proj):
+        for iv in range(scan.det_h):
+            for iu in range(scan.det_w):
+                ref = bf.cylinder_chord(scan, S[p, iv, iu], D[p, iv, iu])
+                assert abs(L[p, iv, iu] - ref) <= 1e-12 * max(ref, scan.radius)
+                hit += ref > 0
+    assert hit > 50
+    A_bf = bf.dense_matrix(scan)
+    A_or = oracle_matrix(orc, scan)
+    np.testing.assert_allclose(A_or, A_bf, rtol=0, atol=1e-12 * np.abs(A_bf).max())
