@@ -66,12 +66,19 @@ typedef struct cyl_grid {
     double radius_mm, height_mm; /* grid cylinder: r <= radius, |h| <= height / 2 */
 } cyl_grid;
 
-/* Circular cone-beam acquisition (Table 1 lists one such geometry). */
+/* Cone-beam acquisition.  Circular (Table 1 lists one such geometry): a fixed source and
+ * detector and a turning stage, frames_mm = NULL.  General trajectory (a conveyor belt, a
+ * helix): frames_mm holds, for each projection, 12 doubles in stage coordinates (no stage
+ * turn): the source S, the centre D0 of pixel (0, 0) and the steps du, dv to the next
+ * pixel column and row, mm; pixel (iu, iv) sits at D0 + iu du + iv dv.  With frames the
+ * fields sod, sdd, pitch, off and angles are not used (angles_rad may be NULL).  Copied
+ * at plan creation.  The server takes circular requests only. */
 typedef struct cyl_geom {
     double sod_mm, sdd_mm;       /* 0 < sod < sdd */
     int32_t n_proj, det_w, det_h;
     double pitch_u_mm, pitch_v_mm, off_u_mm, off_v_mm;
     const double *angles_rad;    /* host array of n_proj stage angles; copied */
+    const double *frames_mm;     /* NULL, or host array of n_proj x 12 (see above); copied */
 } cyl_geom;
 
 /* Part pose (Sec. 2, Eq. 1); see the conventions above. */

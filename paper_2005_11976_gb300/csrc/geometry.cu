@@ -40,12 +40,32 @@ int validate_scan(const cyl_grid *grid, const cyl_geom *geom, const cyl_pose *po
     if (!(grid->radius_mm > 0.0) || !(grid->height_mm > 0.0) || !std::isfinite(grid->radius_mm) ||
         !std::isfinite(grid->height_mm))
         return set_error(CYL_EINVAL, "grid radius and height must be finite and > 0");
-    if (!(geom->sod_mm > 0.0) || !(geom->sdd_mm > geom->sod_mm) || !std::isfinite(geom->sdd_mm))
-        return set_error(CYL_EINVAL, "need 0 < SOD < SDD");
     if (geom->n_proj < 1 || geom->det_w < 1 || geom->det_h < 1)
         return set_error(CYL_EINVAL, "projections and detector size must be >= 1");
     if ((int64_t)geom->det_w * geom->det_h >= (int64_t)1 << 30)
         return set_error(CYL_EINVAL, "detector must have fewer than 2^30 pixels");
+    const double pv[6] = {pose->alpha, pose->beta, pose->gamma, pose->tx, pose->ty, pose->tz};
+    for (double v : pv)
+        if (!std::isfinite(v)) return set_error(CYL_EINVAL, "non-finite pose");
+    // the grid cylinder, wherever the pose puts it, must not reach any source
+    const double sphere = std::sqrt(grid->radius_mm * grid->radius_mm +
+                                    0.25 * grid->height_mm * grid->height_mm);
+    if (geom->frames_mm) {
+        for (int64_t k = 0; k < 12 * (int64_t)geom->n_proj; ++k)
+            if (!std::isfinite(geom->frames_mm[k])) return set_error(CYL_EINVAL, "non-finite frame");
+        for (int p = 0; p < geom->n_proj; ++p) {
+            const double *f = geom->frames_mm + 12 * (int64_t)p;
+            const double du = std::sqrt(f[6] * f[6] + f[7] * f[7] + f[8] * f[8]);
+            const double dv = std::sqrt(f[9] * f[9] + f[10] * f[10] + f[11] * f[11]);
+            if (!(du > 0.0) || !(dv > 0.0)) return set_error(CYL_EINVAL, "zero pixel step in a frame");
+            const double sx = f[0] - pose->tx, sy = f[1] - pose->ty, sz = f[2] - pose->tz;
+            if (std::sqrt(sx * sx + sy * sy + sz * sz) <= sphere)
+                return set_error(CYL_EINVAL, "the grid cylinder reaches a frame's source");
+        }
+        return CYL_OK;
+    }
+    if (!(geom->sod_mm > 0.0) || !(geom->sdd_mm > geom->sod_mm) || !std::isfinite(geom->sdd_mm))
+        return set_error(CYL_EINVAL, "need 0 < SOD < SDD");
     if (!(geom->pitch_u_mm > 0.0) || !(geom->pitch_v_mm > 0.0) ||
         !std::isfinite(geom->pitch_u_mm) || !std::isfinite(geom->pitch_v_mm))
         return set_error(CYL_EINVAL, "pixel pitch must be finite and > 0");
@@ -54,13 +74,7 @@ int validate_scan(const cyl_grid *grid, const cyl_geom *geom, const cyl_pose *po
     if (!geom->angles_rad) return set_error(CYL_EINVAL, "angles_rad is null");
     for (int p = 0; p < geom->n_proj; ++p)
         if (!std::isfinite(geom->angles_rad[p])) return set_error(CYL_EINVAL, "non-finite angle");
-    const double pv[6] = {pose->alpha, pose->beta, pose->gamma, pose->tx, pose->ty, pose->tz};
-    for (double v : pv)
-        if (!std::isfinite(v)) return set_error(CYL_EINVAL, "non-finite pose");
-    // the grid cylinder must lie in front of the source for every view
-    const double reach = std::sqrt(grid->radius_mm * grid->radius_mm +
-                                   0.25 * grid->height_mm * grid->height_mm) +
-                         std::sqrt(pose->tx * pose->tx + pose->ty * pose->ty + pose->tz * pose->tz);
+    const double reach = sphere + std::sqrt(pose->tx * pose->tx + pose->ty * pose->ty + pose->tz * pose->tz);
     if (reach >= geom->sod_mm) return set_error(CYL_EINVAL, "the grid cylinder reaches the source");
     return CYL_OK;
 }
@@ -101,6 +115,20 @@ void build_views(const cyl_geom &geom, const cyl_pose &pose, std::vector<ProjGeo
     const double u0 = -0.5 * (W - 1) * geom.pitch_u_mm + geom.off_u_mm;
     const double v0 = -0.5 * (H - 1) * geom.pitch_v_mm + geom.off_v_mm;
     for (int p = 0; p < geom.n_proj; ++p) {
+        if (geom.frames_mm) {           // general trajectory: stage coordinates, no turn
+            const double *f = geom.frames_mm + 12 * (int64_t)p;
+            auto to_obj = [&](const double *st0, bool point, double out[3]) {
+                double st[3] = {st0[0], st0[1], st0[2]};
+                if (point)
+                    for (int i = 0; i < 3; ++i) st[i] -= T[i];
+                for (int i = 0; i < 3; ++i) out[i] = R[i][0] * st[0] + R[i][1] * st[1] + R[i][2] * st[2];
+            };
+            to_obj(f, true, geo[p].S);
+            to_obj(f + 3, true, geo[p].D0);
+            to_obj(f + 6, false, geo[p].du);
+            to_obj(f + 9, false, geo[p].dv);
+            continue;
+        }
         const double c = cos(geom.angles_rad[p]), s = sin(geom.angles_rad[p]);
         // lab -> stage: Rz(-phi); then X' = R (X - T)
         auto to_obj = [&](const double lab[3], bool point, double out[3]) {

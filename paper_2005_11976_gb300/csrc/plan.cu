@@ -35,8 +35,13 @@ int cyl_plan::init(const cyl_grid &gr, const cyl_geom &ge, const cyl_pose &po, i
     grid = gr;
     geom = ge;
     pose = po;
-    angles.assign(ge.angles_rad, ge.angles_rad + ge.n_proj);
+    if (ge.angles_rad) angles.assign(ge.angles_rad, ge.angles_rad + ge.n_proj);
+    else angles.assign(ge.n_proj, 0.0);
     geom.angles_rad = angles.data();
+    if (ge.frames_mm) {
+        frames.assign(ge.frames_mm, ge.frames_mm + 12 * (size_t)ge.n_proj);
+        geom.frames_mm = frames.data();
+    }
     n_vox = (int64_t)gr.n_h * gr.n_theta * gr.n_r;
     n_pix = (int64_t)ge.det_w * ge.det_h;
     int rc;

@@ -52,6 +52,7 @@ struct cyl_plan {
     cyl_geom geom{};
     cyl_pose pose{};
     std::vector<double> angles;
+    std::vector<double> frames;    // n_proj x 12 of a general trajectory, or empty
     cylct::GridDev g{};
     int64_t n_vox = 0, n_pix = 0;
     size_t bytes = 0;

@@ -482,6 +482,7 @@ extern "C" int cyl_server_add_part(cyl_server *srv, const cyl_grid *grid, const 
                                    const void *x0, const float *w, int32_t *part)
 {
     if (!srv || !grid || !geom || !part) return set_error(CYL_EINVAL, "null argument");
+    if (geom->frames_mm) return set_error(CYL_EINVAL, "the server takes circular scans only");
     // validate with a one-view stand-in for the per-request angles
     const double zero = 0.0;
     cyl_geom g1 = *geom;

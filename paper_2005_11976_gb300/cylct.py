@@ -47,7 +47,8 @@ class cyl_geom(ctypes.Structure):
                 ("n_proj", ctypes.c_int32), ("det_w", ctypes.c_int32), ("det_h", ctypes.c_int32),
                 ("pitch_u_mm", ctypes.c_double), ("pitch_v_mm", ctypes.c_double),
                 ("off_u_mm", ctypes.c_double), ("off_v_mm", ctypes.c_double),
-                ("angles_rad", ctypes.POINTER(ctypes.c_double))]
+                ("angles_rad", ctypes.POINTER(ctypes.c_double)),
+                ("frames_mm", ctypes.POINTER(ctypes.c_double))]
 
 
 class cyl_pose(ctypes.Structure):
@@ -193,14 +194,24 @@ def dtype_code(t) -> int:
 
 
 def structs_from_scan(scan):
-    """(grid, geom, pose, angle array) ctypes structs for a synth.Scan-like object."""
-    ang = np.ascontiguousarray(scan.angles, dtype=np.float64)
+    """(grid, geom, pose, kept arrays) ctypes structs for a synth.Scan-like object (a
+    general trajectory when it carries ``frames``)."""
+    frames = getattr(scan, "frames", None)
+    D = ctypes.POINTER(ctypes.c_double)
+    if frames is not None:
+        fr = np.ascontiguousarray(frames, dtype=np.float64).reshape(-1, 12)
+        n = fr.shape[0]
+        ang = np.zeros(n)
+    else:
+        fr = None
+        ang = np.ascontiguousarray(scan.angles, dtype=np.float64)
+        n = len(ang)
     grid = cyl_grid(scan.n_h, scan.n_theta, scan.n_r, scan.radius, scan.height)
-    geom = cyl_geom(scan.sod, scan.sdd, len(ang), scan.det_w, scan.det_h, scan.pitch_u,
-                    scan.pitch_v, scan.off_u, scan.off_v,
-                    ang.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    geom = cyl_geom(scan.sod, scan.sdd, n, scan.det_w, scan.det_h, scan.pitch_u,
+                    scan.pitch_v, scan.off_u, scan.off_v, ang.ctypes.data_as(D),
+                    fr.ctypes.data_as(D) if fr is not None else None)
     pose = cyl_pose(scan.alpha, scan.beta, scan.gamma, scan.tx, scan.ty, scan.tz)
-    return grid, geom, pose, ang
+    return grid, geom, pose, (ang, fr)
 
 
 def sart_params(n_iter=10, subset_size=1, lam=0.5, clamp_nonneg=False, weight_mode=1,

@@ -63,6 +63,21 @@ def test_host_validation_without_gpu(lib):
                         geom.angles_rad)
     assert lib.cyl_plan_create(ctypes.byref(grid), ctypes.byref(g2), ctypes.byref(pose), 0,
                                ctypes.byref(h)) == cylct.CYL_EINVAL
+    # general trajectories: a zero pixel step, a source inside the grid, a NaN
+    fr = synth.frames_from_circular(scan)
+    for k, v in ((6, 0.0), (0, 0.5), (4, float("nan"))):
+        bad_f = fr.copy()
+        if k == 6:
+            bad_f[2, 6:9] = 0.0
+        elif k == 0:
+            bad_f[1, 0:3] = (0.5, 0.0, 0.0)
+        else:
+            bad_f[3, 4] = v
+        gf = cylct.cyl_geom(0.0, 0.0, geom.n_proj, geom.det_w, geom.det_h, 0.0, 0.0, 0.0, 0.0,
+                            None, np.ascontiguousarray(bad_f).ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        assert lib.cyl_plan_create(ctypes.byref(grid), ctypes.byref(gf), ctypes.byref(pose), 0,
+                                   ctypes.byref(h)) == cylct.CYL_EINVAL
+    assert b"frame" in lib.cyl_last_error_detail()
     p2 = cylct.cyl_pose(float("nan"), 0, 0, 0, 0, 0)
     assert lib.cyl_plan_create(ctypes.byref(grid), ctypes.byref(geom), ctypes.byref(p2), 0,
                                ctypes.byref(h)) == cylct.CYL_EINVAL

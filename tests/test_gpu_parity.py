@@ -354,3 +354,24 @@ def test_precision_size_single_view_projection(lib, orc, vol_dt):
         got = gu.to_np(out)
     assert gu.rel_l2(got, ref) <= TOL_FP32
 
+
+def test_general_trajectory_frames(lib, orc):
+    # frames of a circular scan give the circular plan's projections; a conveyor-belt
+    # trajectory matches the oracle (projection and SART)
+    s = tilted_scan()
+    fs = dataclasses.replace(s, frames=synth.frames_from_circular(s))
+    rng = np.random.default_rng(21)
+    x = rng.uniform(0.0, 0.05, size=s.vol_shape)
+    with cylct.Plan(s) as a, cylct.Plan(fs) as b:
+        assert gu.rel_l2(gu.project(b, x), gu.project(a, x)) <= 1e-6
+    c = synth.Scan(20, 64, 16, 10.0, 20.0, 100.0, 400.0, 48, 40, 1.6, 1.6, np.zeros(24))
+    c.frames = synth.conveyor_frames(24, 100.0, 400.0, 48, 40, 1.6, 120.0)
+    c.alpha, c.beta, c.gamma, c.tx, c.ty, c.tz = 0.5, 0.1, 1.3, 0.6, -0.3, 0.2
+    o = osetup(orc, c)
+    xc = rng.uniform(0.0, 0.05, size=c.vol_shape)
+    ref_q = orc.project(o, xc)
+    with cylct.Plan(c) as plan:
+        assert per_projection_rel(gu.project(plan, xc), ref_q) <= TOL_FP32
+        got = gu.sart(plan, ref_q, n_iter=2, lam=0.5)
+    assert gu.rel_l2(got, orc.sart(o, ref_q, n_iter=2, lam=0.5)) <= TOL_FP32
+
