@@ -454,6 +454,9 @@ def run_batched(args):
     outs_b = [torch.empty(s.vol_shape, device=dev) for s in scans]
     outs_p = [torch.empty(s.vol_shape, device=dev) for s in scans]
     prm = cylct.sart_params(n_iter=10, lam=LAMBDA)
+    # the batch autotuner times round 0 for every piece setting (the batch uses plans[0]'s)
+    cylct.cyl_sart_tune_batch(plans, sinos, cylct.CYL_F32, [x0] * n, [wd] * n, prm, outs_b, cylct.CYL_F32)
+    pieces = plans[0].cyl_plan_get_pieces()
     # warm-up: one small batched and one plain solve
     cylct.cyl_sart_solve_batch(plans[:2], sinos[:2], cylct.CYL_F32, [x0, x0], [wd, wd],
                                cylct.sart_params(n_iter=1, lam=LAMBDA), outs_b[:2], cylct.CYL_F32)
@@ -486,6 +489,7 @@ def run_batched(args):
                                f"N_p in {{60,90,120,180}} ({views} views), |T|<=5 mm, tilt<=3 deg, "
                                "10 sweeps, shared warm start, ROI weights",
                    "launch": "one CUDA graph (batched) vs one cyl_sart_solve graph per scan (plain)"},
+        "pieces_per_ray_tuned": {"projector": pieces[0], "back_projector": pieces[1]},
         "plain_scans_per_s": n / t_plain, "batched_over_plain": t_plain / t_batch,
         "max_rel_err_batched_vs_plain": err,
         "sart_iters_per_s_batched": n * 10 / t_batch,
@@ -499,17 +503,17 @@ def run_batched(args):
 
 
 def run_serving(args):
-    """Poisson arrivals (20 scans/s) of small and medium part types through the server
+    """Poisson arrivals (20 scans/s) of the three part types through the server
     (continuous batching, BF16 storage, 150 GB budget) vs the same scans solved one at a
     time in arrival order."""
     torch, cylct = _gpu_setup()
     from paper_2005_11976_gb300 import synth
     n = args.scans or 48
-    stream = [r for r in synth.serving_stream(20.0, 600.0, part_types=("small", "medium"))][:n]
+    stream = [r for r in synth.serving_stream(20.0, 600.0)][:n]
     dev = torch.device("cuda")
     bf16 = cylct.CYL_BF16
     parts = {}
-    for pt in ("small", "medium"):
+    for pt in ("small", "medium", "large"):
         cfgp = synth.SERVING_PART_TYPES[pt]
         base = synth.medium_scan(n_proj=1, grid=cfgp["grid"], det=cfgp["det"], pitch=204.8 / cfgp["det"])
         rng = synth.rng_for("serving", 500 + len(parts))
@@ -586,9 +590,9 @@ def run_serving(args):
         "warmup": 0, "ms_per_step": t_served * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": f"serving: first {len(reqs)} arrivals of a Poisson stream at 20 scans/s, part "
-                               "types (64,256,64)/128^2 and (128,512,128)/256^2, N_p in {60..360}, 10% with "
-                               "a removed insert, 10 sweeps, BF16 storage, 150 GB budget",
-                   "omitted": "the (256,1024,256)/512^2 part type (about 18 s per scan at this kernel speed)"},
+                               "types (64,256,64)/128^2, (128,512,128)/256^2 and (256,1024,256)/512^2, N_p in "
+                               "{60..360}, 10% with a removed insert, 10 sweeps, BF16 storage, 150 GB budget"},
+        "part_mix": {pt: sum(1 for r in reqs if r[1] == pt) for pt in ("small", "medium", "large")},
         "p50_latency_s": pct(lat, 50), "p99_latency_s": pct(lat, 99),
         "plain_scans_per_s": len(reqs) / free, "plain_p50_latency_s": pct(lat_p, 50),
         "plain_p99_latency_s": pct(lat_p, 99), "served_over_plain": free / t_served,

@@ -199,6 +199,17 @@ int cyl_sart_solve_batch(int32_t n, cyl_plan *const *plans, const void *const *s
                          const cyl_sart_params *params, void *const *x_outs, cyl_dtype x_dtype,
                          void *stream);
 
+/* Autotuner of a batch: takes the arguments of cyl_sart_solve_batch, builds the same
+ * rounds and times the first round's projector and back-projector for 1, 2, 4, 8 and 16
+ * pieces per ray; the fastest setting of each is stored in plans[0] (which the batch
+ * uses; cyl_plan_get_pieces reports it).  Writes only the plans' scratch (the outputs
+ * and the iterate are not touched).  Synchronises the plans' work.  Errors as for
+ * cyl_sart_solve_batch. */
+int cyl_sart_tune_batch(int32_t n, cyl_plan *const *plans, const void *const *sinos,
+                        cyl_dtype sino_dtype, const void *const *x0s, const float *const *ws,
+                        const cyl_sart_params *params, void *const *x_outs, cyl_dtype x_dtype,
+                        void *stream);
+
 /* ---------------------------------------------------------------- serving
  * A server reconstructs a stream of in-line inspection scans of registered part types
  * (Sec. 2.4 / 3.3: series of same-type parts, each with its own pose; the grid is fixed to

@@ -68,10 +68,15 @@ void batch_rounds(const std::vector<int> &n_proj, int subset, int n_iter,
 
 }  // namespace cylct
 
-extern "C" int cyl_sart_solve_batch(int32_t n, cyl_plan *const *plans, const void *const *sinos,
-                                    cyl_dtype sino_dtype, const void *const *x0s,
-                                    const float *const *ws, const cyl_sart_params *prm,
-                                    void *const *x_outs, cyl_dtype x_dtype, void *stream)
+namespace {
+
+// Batched solve, or (tune) the batch autotuner: the same descriptors, then instead of the
+// rounds, round 0's projector and back-projector timed for every piece setting; the
+// fastest of each is stored in plans[0], whose settings the batch uses.  Tuning writes
+// only the plans' scratch (projections and accumulators, cleared by every solve).
+int batch_run(int32_t n, cyl_plan *const *plans, const void *const *sinos, cyl_dtype sino_dtype,
+              const void *const *x0s, const float *const *ws, const cyl_sart_params *prm,
+              void *const *x_outs, cyl_dtype x_dtype, void *stream, bool tune)
 {
     if (n < 0 || (n > 0 && (!plans || !sinos || !x_outs)) || !prm)
         return set_error(CYL_EINVAL, "bad batch arguments");
@@ -120,7 +125,6 @@ extern "C" int cyl_sart_solve_batch(int32_t n, cyl_plan *const *plans, const voi
     const size_t xb = dtype_size(x_dtype);
     int rc;
     int64_t max_vox = 0;
-    const int P = plans[0]->p_fp;
     std::vector<BatchScan> scans(n);
     std::vector<int> n_proj(n);
     for (int i = 0; i < n; ++i) {
@@ -132,8 +136,8 @@ extern "C" int cyl_sart_solve_batch(int32_t n, cyl_plan *const *plans, const voi
         const void *x0 = x0s ? x0s[i] : nullptr;
         const float *w = ws ? ws[i] : nullptr;
         void *xo = x_outs[i];
-        if (x0 && x0 != xo) BT_CUDA(cudaMemcpyAsync(xo, x0, xb * pl->n_vox, cudaMemcpyDeviceToDevice, bs));
-        if (!x0) BT_CUDA(cudaMemsetAsync(xo, 0, xb * pl->n_vox, bs));
+        if (!tune && x0 && x0 != xo) BT_CUDA(cudaMemcpyAsync(xo, x0, xb * pl->n_vox, cudaMemcpyDeviceToDevice, bs));
+        if (!tune && !x0) BT_CUDA(cudaMemsetAsync(xo, 0, xb * pl->n_vox, bs));
         BatchScan &sc = scans[i];
         sc.sd = pl->scan_dev();
         sc.sino = sinos[i];
@@ -160,19 +164,20 @@ extern "C" int cyl_sart_solve_batch(int32_t n, cyl_plan *const *plans, const voi
             if ((rc = pl->ensure((void **)&pl->d_x32, pl->x32_cap, sizeof(float) * pl->n_vox))) return rc;
             u.x32 = pl->d_x32;
             sc.x_proj = pl->d_x32;
-            BT_CUDA(launch_convert(xo, x_dtype, pl->d_x32, CYL_F32, pl->n_vox, bs));
+            if (!tune) BT_CUDA(launch_convert(xo, x_dtype, pl->d_x32, CYL_F32, pl->n_vox, bs));
         }
         u.w = w;
         u.wscale = w ? pl->d_wscale : nullptr;
         u.lambda = (float)prm->lambda;
         u.clamp = prm->clamp_nonneg ? 1 : 0;
-        if (w) BT_CUDA(launch_weight_scale(w, pl->n_vox, prm->weight_mode, (float)prm->lambda, pl->d_wscale, bs));
+        if (w && !tune)
+            BT_CUDA(launch_weight_scale(w, pl->n_vox, prm->weight_mode, (float)prm->lambda, pl->d_wscale, bs));
         n_proj[i] = pl->geom.n_proj;
     }
     std::vector<BatchItem> items;
     std::vector<int> n_items;
     int rounds = 0;
-    batch_rounds(n_proj, prm->subset_size, prm->n_iter, items, n_items, rounds);
+    batch_rounds(n_proj, prm->subset_size, tune ? 1 : prm->n_iter, items, n_items, rounds);
 
     if (rounds > 0) {
         void *d_blob = nullptr;
@@ -192,14 +197,44 @@ extern "C" int cyl_sart_solve_batch(int32_t n, cyl_plan *const *plans, const voi
         // projector and update types: the 16-bit iterate in strict mode, else FP32
         const bool strict = x_dtype != CYL_F32 && prm->strict_16bit;
         const cyl_dtype xt = strict ? x_dtype : CYL_F32, x16t = xt;
-        if (prm->use_graph) {
+        const int Pf = plans[0]->p_fp, Pb = plans[0]->p_bp;
+        if (tune) {
+            cudaEvent_t e[2];
+            BT_CUDA(cudaEventCreate(&e[0]));
+            BT_CUDA(cudaEventCreate(&e[1]));
+            float best[2] = {1e30f, 1e30f};
+            int pick[2] = {0, 0};
+            cudaError_t ce = cudaSuccess;
+            for (int part = 0; part < 2 && ce == cudaSuccess; ++part)
+                for (int P = 1; P <= kSplit && ce == cudaSuccess; P *= 2)
+                    for (int rep = 0; rep < 3 && ce == cudaSuccess; ++rep) {
+                        ce = cudaEventRecord(e[0], bs);
+                        if (ce == cudaSuccess)
+                            ce = launch_batch_round(d_scans, d_items, d_n, n, 0, max_vox, P, P,
+                                                    part ? kRoundBp : kRoundFp, d_sched, xt, sino_dtype, x16t, bs);
+                        if (ce == cudaSuccess) ce = cudaEventRecord(e[1], bs);
+                        if (ce == cudaSuccess) ce = cudaEventSynchronize(e[1]);
+                        float ms = 0.f;
+                        if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e[0], e[1]);
+                        if (ce == cudaSuccess && rep > 0 && ms < best[part]) {
+                            best[part] = ms;
+                            pick[part] = P;
+                        }
+                    }
+            cudaEventDestroy(e[0]);
+            cudaEventDestroy(e[1]);
+            if (ce != cudaSuccess) return cuda_error(ce, "batch autotuner");
+            plans[0]->p_fp = pick[0];
+            plans[0]->p_bp = pick[1];
+            plans[0]->drop_graphs();
+        } else if (prm->use_graph) {
             cudaGraph_t graph = nullptr;
             cudaGraphExec_t exec = nullptr;
             BT_CUDA(cudaStreamBeginCapture(bs, cudaStreamCaptureModeThreadLocal));
             cudaError_t ce = cudaSuccess;
             for (int r = 0; r < rounds && ce == cudaSuccess; ++r)
-                ce = launch_batch_round(d_scans, d_items, d_n, n, r, max_vox, P, d_sched, xt,
-                                        sino_dtype, x16t, bs);
+                ce = launch_batch_round(d_scans, d_items, d_n, n, r, max_vox, Pf, Pb, kRoundAll, d_sched,
+                                        xt, sino_dtype, x16t, bs);
             cudaError_t ee = cudaStreamEndCapture(bs, &graph);
             if (ce != cudaSuccess) {
                 if (graph) cudaGraphDestroy(graph);
@@ -214,12 +249,12 @@ extern "C" int cyl_sart_solve_batch(int32_t n, cyl_plan *const *plans, const voi
             if (ce != cudaSuccess) return cuda_error(ce, "cudaGraphLaunch");
         } else {
             for (int r = 0; r < rounds; ++r)
-                BT_CUDA(launch_batch_round(d_scans, d_items, d_n, n, r, max_vox, P, d_sched, xt,
-                                           sino_dtype, x16t, bs));
+                BT_CUDA(launch_batch_round(d_scans, d_items, d_n, n, r, max_vox, Pf, Pb, kRoundAll, d_sched,
+                                           xt, sino_dtype, x16t, bs));
         }
         BT_CUDA(cudaFreeAsync(d_blob, bs));
     }
-    if (x_dtype != CYL_F32 && !prm->strict_16bit)
+    if (!tune && x_dtype != CYL_F32 && !prm->strict_16bit)
         for (int i = 0; i < n; ++i)
             BT_CUDA(launch_convert(plans[i]->d_x32, CYL_F32, x_outs[i], x_dtype, plans[i]->n_vox, bs));
     BT_CUDA(cudaEventRecord(plans[0]->ev_out, bs));
@@ -232,4 +267,22 @@ extern "C" int cyl_sart_solve_batch(int32_t n, cyl_plan *const *plans, const voi
         }
     }
     return CYL_OK;
+}
+
+}  // namespace
+
+extern "C" int cyl_sart_solve_batch(int32_t n, cyl_plan *const *plans, const void *const *sinos,
+                                    cyl_dtype sino_dtype, const void *const *x0s,
+                                    const float *const *ws, const cyl_sart_params *prm,
+                                    void *const *x_outs, cyl_dtype x_dtype, void *stream)
+{
+    return batch_run(n, plans, sinos, sino_dtype, x0s, ws, prm, x_outs, x_dtype, stream, false);
+}
+
+extern "C" int cyl_sart_tune_batch(int32_t n, cyl_plan *const *plans, const void *const *sinos,
+                                   cyl_dtype sino_dtype, const void *const *x0s,
+                                   const float *const *ws, const cyl_sart_params *prm,
+                                   void *const *x_outs, cyl_dtype x_dtype, void *stream)
+{
+    return batch_run(n, plans, sinos, sino_dtype, x0s, ws, prm, x_outs, x_dtype, stream, true);
 }

@@ -102,10 +102,13 @@ cudaError_t launch_update_nd(int64_t n_vox, const float2 *nd, const UpdateArgs &
 cudaError_t launch_count_rays(const ScanDev &sd, int p0, int np, unsigned long long *counts,
                               cudaStream_t st);
 // One round of a batched solve: forward projection, back-projection and update of every
-// item of the round.  sched: the batch's scheduler state (kSched ints, zero at rest).
+// item of the round (the kernels selected by `parts`).  Pf, Pb: pieces per ray of the
+// two kernels (<= 0: their defaults).  sched: the batch's scheduler state (kSched ints,
+// zero at rest).
+constexpr int kRoundFp = 1, kRoundBp = 2, kRoundUpdate = 4, kRoundAll = 7;
 cudaError_t launch_batch_round(const BatchScan *scans, const BatchItem *items, const int *n_items,
-                               int max_items, int round, int64_t max_vox, int P, int *sched,
-                               cyl_dtype xt, cyl_dtype yt, cyl_dtype x16t, cudaStream_t st);
+                               int max_items, int round, int64_t max_vox, int Pf, int Pb, int parts,
+                               int *sched, cyl_dtype xt, cyl_dtype yt, cyl_dtype x16t, cudaStream_t st);
 cudaError_t launch_log(const void *in, cyl_dtype it, double i0, void *out, cyl_dtype ot,
                        int64_t n, cudaStream_t st);
 cudaError_t launch_convert(const void *in, cyl_dtype it, void *out, cyl_dtype ot,

@@ -515,26 +515,29 @@ cudaError_t launch_count_rays(const ScanDev &sd, int p0, int np, unsigned long l
 }
 
 cudaError_t launch_batch_round(const BatchScan *scans, const BatchItem *items, const int *n_items,
-                               int max_items, int round, int64_t max_vox, int P, int *sched,
-                               cyl_dtype xt, cyl_dtype yt, cyl_dtype x16t, cudaStream_t st)
+                               int max_items, int round, int64_t max_vox, int Pf, int Pb, int parts,
+                               int *sched, cyl_dtype xt, cyl_dtype yt, cyl_dtype x16t, cudaStream_t st)
 {
-    const int lgPf = log2_pieces(P, kPiecesFp), lgPb = log2_pieces(P, kPiecesBp);
+    const int lgPf = log2_pieces(Pf, kPiecesFp), lgPb = log2_pieces(Pb, kPiecesBp);
     if (lgPf < 0 || lgPb < 0 || max_items < 1) return cudaErrorInvalidValue;
     const size_t smem = sizeof(int) * ((size_t)max_items + 1);
-    cudaError_t e = dispatch_t(xt, [&](auto *tx) {
-        using T = std::remove_pointer_t<decltype(tx)>;
-        const unsigned blocks = persistent_blocks((const void *)k_fp_batch<T>, smem);
-        k_fp_batch<T><<<blocks, 256, smem, st>>>(scans, items, n_items, max_items, round, lgPf, sched);
-        return cudaGetLastError();
-    });
+    cudaError_t e = cudaSuccess;
+    if (parts & kRoundFp)
+        e = dispatch_t(xt, [&](auto *tx) {
+            using T = std::remove_pointer_t<decltype(tx)>;
+            const unsigned blocks = persistent_blocks((const void *)k_fp_batch<T>, smem);
+            k_fp_batch<T><<<blocks, 256, smem, st>>>(scans, items, n_items, max_items, round, lgPf, sched);
+            return cudaGetLastError();
+        });
     if (e != cudaSuccess) return e;
-    e = dispatch_t(yt, [&](auto *ty) {
-        using S = std::remove_pointer_t<decltype(ty)>;
-        const unsigned blocks = persistent_blocks((const void *)k_bp_batch<S>, smem);
-        k_bp_batch<S><<<blocks, 256, smem, st>>>(scans, items, n_items, max_items, round, lgPb, sched);
-        return cudaGetLastError();
-    });
-    if (e != cudaSuccess) return e;
+    if (parts & kRoundBp)
+        e = dispatch_t(yt, [&](auto *ty) {
+            using S = std::remove_pointer_t<decltype(ty)>;
+            const unsigned blocks = persistent_blocks((const void *)k_bp_batch<S>, smem);
+            k_bp_batch<S><<<blocks, 256, smem, st>>>(scans, items, n_items, max_items, round, lgPb, sched);
+            return cudaGetLastError();
+        });
+    if (e != cudaSuccess || !(parts & kRoundUpdate)) return e;
     const dim3 grid_u((unsigned)std::min(update_blocks(max_vox), 512), max_items);
     return dispatch_t(x16t, [&](auto *tx) {
         using X = std::remove_pointer_t<decltype(tx)>;

@@ -273,7 +273,7 @@ int cyl_server::run_round()
     std::vector<BatchScan> scans;
     std::vector<BatchItem> items;
     std::vector<std::shared_ptr<Scan>> members;
-    int P = 0;
+    int Pf = 0, Pb = 0, have_p = 0;
     int64_t max_vox = 0;
     for (auto &s : active) {
         if (s->state != 1 || s->rounds_done >= s->rounds_total) continue;
@@ -304,7 +304,11 @@ int cyl_server::run_round()
         scans.push_back(sc);
         members.push_back(s);
         max_vox = std::max(max_vox, pl->n_vox);
-        if (!P) P = pl->p_fp;
+        if (!have_p) {
+            Pf = pl->p_fp;
+            Pb = pl->p_bp;
+            have_p = 1;
+        }
     }
     if (scans.empty()) return CYL_OK;
     const int n = (int)scans.size();
@@ -322,8 +326,8 @@ int cyl_server::run_round()
         return set_error(CYL_EDEVICE, "round descriptors");
     if (cudaEventRecord(slot_ev[slot], st) != cudaSuccess) return set_error(CYL_EDEVICE, "event");
     cudaError_t e = launch_batch_round(reinterpret_cast<BatchScan *>(d), reinterpret_cast<BatchItem *>(d + b_scans),
-                                       reinterpret_cast<int *>(d + b_scans + b_items), n, 0, max_vox, P,
-                                       d_sched, CYL_F32, cfg.storage, CYL_F32, st);
+                                       reinterpret_cast<int *>(d + b_scans + b_items), n, 0, max_vox, Pf, Pb,
+                                       kRoundAll, d_sched, CYL_F32, cfg.storage, CYL_F32, st);
     if (e != cudaSuccess) return cuda_error(e, "round launch");
     ++stats.rounds;
     for (auto &s : members) {

@@ -113,6 +113,8 @@ SIGNATURES = {
     "cyl_count_segments": (ctypes.c_int, [_VP, _I32, _I32, _VP, _VP]),
     "cyl_sart_solve_batch": (ctypes.c_int, [_I32, _VP, _VP, ctypes.c_int, _VP, _VP,
                                             ctypes.POINTER(cyl_sart_params), _VP, ctypes.c_int, _VP]),
+    "cyl_sart_tune_batch": (ctypes.c_int, [_I32, _VP, _VP, ctypes.c_int, _VP, _VP,
+                                           ctypes.POINTER(cyl_sart_params), _VP, ctypes.c_int, _VP]),
     "cyl_server_create": (ctypes.c_int, [ctypes.POINTER(cyl_server_cfg), ctypes.POINTER(_VP)]),
     "cyl_server_add_part": (ctypes.c_int, [_VP, ctypes.POINTER(cyl_grid), ctypes.POINTER(cyl_geom),
                                            _VP, _VP, ctypes.POINTER(_I32)]),
@@ -321,6 +323,18 @@ def cyl_sart_solve_batch(plans, sinos, sino_dtype, x0s, ws, params, x_outs, x_dt
     ho = _ptr_array(x_outs)
     _check(load().cyl_sart_solve_batch(n, hp, hs, sino_dtype, hx0, hw, ctypes.byref(params), ho,
                                        x_dtype, stream_ptr(stream)), "cyl_sart_solve_batch")
+
+
+def cyl_sart_tune_batch(plans, sinos, sino_dtype, x0s, ws, params, x_outs, x_dtype, stream=None):
+    """Batch autotuner (same arguments as cyl_sart_solve_batch); the choice lands in plans[0]."""
+    n = len(plans)
+    hp = _ptr_array([p.h.value for p in plans])
+    hs = _ptr_array(sinos)
+    hx0 = _ptr_array(x0s) if x0s is not None else None
+    hw = _ptr_array(ws) if ws is not None else None
+    ho = _ptr_array(x_outs)
+    _check(load().cyl_sart_tune_batch(n, hp, hs, sino_dtype, hx0, hw, ctypes.byref(params), ho,
+                                      x_dtype, stream_ptr(stream)), "cyl_sart_tune_batch")
 
 
 def cyl_log_transform(counts, in_dtype, i0, p_out, out_dtype, n, stream=None):

@@ -89,3 +89,29 @@ def test_batch_rejects_host_arrays(lib):
                                    cylct.sart_params(n_iter=1), [out], cylct.CYL_F32)
     assert e.value.code == cylct.CYL_EINVAL
     plan.close()
+
+
+scans_ = scans
+
+
+def test_batch_autotuner_keeps_results(lib, orc):
+    # the tuner touches only scratch: a batch tuned before solving gives the same volumes
+    scans = scans_()[:2]
+    rng = np.random.default_rng(9)
+    ps = [orc.project(orc.Setup(**s.fields()), rng.uniform(0.0, 0.05, size=s.vol_shape)) for s in scans]
+    plans = [cylct.Plan(s) for s in scans]
+    try:
+        sinos = [gu.to_dev(p) for p in ps]
+        outs = [gu.to_dev(np.full(s.vol_shape, 7.0)) for s in scans]
+        prm = cylct.sart_params(n_iter=2, lam=0.5)
+        cylct.cyl_sart_tune_batch(plans, sinos, cylct.CYL_F32, None, None, prm, outs, cylct.CYL_F32)
+        assert all(np.all(gu.to_np(o) == 7.0) for o in outs)      # outputs untouched
+        fp, bp = plans[0].cyl_plan_get_pieces()
+        assert fp in (1, 2, 4, 8, 16) and bp in (1, 2, 4, 8, 16)
+        cylct.cyl_sart_solve_batch(plans, sinos, cylct.CYL_F32, None, None, prm, outs, cylct.CYL_F32)
+        for s, p, o in zip(scans, ps, outs):
+            assert gu.rel_l2(gu.to_np(o), orc.sart(orc.Setup(**s.fields()), p, n_iter=2, lam=0.5)) <= 1e-5
+    finally:
+        for p in plans:
+            p.close()
+
