@@ -37,6 +37,9 @@ N_ITER = 20
 # DRAM bytes (read + write) per launch of each kernel at the medium workload, from one ncu
 # capture of the current kernels (profiles/sart_medium_kernels.md).
 TRAFFIC: dict = {"k_fp": 73.3e6, "k_bp": 82.9e6, "k_update_nd": 145.8e6}
+# DRAM bytes per scan of the corner pass on Table 1 scans (FP16), from one ncu capture of
+# 20 scans (profiles/pose_corners_table1.md); a launch's traffic scales with its scans.
+TRAFFIC_PER_SCAN: dict = {"k_corners": 2.5122e9 / 20}
 LAMBDA = 0.5
 I0 = 1.0e4
 CONFIG_MEDIUM = {
@@ -188,13 +191,15 @@ def main():
                     help="one captured CUDA graph per sweep, timing events captured in it "
                          "(default: eager launches with an event between kernels)")
     ap.add_argument("--workload", default="medium",
-                    choices=["medium", "batched", "serving", "precision", "mtf"])
+                    choices=["medium", "batched", "serving", "precision", "mtf", "pose"])
     ap.add_argument("--scans", type=int, default=0, help="batched/serving: number of scans")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "pose":
+        return run_pose(args)
     if args.workload == "serving":
         return run_serving(args)
     if args.workload == "precision":
@@ -499,6 +504,149 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
     for p in plans:
         p.close()
+    return 0
+
+
+def run_pose(args):
+    """Pose estimation from the projections (Sec. 2.1) on Table 1's scans, as in Sec. 3.2:
+    50 parts (a tube 64 mm high, 8 mm outer and 3 mm inner radius), each scanned five
+    times with the stage axis on the five detector columns of Sec. 3.2; 21 projections
+    over 200 deg on the 1944 x 1536 panel at 0.0748 mm, SOD 679, SDD 791; FP16 line
+    integrals from Poisson counts at I0 = 4e4.  Timed: the batched estimate of all 250
+    scans (one corner launch over every projection, one Levenberg-Marquardt launch), and
+    one scan alone.  Precision: per part, the standard deviation of its five estimates."""
+    import dataclasses
+    torch, cylct = _gpu_setup()
+    from paper_2005_11976_gb300 import synth
+    dev = torch.device("cuda")
+    n_parts = args.scans or 50
+    cols = synth.TABLE1_STAGE_COLUMNS
+    base = synth.table1_scan()
+    # radial profile of the tube on the (1, 1, 8) grid: r in [3, 8] mm at 0.05 / mm
+    rc = (np.arange(8) + 0.5) * base.radius / 8
+    x = torch.from_numpy(np.where(rc >= 3.0, 0.05, 0.0).astype(np.float32).reshape(1, 1, 8)).to(dev)
+    i0_pose, thr, k = 4.0e4, 0.1, 2
+    rng = synth.rng_for("pose", 0)
+    truth = []
+    for i in range(n_parts):
+        truth.append((float(rng.uniform(0, 2 * math.pi)), math.radians(float(rng.uniform(0.5, 3.0))), 0.0,
+                      *[float(v) for v in rng.uniform(-2.0, 2.0, 3)]))
+    scans = [dataclasses.replace(base, frames=synth.frames_from_circular(base, synth.stage_shift_mm(c)))
+             for c in cols]
+    sinos = []
+    p32 = torch.empty(base.sino_shape, device=dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(4242)
+    plans = [cylct.Plan(dataclasses.replace(sc, alpha=truth[0][0], beta=truth[0][1])) for sc in scans]
+    for i in range(n_parts):
+        for c, pl in enumerate(plans):
+            pl.cyl_plan_set_pose(truth[i])
+            pl.cyl_project(x, cylct.CYL_F32, 0, base.n_proj, p32, cylct.CYL_F32)
+            counts = torch.poisson(i0_pose * torch.exp(-p32), generator=gen)
+            out = torch.empty(base.sino_shape, dtype=torch.float16, device=dev)
+            cylct.cyl_log_transform(counts, cylct.CYL_F32, i0_pose, out, cylct.CYL_F16, counts.numel())
+            sinos.append(out)
+    for pl in plans:
+        pl.close()
+    del p32, counts
+    all_scans = [scans[c] for _ in range(n_parts) for c in range(len(cols))]
+    prm = cylct.pose_params(thr, k)
+    f16 = cylct.CYL_F16
+    torch.cuda.synchronize()
+    for _ in range(max(3, args.warmup)):
+        cylct.cyl_estimate_pose_batch(all_scans, sinos, f16, prm)
+    cylct.cyl_pose_set_timing(True)
+    clocks = ClockSampler(0)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    times = []
+    for _ in range(args.steps):
+        e0.record()
+        poses, infos = cylct.cyl_estimate_pose_batch(all_scans, sinos, f16, prm)
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    k_ms, k_n = cylct.cyl_pose_kernel_time(0)
+    t_ms, t_n = cylct.cyl_pose_kernel_time(1)
+    single = []
+    for j in range(20):
+        e0.record()
+        cylct.cyl_estimate_pose(all_scans[j % len(all_scans)], sinos[j % len(sinos)], f16, prm)
+        e1.record()
+        e1.synchronize()
+        single.append(e0.elapsed_time(e1))
+    clk = clocks.stop()
+    cylct.cyl_pose_set_timing(False)
+    n_scans = len(all_scans)
+    t_step = float(np.mean(times))
+    value = n_scans / t_step
+    # precision (Sec. 3.2): std of each part's five estimates; accuracy against the truth
+    P = np.array(poses).reshape(n_parts, len(cols), 6)
+    T = np.array(truth)
+    ax = lambda a, b: np.stack([np.sin(a) * np.sin(b), -np.cos(a) * np.sin(b), np.cos(b)], -1)
+    axis_err = np.degrees(np.arccos(np.clip((ax(P[..., 0], P[..., 1]) * ax(T[:, None, 0], T[:, None, 1])).sum(-1),
+                                            -1, 1)))
+    prec = {"t_mm": P[..., 3:].std(axis=1).mean(axis=0).tolist(),
+            "alpha_deg": float(np.degrees(P[..., 0]).std(axis=1).mean()),
+            "beta_deg": float(np.degrees(P[..., 1]).std(axis=1).mean())}
+    acc = {"axis_deg_mean": float(axis_err.mean()), "axis_deg_max": float(axis_err.max()),
+           "t_mm_mean_abs": np.abs(P[..., 3:] - T[:, None, 3:]).mean(axis=(0, 1)).tolist()}
+    # roofline of the corner pass: every pixel of every projection read once (2 bytes)
+    px = base.det_w * base.det_h * base.n_proj
+    bytes_launch = 2.0 * px * n_scans
+    hbm, peak_kind = peaks()
+    ach = bytes_launch / (k_ms / k_n / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+            "traffic": TRAFFIC_PER_SCAN["k_corners"] * n_scans, "kernel": "k_corners", "peak_source": peak_kind,
+            "traffic_note": "ncu capture of 20 scans scaled by the scans per launch",
+            "algorithmic_bytes_per_launch": bytes_launch,
+            "units_per_launch": f"{n_scans} scans x 21 projections x 1944 x 1536 FP16 pixels",
+            "kernel_ms_avg": {"k_corners": k_ms / k_n, "k_track_pose": t_ms / t_n},
+            "kernel_share": {"k_corners": k_ms / (k_ms + t_ms), "k_track_pose": t_ms / (k_ms + t_ms)}}
+    # e2e: a chunk of scans from pinned host memory through the public API
+    e2e = None
+    if not args.no_e2e:
+        m = min(25, n_scans)
+        host = [sv.cpu().pin_memory() for sv in sinos[:m]]
+        dbuf = [torch.empty_like(sv) for sv in sinos[:m]]
+        e0.record()
+        for h, d in zip(host, dbuf):
+            d.copy_(h, non_blocking=True)
+        ps, _ = cylct.cyl_estimate_pose_batch(all_scans[:m], dbuf, f16, prm)
+        e1.record()
+        e1.synchronize()
+        t_e2e = e0.elapsed_time(e1) / 1e3
+        e2e = {"value": m / t_e2e, "unit": "scans/s", "h2d_bytes_per_step": int(sum(h.numel() * 2 for h in host)),
+               "d2h_bytes_per_step": int(m * (6 * 8 + 72)),
+               "scans_per_step": m, "note": "FP16 sinograms copied from pinned host memory, poses returned to the host"}
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        from oracle import pose as opose
+        oracle.build()
+        s0 = dataclasses.replace(all_scans[0])
+        sino0 = sinos[0].float().cpu().numpy().astype(np.float64)
+        t0 = time.perf_counter()
+        opose.estimate_pose(oracle.Setup(**s0.fields()), sino0, thr, k)
+        dt = time.perf_counter() - t0
+        cpu = {"value": 1.0 / dt, "unit": "scans/s", "cores": 1, "kind": "oracle",
+               "sample": f"one scan (21 projections of 1944 x 1536) of the workload, {dt:.2f} s"}
+    line = {
+        "metric": "pose estimates per second (axis detection by corner pixels + Levenberg-Marquardt)",
+        "value": value, "unit": "scans/s", "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup),
+        "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": value * 0.23, "dtype": "f16", "data": "synthetic",
+        "config": {"workload": f"pose: Table 1 scans (21 projections over 200 deg, 1944x1536 at 0.0748 mm, "
+                               f"SOD 679, SDD 791), {n_parts} parts x 5 stage positions, tube 64 mm x R8/R3, "
+                               "Poisson I0 4e4, FP16 line integrals, threshold 0.1, dilation 2",
+                   "l2": f"inputs {bytes_launch / 1e9:.1f} GB per step, larger than L2"},
+        "baseline_note": "the paper's axis detection took 0.23 s per scan (its GPU unstated)",
+        "single_scan_ms_median": float(np.median(single)),
+        "precision_std_over_stage_positions": prec, "accuracy_vs_truth": acc,
+        "clocks": clk, "gpu_launches": 2 * args.steps,
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+    }
+    print(json.dumps(line), flush=True)
     return 0
 
 

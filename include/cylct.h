@@ -325,6 +325,154 @@ int cyl_plan_get_pieces(const cyl_plan *plan, int32_t *fp_pieces, int32_t *bp_pi
 int cyl_plan_sizes(const cyl_plan *plan, int64_t *n_vox, int64_t *n_pix, int32_t *n_proj,
                    int64_t *device_bytes);
 
+/* ------------------------------------------------------------------------------------
+ * Pose estimation from the projections (Sec. 2.1, "Projection based pose estimation").
+ *
+ * These calls need no plan and no grid: they take the acquisition geometry alone and run
+ * on the calling thread's current CUDA device, where the sinograms must live.  Stage
+ * coordinates are those of the conventions above (X = Rz(-phi_p) X_lab; with frames_mm,
+ * the frames' own coordinates).
+ *
+ * Axis tracking.  In every projection the segment is the set of pixels with p > threshold
+ * inside a detector window, dilated with the (2k+1) x (2k+1) square (clipped to the
+ * window).  Its four corner pixels are the extremes along the detector diagonals:
+ * top-left maximises -iu + iv, top-right iu + iv, bottom-left -iu - iv, bottom-right
+ * iu - iv (ties go to the larger iv for the top corners and the smaller iv for the
+ * bottom ones).  The centre of the two top corners and the centre of the two bottom
+ * corners lie on the projected symmetry axis; over the projections they form two tracks.
+ *
+ * Point tracking (Eq. 3-4).  Each track's 3-D point is the stage point X minimising
+ * sum_i |(u, v)_i - V_i(X)|^2, with V_i(X) the detector position (mm along the pixel
+ * steps) where the line from projection i's source through X meets the detector.
+ * Levenberg-Marquardt with the analytic Jacobian of V_i, in FP64: start on the first
+ * tracked projection's ray at the stage origin's distance from its source; damping mu =
+ * 1e-3 on the diagonal of J^T J, divided by 10 after an accepted step (not below 1e-15)
+ * and multiplied by 10 after a rejected one; stop after a step shorter than
+ * 1e-10 (1 + |X|) mm, when mu exceeds 1e15, or after max_iter steps.
+ *
+ * Pose.  The two axis points fix five of the six degrees of freedom of Eq. 1: the axis
+ * direction a = (top - bottom) / |top - bottom| = (sin alpha sin beta,
+ * -cos alpha sin beta, cos beta) gives alpha and beta (alpha = 0 when the axis is
+ * vertical), the midpoint of the points gives T.  gamma, the spin about the part's own
+ * axis, does not show in a silhouette; it is copied from the parameters (see
+ * cyl_estimate_gamma).
+ * ------------------------------------------------------------------------------------ */
+#define CYL_MAX_DET_SIDE 262143      /* det_w, det_h limit of the corner keys (2^18 - 1) */
+typedef struct cyl_pose_params {
+    double threshold;     /* segment: p > threshold, in the sinogram's units */
+    int32_t dilate_px;    /* k: 0 .. 65535 */
+    int32_t roi[4];       /* window [u0, u1) x [v0, v1) in pixels; all 0 = whole detector */
+    int32_t max_iter;     /* Levenberg-Marquardt steps per point; <= 0 selects 100 */
+    double gamma;         /* copied into the estimated pose */
+} cyl_pose_params;
+
+typedef struct cyl_pose_info {
+    double top_mm[3], bottom_mm[3];  /* tracked axis points, stage coordinates */
+    double rms_mm[2];                /* rms detector distance between each track and V_i */
+    int32_t iters[2];                /* Levenberg-Marquardt steps taken per point */
+    int32_t n_views;                 /* projections whose window held a segment */
+    int32_t status;                  /* 0: estimated; 1: fewer than 2 such projections (the
+                                        pose is then the input gamma and zeros) */
+} cyl_pose_info;
+
+/* Corner pixels of every projection.  sino: device [n_proj][H][W] of sino_dtype.
+ * corners_out: device int32[n_proj][4][2], (iu, iv) of the top-left, top-right,
+ * bottom-left and bottom-right corners, (-1, -1) where the window holds no segment.
+ * counts_out: device int64[n_proj] (pixels over the threshold, before dilation), or NULL.
+ * Asynchronous on `stream`.  Errors: CYL_EINVAL (geometry, window, parameters, det_w or
+ * det_h above CYL_MAX_DET_SIDE), CYL_ENOMEM, CYL_EDEVICE. */
+int cyl_axis_corners(const cyl_geom *geom, const void *sino, cyl_dtype sino_dtype,
+                     const cyl_pose_params *params, int32_t *corners_out, int64_t *counts_out,
+                     void *stream);
+
+/* Eq. 4 for one track.  track: device double[n_proj][2], the pixel coordinates (iu, iv)
+ * of the point in each projection; NaN in either marks a projection where it was not
+ * seen.  out: device double[5] = x, y, z (stage, mm), rms distance (mm), steps taken;
+ * with fewer than 2 observed projections out is x = y = z = rms = NaN, steps = 0.
+ * Asynchronous on `stream`. */
+int cyl_track_point(const cyl_geom *geom, const double *track, int32_t max_iter, double *out,
+                    void *stream);
+
+/* The whole estimate for one scan: corners, both tracks, Eq. 4 for each, and the pose.
+ * pose_out and info_out (may be NULL) are HOST structs; the call synchronises `stream`. */
+int cyl_estimate_pose(const cyl_geom *geom, const void *sino, cyl_dtype sino_dtype,
+                      const cyl_pose_params *params, cyl_pose *pose_out, cyl_pose_info *info_out,
+                      void *stream);
+
+/* n scans in one pass (one corner launch over all projections of all scans, one
+ * Levenberg-Marquardt launch).  geoms, sinos, params: host arrays of n; poses_out,
+ * infos_out (may be NULL): host arrays of n.  0 <= n <= CYL_MAX_BATCH.  Synchronises
+ * `stream`. */
+int cyl_estimate_pose_batch(int32_t n, const cyl_geom *geoms, const void *const *sinos,
+                            cyl_dtype sino_dtype, const cyl_pose_params *params,
+                            cyl_pose *poses_out, cyl_pose_info *infos_out, void *stream);
+
+/* Device time of the pose kernels in the calls that synchronise (cyl_estimate_pose,
+ * cyl_estimate_pose_batch): kind 0 the corner pass, 1 the Levenberg-Marquardt pass.  A
+ * CUDA event pair on the call's stream brackets each launch while timing is enabled
+ * (process-wide); cyl_pose_set_timing also resets the totals.  ms_total and launches
+ * receive the summed durations and the number of launches timed. */
+int cyl_pose_set_timing(int enable);
+int cyl_pose_kernel_time(int kind, double *ms_total, int64_t *launches);
+
+/* ------------------------------------------------------------------------------------
+ * Azimuthal phase (Sec. 2.1, "Azimuthal phase", Eq. 5).
+ *
+ * The grey values of a band along the projected axis are followed over the projection
+ * angle.  The band holds the pixels whose position, measured from the projection A of
+ * the axis point (0, 0, h_lo) towards the projection B of (0, 0, h_hi), lies between A and
+ * B (0 <= s <= 1) and within half_width of the line AB (|d| <= half_width, d in mm on the
+ * detector, positive towards +u).  Per projection the library forms the band's grey-value
+ * sum m0 = sum p and first moment m1 = sum p d, and the centroid offset c = m1 / m0.
+ * Material off the axis pulls c to its side in a sine of the projection angle; the
+ * first-harmonic phase phi_P of c (least-squares fit c ~ c0 + c1 cos phi + c2 sin phi,
+ * phi_P = atan2(c2, c1)) moves with the part's spin gamma.
+ *
+ * s and d are evaluated in FP32 with rounding to nearest and no contraction:
+ * d = (iu - A_u) c_du + (iv - A_v) c_dv, s = (iu - A_u) c_su + (iv - A_v) c_sv, with FP32
+ * constants rounded from FP64 (c_du = |du| L_v / |L|, c_dv = -|dv| L_u / |L|,
+ * c_su = |du| L_u / |L|^2, c_sv = |dv| L_v / |L|^2, L = B - A in mm).
+ * ------------------------------------------------------------------------------------ */
+typedef struct cyl_band {
+    double h_lo_mm, h_hi_mm;   /* axis segment in object heights, h_lo < h_hi */
+    double half_width_mm;      /* > 0 */
+} cyl_band;
+
+/* Band moments of a sinogram for a posed part.  moments_out: device double[n_proj][2] =
+ * (m0, m1).  Asynchronous on `stream`. */
+int cyl_band_moments(const cyl_geom *geom, const cyl_pose *pose, const void *sino,
+                     cyl_dtype sino_dtype, const cyl_band *band, double *moments_out,
+                     void *stream);
+
+/* Eq. 5 with the tilt correction applied exactly.  The centroid moves furthest to +u for
+ * material at lab azimuth phi_G = 90 deg, so material at stage azimuth psi peaks at
+ * phi_P = phi_G - psi (stage turning counter-clockwise, as in the conventions above).
+ * The stage azimuth psi of a direction at angle e from the line of nodes in the part's
+ * tilted plane is psi = alpha + atan2(cos beta sin e, cos e), so
+ * e(phi_P) = atan2(sin(phi_G - phi_P - alpha), cos beta cos(phi_G - phi_P - alpha)).
+ * With phi_P_ref the phase of a reference whose spin is gamma_ref,
+ * gamma = gamma_ref + e(phi_P) - e(phi_P_ref), wrapped to (-pi, pi].  (Eq. 5 as printed,
+ * gamma = phi_P - phi_G - arctan(tan alpha / cos beta), is this relation with the phase
+ * read in the tilted plane from the direction above the stage x axis and the stage
+ * turning the other way.)  Host-only arithmetic. */
+int cyl_gamma_from_phase(double phi_p, double phi_p_ref, double alpha, double beta,
+                         double gamma_ref, double *gamma_out);
+
+/* Spin of the scanned part relative to a template (the initial volume of Sec. 2.2).  The
+ * plan must be posed with the part's alpha, beta and T (from cyl_estimate_pose) and the
+ * template's reference spin as gamma; its geometry must be circular.  The call projects,
+ * at the plan's pose, the template and its azimuthal mean (the axisymmetric part, whose
+ * centroid signal holds the geometric terms of an off-centre part); takes the phases of
+ * (c_scan - c_mean) and (c_template - c_mean); and converts them by cyl_gamma_from_phase.
+ * sino: device [n_proj][H][W] of sino_dtype; tmpl: device volume of tmpl_dtype.
+ * gamma_out: HOST double, the part's gamma.  diag_out: HOST double[4] = phi_P, amplitude,
+ * phi_P_ref, reference amplitude (amplitudes in mm), or NULL.  Uses the plan's scratch;
+ * synchronises `stream`.  Errors: CYL_EINVAL (frames geometry, band), CYL_ENOMEM,
+ * CYL_EDEVICE. */
+int cyl_estimate_gamma(cyl_plan *plan, const void *sino, cyl_dtype sino_dtype, const void *tmpl,
+                       cyl_dtype tmpl_dtype, const cyl_band *band, double *gamma_out,
+                       double *diag_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

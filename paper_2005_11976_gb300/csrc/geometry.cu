@@ -1,5 +1,5 @@
-// Host geometry (FP64): validation, the alignment of Eq. 1, per-view ray tables, the
-// wedge table, the volume tiling and each tile's candidate pixel box per view.
+// Host geometry (FP64): validation, the alignment of Eq. 1, per-view geometry tables and
+// the grid constants with the wedge table.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -12,7 +12,7 @@ namespace cylct {
 
 // Rotation of the alignment of Eq. 1: R = O^T with O = Rz(alpha) Rx(beta) Rz(gamma),
 // written out in closed form.
-static void alignment_matrix(const cyl_pose &ps, double R[3][3])
+void alignment_matrix(const cyl_pose &ps, double R[3][3])
 {
     const double ca = cos(ps.alpha), sa = sin(ps.alpha);
     const double cb = cos(ps.beta), sb = sin(ps.beta);
@@ -24,6 +24,41 @@ static void alignment_matrix(const cyl_pose &ps, double R[3][3])
     };
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) R[i][j] = O[j][i];
+}
+
+int validate_geom(const cyl_geom *geom)
+{
+    if (!geom) return set_error(CYL_EINVAL, "null geometry");
+    if (geom->n_proj < 1 || geom->det_w < 1 || geom->det_h < 1)
+        return set_error(CYL_EINVAL, "projections and detector size must be >= 1");
+    if ((int64_t)geom->det_w * geom->det_h >= (int64_t)1 << 30)
+        return set_error(CYL_EINVAL, "detector must have fewer than 2^30 pixels");
+    if (geom->frames_mm) {
+        for (int64_t k = 0; k < 12 * (int64_t)geom->n_proj; ++k)
+            if (!std::isfinite(geom->frames_mm[k])) return set_error(CYL_EINVAL, "non-finite frame");
+        for (int p = 0; p < geom->n_proj; ++p) {
+            const double *f = geom->frames_mm + 12 * (int64_t)p;
+            const double du = std::sqrt(f[6] * f[6] + f[7] * f[7] + f[8] * f[8]);
+            const double dv = std::sqrt(f[9] * f[9] + f[10] * f[10] + f[11] * f[11]);
+            if (!(du > 0.0) || !(dv > 0.0)) return set_error(CYL_EINVAL, "zero pixel step in a frame");
+            // the detector plane must not contain the source
+            const double n[3] = {f[7] * f[11] - f[8] * f[10], f[8] * f[9] - f[6] * f[11], f[6] * f[10] - f[7] * f[9]};
+            const double h = n[0] * (f[3] - f[0]) + n[1] * (f[4] - f[1]) + n[2] * (f[5] - f[2]);
+            if (!(std::fabs(h) > 0.0)) return set_error(CYL_EINVAL, "a frame's source lies in its detector plane");
+        }
+        return CYL_OK;
+    }
+    if (!(geom->sod_mm > 0.0) || !(geom->sdd_mm > geom->sod_mm) || !std::isfinite(geom->sdd_mm))
+        return set_error(CYL_EINVAL, "need 0 < SOD < SDD");
+    if (!(geom->pitch_u_mm > 0.0) || !(geom->pitch_v_mm > 0.0) ||
+        !std::isfinite(geom->pitch_u_mm) || !std::isfinite(geom->pitch_v_mm))
+        return set_error(CYL_EINVAL, "pixel pitch must be finite and > 0");
+    if (!std::isfinite(geom->off_u_mm) || !std::isfinite(geom->off_v_mm))
+        return set_error(CYL_EINVAL, "detector offset must be finite");
+    if (!geom->angles_rad) return set_error(CYL_EINVAL, "angles_rad is null");
+    for (int p = 0; p < geom->n_proj; ++p)
+        if (!std::isfinite(geom->angles_rad[p])) return set_error(CYL_EINVAL, "non-finite angle");
+    return CYL_OK;
 }
 
 int validate_scan(const cyl_grid *grid, const cyl_geom *geom, const cyl_pose *pose)
@@ -40,10 +75,8 @@ int validate_scan(const cyl_grid *grid, const cyl_geom *geom, const cyl_pose *po
     if (!(grid->radius_mm > 0.0) || !(grid->height_mm > 0.0) || !std::isfinite(grid->radius_mm) ||
         !std::isfinite(grid->height_mm))
         return set_error(CYL_EINVAL, "grid radius and height must be finite and > 0");
-    if (geom->n_proj < 1 || geom->det_w < 1 || geom->det_h < 1)
-        return set_error(CYL_EINVAL, "projections and detector size must be >= 1");
-    if ((int64_t)geom->det_w * geom->det_h >= (int64_t)1 << 30)
-        return set_error(CYL_EINVAL, "detector must have fewer than 2^30 pixels");
+    int rc = validate_geom(geom);
+    if (rc) return rc;
     const double pv[6] = {pose->alpha, pose->beta, pose->gamma, pose->tx, pose->ty, pose->tz};
     for (double v : pv)
         if (!std::isfinite(v)) return set_error(CYL_EINVAL, "non-finite pose");
@@ -51,29 +84,14 @@ int validate_scan(const cyl_grid *grid, const cyl_geom *geom, const cyl_pose *po
     const double sphere = std::sqrt(grid->radius_mm * grid->radius_mm +
                                     0.25 * grid->height_mm * grid->height_mm);
     if (geom->frames_mm) {
-        for (int64_t k = 0; k < 12 * (int64_t)geom->n_proj; ++k)
-            if (!std::isfinite(geom->frames_mm[k])) return set_error(CYL_EINVAL, "non-finite frame");
         for (int p = 0; p < geom->n_proj; ++p) {
             const double *f = geom->frames_mm + 12 * (int64_t)p;
-            const double du = std::sqrt(f[6] * f[6] + f[7] * f[7] + f[8] * f[8]);
-            const double dv = std::sqrt(f[9] * f[9] + f[10] * f[10] + f[11] * f[11]);
-            if (!(du > 0.0) || !(dv > 0.0)) return set_error(CYL_EINVAL, "zero pixel step in a frame");
             const double sx = f[0] - pose->tx, sy = f[1] - pose->ty, sz = f[2] - pose->tz;
             if (std::sqrt(sx * sx + sy * sy + sz * sz) <= sphere)
                 return set_error(CYL_EINVAL, "the grid cylinder reaches a frame's source");
         }
         return CYL_OK;
     }
-    if (!(geom->sod_mm > 0.0) || !(geom->sdd_mm > geom->sod_mm) || !std::isfinite(geom->sdd_mm))
-        return set_error(CYL_EINVAL, "need 0 < SOD < SDD");
-    if (!(geom->pitch_u_mm > 0.0) || !(geom->pitch_v_mm > 0.0) ||
-        !std::isfinite(geom->pitch_u_mm) || !std::isfinite(geom->pitch_v_mm))
-        return set_error(CYL_EINVAL, "pixel pitch must be finite and > 0");
-    if (!std::isfinite(geom->off_u_mm) || !std::isfinite(geom->off_v_mm))
-        return set_error(CYL_EINVAL, "detector offset must be finite");
-    if (!geom->angles_rad) return set_error(CYL_EINVAL, "angles_rad is null");
-    for (int p = 0; p < geom->n_proj; ++p)
-        if (!std::isfinite(geom->angles_rad[p])) return set_error(CYL_EINVAL, "non-finite angle");
     const double reach = sphere + std::sqrt(pose->tx * pose->tx + pose->ty * pose->ty + pose->tz * pose->tz);
     if (reach >= geom->sod_mm) return set_error(CYL_EINVAL, "the grid cylinder reaches the source");
     return CYL_OK;

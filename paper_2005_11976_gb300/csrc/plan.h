@@ -12,6 +12,8 @@ int set_error(int code, const char *msg);
 int cuda_error(cudaError_t e, const char *what);
 
 // geometry.cu
+int validate_geom(const cyl_geom *geom);   // acquisition only (no grid, no pose)
+void alignment_matrix(const cyl_pose &pose, double R[3][3]);   // X' = R (X - T)
 int validate_scan(const cyl_grid *grid, const cyl_geom *geom, const cyl_pose *pose);
 void build_grid(const cyl_grid &grid, const cyl_geom &geom, GridDev &g, std::vector<float2> &trig);
 void build_views(const cyl_geom &geom, const cyl_pose &pose, std::vector<ProjGeom> &geo);
@@ -70,6 +72,8 @@ struct cyl_plan {
     float *d_x32 = nullptr;
     size_t x32_cap = 0;
     void *d_stage[4] = {nullptr, nullptr, nullptr, nullptr};  // sino, x0, w, x_out
+    void *d_gamma = nullptr;       // scratch of cyl_estimate_gamma
+    size_t gamma_cap = 0;
     size_t stage_cap[4] = {0, 0, 0, 0};
 
     cudaStream_t ws = nullptr;

@@ -28,6 +28,8 @@ CYL_EPENDING = -7
 CYL_ECANCELLED = -8
 
 CYL_F32, CYL_F16, CYL_BF16 = 0, 1, 2
+CYL_MAX_BATCH = 4096
+CYL_MAX_DET_SIDE = 262143
 KIND_FORWARD, KIND_BACK, KIND_UPDATE = 0, 1, 2
 
 
@@ -89,9 +91,27 @@ class cyl_server_stats(ctypes.Structure):
                 ("hbm_in_use", ctypes.c_int64)]
 
 
+class cyl_pose_params(ctypes.Structure):
+    _fields_ = [("threshold", ctypes.c_double), ("dilate_px", ctypes.c_int32),
+                ("roi", ctypes.c_int32 * 4), ("max_iter", ctypes.c_int32),
+                ("gamma", ctypes.c_double)]
+
+
+class cyl_pose_info(ctypes.Structure):
+    _fields_ = [("top_mm", ctypes.c_double * 3), ("bottom_mm", ctypes.c_double * 3),
+                ("rms_mm", ctypes.c_double * 2), ("iters", ctypes.c_int32 * 2),
+                ("n_views", ctypes.c_int32), ("status", ctypes.c_int32)]
+
+
+class cyl_band(ctypes.Structure):
+    _fields_ = [("h_lo_mm", ctypes.c_double), ("h_hi_mm", ctypes.c_double),
+                ("half_width_mm", ctypes.c_double)]
+
+
 _VP = ctypes.c_void_p
 _I32 = ctypes.c_int32
 _I64 = ctypes.c_int64
+_D = ctypes.c_double
 
 # name -> (restype, argtypes); the exported C ABI
 SIGNATURES = {
@@ -131,6 +151,22 @@ SIGNATURES = {
                                             ctypes.POINTER(_I64)]),
     "cyl_plan_sizes": (ctypes.c_int, [_VP, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
                                       ctypes.POINTER(_I32), ctypes.POINTER(_I64)]),
+    "cyl_axis_corners": (ctypes.c_int, [ctypes.POINTER(cyl_geom), _VP, ctypes.c_int,
+                                        ctypes.POINTER(cyl_pose_params), _VP, _VP, _VP]),
+    "cyl_track_point": (ctypes.c_int, [ctypes.POINTER(cyl_geom), _VP, _I32, _VP, _VP]),
+    "cyl_estimate_pose": (ctypes.c_int, [ctypes.POINTER(cyl_geom), _VP, ctypes.c_int,
+                                         ctypes.POINTER(cyl_pose_params), ctypes.POINTER(cyl_pose),
+                                         ctypes.POINTER(cyl_pose_info), _VP]),
+    "cyl_estimate_pose_batch": (ctypes.c_int, [_I32, ctypes.POINTER(cyl_geom), _VP, ctypes.c_int,
+                                               ctypes.POINTER(cyl_pose_params), ctypes.POINTER(cyl_pose),
+                                               ctypes.POINTER(cyl_pose_info), _VP]),
+    "cyl_band_moments": (ctypes.c_int, [ctypes.POINTER(cyl_geom), ctypes.POINTER(cyl_pose), _VP,
+                                        ctypes.c_int, ctypes.POINTER(cyl_band), _VP, _VP]),
+    "cyl_gamma_from_phase": (ctypes.c_int, [_D, _D, _D, _D, _D, ctypes.POINTER(_D)]),
+    "cyl_pose_set_timing": (ctypes.c_int, [ctypes.c_int]),
+    "cyl_pose_kernel_time": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
+    "cyl_estimate_gamma": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, ctypes.c_int,
+                                          ctypes.POINTER(cyl_band), ctypes.POINTER(_D), _VP, _VP]),
 }
 
 _lock = threading.Lock()
@@ -301,6 +337,15 @@ class Plan:
     def cyl_plan_set_timing(self, enable: bool):
         _check(load().cyl_plan_set_timing(self.h, int(enable)), "cyl_plan_set_timing")
 
+    def cyl_estimate_gamma(self, sino, sino_dtype, tmpl, tmpl_dtype, band_, stream=None):
+        """(gamma, (phi_P, amplitude, phi_P_ref, reference amplitude))."""
+        g = ctypes.c_double()
+        diag = (ctypes.c_double * 4)()
+        _check(load().cyl_estimate_gamma(self.h, ptr(sino), sino_dtype, ptr(tmpl), tmpl_dtype,
+                                         ctypes.byref(band_), ctypes.byref(g), diag, stream_ptr(stream)),
+               "cyl_estimate_gamma")
+        return g.value, tuple(diag)
+
     def cyl_plan_kernel_time(self, kind: int):
         ms, n = ctypes.c_double(), _I64()
         _check(load().cyl_plan_kernel_time(self.h, kind, ctypes.byref(ms), ctypes.byref(n)),
@@ -335,6 +380,83 @@ def cyl_sart_tune_batch(plans, sinos, sino_dtype, x0s, ws, params, x_outs, x_dty
     ho = _ptr_array(x_outs)
     _check(load().cyl_sart_tune_batch(n, hp, hs, sino_dtype, hx0, hw, ctypes.byref(params), ho,
                                       x_dtype, stream_ptr(stream)), "cyl_sart_tune_batch")
+
+
+def pose_params(threshold, dilate_px=0, roi=(0, 0, 0, 0), max_iter=100, gamma=0.0) -> cyl_pose_params:
+    return cyl_pose_params(float(threshold), int(dilate_px), (ctypes.c_int32 * 4)(*roi), int(max_iter),
+                           float(gamma))
+
+
+def band(h_lo_mm, h_hi_mm, half_width_mm) -> cyl_band:
+    return cyl_band(float(h_lo_mm), float(h_hi_mm), float(half_width_mm))
+
+
+def _info_dict(f: cyl_pose_info) -> dict:
+    return dict(top=np.array(f.top_mm[:]), bottom=np.array(f.bottom_mm[:]), rms=tuple(f.rms_mm),
+                iters=tuple(f.iters), n_views=f.n_views, status=f.status)
+
+
+def cyl_axis_corners(scan, sino, sino_dtype, params, corners_out, counts_out=None, stream=None):
+    """Corner pixels of every projection of ``scan``'s geometry (device outputs)."""
+    _, geom, _, keep = structs_from_scan(scan)
+    _check(load().cyl_axis_corners(ctypes.byref(geom), ptr(sino), sino_dtype, ctypes.byref(params),
+                                   ptr(corners_out), ptr(counts_out), stream_ptr(stream)),
+           "cyl_axis_corners")
+
+
+def cyl_track_point(scan, track, max_iter, out, stream=None):
+    _, geom, _, keep = structs_from_scan(scan)
+    _check(load().cyl_track_point(ctypes.byref(geom), ptr(track), int(max_iter), ptr(out),
+                                  stream_ptr(stream)), "cyl_track_point")
+
+
+def cyl_estimate_pose(scan, sino, sino_dtype, params, stream=None):
+    """(pose tuple (alpha, beta, gamma, tx, ty, tz), info dict)."""
+    _, geom, _, keep = structs_from_scan(scan)
+    pose, info = cyl_pose(), cyl_pose_info()
+    _check(load().cyl_estimate_pose(ctypes.byref(geom), ptr(sino), sino_dtype, ctypes.byref(params),
+                                    ctypes.byref(pose), ctypes.byref(info), stream_ptr(stream)),
+           "cyl_estimate_pose")
+    return (pose.alpha, pose.beta, pose.gamma, pose.tx, pose.ty, pose.tz), _info_dict(info)
+
+
+def cyl_estimate_pose_batch(scans, sinos, sino_dtype, params, stream=None):
+    """Poses and info dicts of many scans; ``params`` is one cyl_pose_params or a list."""
+    n = len(scans)
+    made = [structs_from_scan(s) for s in scans]
+    geoms = (cyl_geom * n)(*[m[1] for m in made])
+    prms = params if isinstance(params, (list, tuple)) else [params] * n
+    hp = (cyl_pose_params * n)(*prms)
+    poses, infos = (cyl_pose * n)(), (cyl_pose_info * n)()
+    _check(load().cyl_estimate_pose_batch(n, geoms, _ptr_array(sinos), sino_dtype, hp, poses, infos,
+                                          stream_ptr(stream)), "cyl_estimate_pose_batch")
+    return ([(p.alpha, p.beta, p.gamma, p.tx, p.ty, p.tz) for p in poses],
+            [_info_dict(f) for f in infos])
+
+
+def cyl_band_moments(scan, pose, sino, sino_dtype, band_, moments_out, stream=None):
+    _, geom, _, keep = structs_from_scan(scan)
+    cp = cyl_pose(*pose)
+    _check(load().cyl_band_moments(ctypes.byref(geom), ctypes.byref(cp), ptr(sino), sino_dtype,
+                                   ctypes.byref(band_), ptr(moments_out), stream_ptr(stream)),
+           "cyl_band_moments")
+
+
+def cyl_pose_set_timing(enable: bool):
+    _check(load().cyl_pose_set_timing(int(enable)), "cyl_pose_set_timing")
+
+
+def cyl_pose_kernel_time(kind: int):
+    ms, n = ctypes.c_double(), _I64()
+    _check(load().cyl_pose_kernel_time(int(kind), ctypes.byref(ms), ctypes.byref(n)), "cyl_pose_kernel_time")
+    return ms.value, n.value
+
+
+def cyl_gamma_from_phase(phi_p, phi_p_ref, alpha, beta, gamma_ref=0.0) -> float:
+    g = ctypes.c_double()
+    _check(load().cyl_gamma_from_phase(float(phi_p), float(phi_p_ref), float(alpha), float(beta),
+                                       float(gamma_ref), ctypes.byref(g)), "cyl_gamma_from_phase")
+    return g.value
 
 
 def cyl_log_transform(counts, in_dtype, i0, p_out, out_dtype, n, stream=None):

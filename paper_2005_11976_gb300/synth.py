@@ -31,7 +31,7 @@ import math
 import numpy as np
 
 BASE_SEED = 20051197
-WORKLOAD_INDEX = {"tiny": 0, "medium": 1, "precision": 2, "batched": 3, "serving": 4}
+WORKLOAD_INDEX = {"tiny": 0, "medium": 1, "precision": 2, "batched": 3, "serving": 4, "pose": 5}
 
 
 @dataclasses.dataclass
@@ -100,21 +100,47 @@ def limited_arc(n_proj: int, last_angle_deg: float) -> np.ndarray:
     return np.deg2rad(last_angle_deg) * np.arange(n_proj) / max(n_proj - 1, 1)
 
 
-def frames_from_circular(scan: Scan) -> np.ndarray:
+def frames_from_circular(scan: Scan, stage_y_mm: float = 0.0) -> np.ndarray:
     """The (n_proj, 12) frames (source, pixel (0, 0) centre, pixel steps du, dv, in stage
     coordinates) of a circular scan: the stage turn of each projection applied to the
-    fixed source and detector."""
+    fixed source and detector.  ``stage_y_mm`` moves the turning stage sideways (along
+    the detector's u) off the line from the source to the detector centre."""
     out = np.zeros((scan.n_proj, 12))
     u0 = -0.5 * (scan.det_w - 1) * scan.pitch_u + scan.off_u
     v0 = -0.5 * (scan.det_h - 1) * scan.pitch_v + scan.off_v
+    y = stage_y_mm
     for p, phi in enumerate(scan.angles):
         c, s_ = math.cos(phi), math.sin(phi)
         rot = lambda v: (c * v[0] + s_ * v[1], -s_ * v[0] + c * v[1], v[2])
-        out[p, 0:3] = rot((-scan.sod, 0.0, 0.0))
-        out[p, 3:6] = rot((scan.sdd - scan.sod, u0, v0))
+        out[p, 0:3] = rot((-scan.sod, -y, 0.0))
+        out[p, 3:6] = rot((scan.sdd - scan.sod, u0 - y, v0))
         out[p, 6:9] = rot((0.0, scan.pitch_u, 0.0))
         out[p, 9:12] = rot((0.0, 0.0, scan.pitch_v))
     return out
+
+
+# Table 1 (circular cone-beam scans of medical devices) and Sec. 3.2.  The detector is
+# the named 1944 x 1536 panel with 0.0748 mm pixels (the printed 0.748 mm would make it
+# 1.45 m wide at 791 mm from the source).  The part (KN-S) is 64 mm high with an 8 mm
+# radius; the five scans of each part put the stage's axis on these detector columns.
+TABLE1 = dict(sod=679.0, sdd=791.0, n_proj=21, last_angle_deg=200.0, det_w=1944, det_h=1536,
+              pixel_mm=0.0748, height_mm=64.0, radius_mm=8.0)
+TABLE1_STAGE_COLUMNS = (185.2, 574.5, 963.9, 1353.25, 1742.6)
+
+
+def table1_scan(grid=(1, 1, 8)) -> Scan:
+    """Table 1's acquisition, on a coarse grid over the part (for synthesising its
+    projections from a radial profile)."""
+    t = TABLE1
+    return Scan(grid[0], grid[1], grid[2], t["radius_mm"], t["height_mm"], t["sod"], t["sdd"],
+                t["det_w"], t["det_h"], t["pixel_mm"], t["pixel_mm"],
+                limited_arc(t["n_proj"], t["last_angle_deg"]))
+
+
+def stage_shift_mm(column_px: float) -> float:
+    """Sideways stage position that puts the stage axis's shadow on a detector column."""
+    t = TABLE1
+    return (column_px - 0.5 * (t["det_w"] - 1)) * t["pixel_mm"] * t["sod"] / t["sdd"]
 
 
 def conveyor_frames(n_proj: int, sod: float, sdd: float, det_w: int, det_h: int, pitch: float,

@@ -114,3 +114,40 @@ def test_server_config_validation_without_gpu(lib):
     assert lib.cyl_server_destroy(None) == cylct.CYL_OK
     assert lib.cyl_poll(None, 1, None) == cylct.CYL_EINVAL
     assert lib.cyl_sart_solve_batch(-1, None, None, 0, None, None, None, None, 0, None) == cylct.CYL_EINVAL
+
+
+def test_pose_calls_validate_on_the_host(lib, orc):
+    from oracle import pose as op
+    scan = synth.tiny_scan()
+    grid, geom, pose, keep = cylct.structs_from_scan(scan)
+    info = cylct.cyl_pose_info()
+    out = cylct.cyl_pose()
+    bad = [cylct.pose_params(float("nan")), cylct.pose_params(0.1, -1),
+           cylct.pose_params(0.1, 0, (5, 5, 0, 10)), cylct.pose_params(0.1, 0, (0, 40, 0, 10)),
+           cylct.pose_params(0.1, gamma=float("inf"))]
+    for prm in bad:
+        assert lib.cyl_estimate_pose(ctypes.byref(geom), 1, 0, ctypes.byref(prm), ctypes.byref(out),
+                                     ctypes.byref(info), None) == cylct.CYL_EINVAL
+    prm = cylct.pose_params(0.1)
+    assert lib.cyl_estimate_pose(ctypes.byref(geom), None, 0, ctypes.byref(prm), ctypes.byref(out),
+                                 None, None) == cylct.CYL_EINVAL
+    assert lib.cyl_estimate_pose(ctypes.byref(geom), 1, 9, ctypes.byref(prm), ctypes.byref(out),
+                                 None, None) == cylct.CYL_EINVAL
+    wide = cylct.cyl_geom(100.0, 400.0, geom.n_proj, cylct.CYL_MAX_DET_SIDE + 1, 2, 1.0, 1.0, 0.0, 0.0,
+                          geom.angles_rad)
+    assert lib.cyl_axis_corners(ctypes.byref(wide), 1, 0, ctypes.byref(prm), 1, None, None) == cylct.CYL_EINVAL
+    assert lib.cyl_estimate_pose_batch(-1, None, None, 0, None, None, None, None) == cylct.CYL_EINVAL
+    assert lib.cyl_estimate_pose_batch(0, None, None, 0, None, None, None, None) == cylct.CYL_OK
+    cp = cylct.cyl_pose(0, 0, 0, 0, 0, 0)
+    for b in (cylct.band(1.0, 1.0, 2.0), cylct.band(-1.0, 1.0, 0.0), cylct.band(float("nan"), 1.0, 1.0)):
+        assert lib.cyl_band_moments(ctypes.byref(geom), ctypes.byref(cp), 1, 0, ctypes.byref(b), 1,
+                                    None) == cylct.CYL_EINVAL
+    assert lib.cyl_estimate_gamma(None, None, 0, None, 0, None, None, None, None) == cylct.CYL_EINVAL
+    # Eq. 5 is host arithmetic: the library and the oracle agree
+    rng = np.random.default_rng(0)
+    for _ in range(20):
+        a = rng.uniform(-3, 3, 5)
+        a[3] = abs(a[3]) % 1.4
+        assert cylct.cyl_gamma_from_phase(*a) == pytest.approx(op.gamma_from_phase(*a), abs=1e-14)
+    g = ctypes.c_double()
+    assert lib.cyl_gamma_from_phase(float("nan"), 0, 0, 0, 0, ctypes.byref(g)) == cylct.CYL_EINVAL
