@@ -347,8 +347,8 @@ int cyl_plan_sizes(const cyl_plan *plan, int64_t *n_vox, int64_t *n_pix, int32_t
  * Levenberg-Marquardt with the analytic Jacobian of V_i, in FP64: start on the first
  * tracked projection's ray at the stage origin's distance from its source; damping mu =
  * 1e-3 on the diagonal of J^T J, divided by 10 after an accepted step (not below 1e-15)
- * and multiplied by 10 after a rejected one; stop after a step shorter than
- * 1e-10 (1 + |X|) mm, when mu exceeds 1e15, or after max_iter steps.
+ * and multiplied by 10 after a rejected one; stop after a step (accepted or not) shorter
+ * than 1e-10 (1 + |X|) mm, when mu exceeds 1e15, or after max_iter steps.
  *
  * Pose.  The two axis points fix five of the six degrees of freedom of Eq. 1: the axis
  * direction a = (top - bottom) / |top - bottom| = (sin alpha sin beta,

@@ -157,8 +157,8 @@ def track_point(views, obs, valid, max_iter: int = 100):
     """Eq. 4 by Levenberg-Marquardt: minimise the squared detector distances (mm)
     between the track and V_i(X).  Damping mu starts at 1e-3, falls tenfold after an
     accepted step (not below 1e-15) and rises tenfold after a rejected one; the
-    iteration stops after a step shorter than 1e-10 (1 + |X|), when mu exceeds 1e15, or
-    after max_iter steps.  Returns (X, rms distance in mm, steps taken)."""
+    iteration stops after a step (accepted or not) shorter than 1e-10 (1 + |X|), when mu
+    exceeds 1e15, or after max_iter steps.  Returns (X, rms distance in mm, steps taken)."""
     valid = np.asarray(valid, bool)
     X = initial_point(views, obs, valid)
     mu = 1e-3
@@ -179,15 +179,14 @@ def track_point(views, obs, valid, max_iter: int = 100):
         Xn = X + step
         rn, Jn = _residuals(views, obs, valid, Xn)
         cn = float(rn @ rn)
+        small = np.linalg.norm(step) <= 1e-10 * (1.0 + np.linalg.norm(Xn if cn < cost else X))
         if cn < cost:
             X, r, J, cost = Xn, rn, Jn, cn
             mu = max(mu / 10.0, 1e-15)
-            if np.linalg.norm(step) <= 1e-10 * (1.0 + np.linalg.norm(X)):
-                break
         else:
             mu *= 10.0
-            if mu > 1e15:
-                break
+        if small or mu > 1e15:
+            break
     return X, math.sqrt(cost / int(valid.sum())), it
 
 

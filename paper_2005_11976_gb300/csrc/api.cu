@@ -212,7 +212,10 @@ extern "C" int cyl_project(cyl_plan *plan, const void *vol, cyl_dtype vol_dtype,
     }
     OnPlanStream ps{plan, (cudaStream_t)stream};
     CYL_CUDA(ps.begin());
-    CYL_CUDA(launch_fp_rays(plan->scan_dev(), plan->p_fp, p0, np, vol, vol_dtype, q, nullptr, 0, plan->ws));
+    // the projector writes the rays of positive chord only
+    if (plan->use_list) CYL_CUDA(cudaMemsetAsync(q, 0, sizeof(float) * n, plan->ws));
+    CYL_CUDA(launch_fp_rays(plan->scan_dev(), plan->p_fp, p0, np, vol, vol_dtype, q, nullptr, 0, plan->ws,
+                            plan->ray_list()));
     if (sino_dtype != CYL_F32)
         CYL_CUDA(launch_convert(q, CYL_F32, sino_out, sino_dtype, (int64_t)n, plan->ws));
     CYL_CUDA(ps.end());
@@ -233,7 +236,7 @@ extern "C" int cyl_backproject(cyl_plan *plan, const void *sino, cyl_dtype sino_
     CYL_CUDA(cudaMemsetAsync(vol_out, 0, sizeof(float) * plan->n_vox, plan->ws));
     if (colsum_out) CYL_CUDA(cudaMemsetAsync(colsum_out, 0, sizeof(float) * plan->n_vox, plan->ws));
     CYL_CUDA(launch_bp_rays(plan->scan_dev(), plan->p_bp, p0, np, sino, sino_dtype, nullptr, nullptr,
-                            vol_out, colsum_out, plan->ws));
+                            vol_out, colsum_out, plan->ws, plan->ray_list()));
     CYL_CUDA(ps.end());
     return CYL_OK;
 }

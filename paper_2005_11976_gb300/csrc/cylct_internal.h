@@ -44,6 +44,14 @@ struct ScanDev {
     int *sched;             // two self-resetting work counters per kernel kind (kSched)
 };
 
+// Per pose, the rays of positive chord, view by view in ray order (plan ray index), made
+// where many rays miss the grid; act = null: every ray is a task.  Passed to the ray
+// kernels as their last argument.
+struct RayList {
+    const uint32_t *act;
+    const int64_t *act_off;   // [n_proj + 1]: start of each view's rays in act
+};
+
 constexpr int kSplit = 16;  // pieces per ray recorded at set-up (P divides it)
 constexpr int kPiecesFp = 8, kPiecesBp = 4;   // default pieces per ray of each kernel
 constexpr int kSched = 8;   // ints of scheduler state per plan
@@ -90,14 +98,20 @@ int valid_pieces(int P);
 int default_pieces(int kind /* 0 forward, 1 back */);
 // Cut every ray of all views into kSplit pieces of equal step counts (once per pose).
 cudaError_t launch_split(const ScanDev &sd, int n_proj, uint16_t *split, cudaStream_t st);
+// The list of rays of positive chord (ScanDev::act) of every view, in ray order.
+constexpr int kActChunk = 1024;   // rays per block of the list's count and fill passes
+cudaError_t launch_active(const ScanDev &sd, int n_proj, int64_t *chunk, uint32_t *act, int64_t *act_off,
+                          cudaStream_t st);
 // q[v][pix] = (A x)_j for views p0 .. p0+np-1 (overwritten); zero_buf (if not null) is
 // cleared on the way.
 cudaError_t launch_fp_rays(const ScanDev &sd, int P, int p0, int np, const void *x, cyl_dtype xt,
-                           float *q, float2 *zero_buf, int64_t zero_len, cudaStream_t st);
+                           float *q, float2 *zero_buf, int64_t zero_len, cudaStream_t st,
+                           const RayList &rl = RayList{nullptr, nullptr});
 // q != null: SART residual (y - q) / L into nd; q == null: pure A^T y into nd, or into
 // num / den (den may be null) when nd is null.  The outputs accumulate.
 cudaError_t launch_bp_rays(const ScanDev &sd, int P, int p0, int np, const void *y, cyl_dtype yt,
-                           const float *q, float2 *nd, float *num, float *den, cudaStream_t st);
+                           const float *q, float2 *nd, float *num, float *den, cudaStream_t st,
+                           const RayList &rl = RayList{nullptr, nullptr});
 cudaError_t launch_update_nd(int64_t n_vox, const float2 *nd, const UpdateArgs &u, cudaStream_t st);
 cudaError_t launch_count_rays(const ScanDev &sd, int p0, int np, unsigned long long *counts,
                               cudaStream_t st);

@@ -167,3 +167,62 @@ void build_views(const cyl_geom &geom, const cyl_pose &pose, std::vector<ProjGeo
 }
 
 }  // namespace cylct
+
+namespace cylct {
+
+double hit_fraction_bound(const cyl_grid &grid, const cyl_geom &geom, const std::vector<ProjGeom> &geo)
+{
+    constexpr int kRim = 64;
+    const double W = geom.det_w, H = geom.det_h;
+    double covered = 0.0;
+    for (const ProjGeom &v : geo) {
+        // pixel coordinates (a, b) of an object point: D0 + a du + b dv on the line from S
+        const double n[3] = {v.du[1] * v.dv[2] - v.du[2] * v.dv[1], v.du[2] * v.dv[0] - v.du[0] * v.dv[2],
+                             v.du[0] * v.dv[1] - v.du[1] * v.dv[0]};
+        double e1[3], e2[3];
+        {
+            const double t1[3] = {v.dv[1] * n[2] - v.dv[2] * n[1], v.dv[2] * n[0] - v.dv[0] * n[2],
+                                  v.dv[0] * n[1] - v.dv[1] * n[0]};
+            const double t2[3] = {n[1] * v.du[2] - n[2] * v.du[1], n[2] * v.du[0] - n[0] * v.du[2],
+                                  n[0] * v.du[1] - n[1] * v.du[0]};
+            const double q1 = t1[0] * v.du[0] + t1[1] * v.du[1] + t1[2] * v.du[2];
+            const double q2 = t2[0] * v.dv[0] + t2[1] * v.dv[1] + t2[2] * v.dv[2];
+            for (int k = 0; k < 3; ++k) {
+                e1[k] = t1[k] / q1;
+                e2[k] = t2[k] / q2;
+            }
+        }
+        const double c0 = n[0] * (v.D0[0] - v.S[0]) + n[1] * (v.D0[1] - v.S[1]) + n[2] * (v.D0[2] - v.S[2]);
+        double a_lo = 1e300, a_hi = -1e300, b_lo = 1e300, b_hi = -1e300;
+        bool ok = true;
+        for (int side = 0; side < 2 && ok; ++side)
+            for (int k = 0; k < kRim; ++k) {
+                // rim points of a slightly larger polygon that contains the circle
+                const double th = 2.0 * M_PI * k / kRim, rr = grid.radius_mm / cos(M_PI / kRim);
+                const double X[3] = {rr * cos(th), rr * sin(th), (side ? 0.5 : -0.5) * grid.height_mm};
+                const double Y[3] = {X[0] - v.S[0], X[1] - v.S[1], X[2] - v.S[2]};
+                const double nY = n[0] * Y[0] + n[1] * Y[1] + n[2] * Y[2];
+                const double t = c0 / nY;
+                if (!(t > 0.0) || !std::isfinite(t)) {   // the point is not in front of the source
+                    ok = false;
+                    break;
+                }
+                const double P[3] = {v.S[0] + t * Y[0] - v.D0[0], v.S[1] + t * Y[1] - v.D0[1],
+                                     v.S[2] + t * Y[2] - v.D0[2]};
+                const double a = e1[0] * P[0] + e1[1] * P[1] + e1[2] * P[2];
+                const double b = e2[0] * P[0] + e2[1] * P[1] + e2[2] * P[2];
+                a_lo = std::min(a_lo, a);
+                a_hi = std::max(a_hi, a);
+                b_lo = std::min(b_lo, b);
+                b_hi = std::max(b_hi, b);
+            }
+        if (!ok) return 1.0;
+        // pixel centres a in [0, W - 1]; a box [a_lo, a_hi] holds at most this many
+        const double wa = std::max(0.0, std::min(W - 1.0, std::floor(a_hi)) - std::max(0.0, std::ceil(a_lo)) + 1.0);
+        const double wb = std::max(0.0, std::min(H - 1.0, std::floor(b_hi)) - std::max(0.0, std::ceil(b_lo)) + 1.0);
+        covered += wa * wb;
+    }
+    return covered / (W * H * (double)geo.size());
+}
+
+}  // namespace cylct

@@ -70,7 +70,10 @@ extern "C" int cyl_project_noalloc(cyl_plan *plan, const void *vol, cyl_dtype vo
     cudaStream_t user = (cudaStream_t)stream, st = plan->ws;
     cudaError_t e = cudaEventRecord(plan->ev_in, user);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(st, plan->ev_in, 0);
-    if (e == cudaSuccess) e = launch_fp_rays(plan->scan_dev(), plan->p_fp, p0, np, vol, vol_dtype, acc, nullptr, 0, st);
+    // the projector writes the rays of positive chord only
+    if (e == cudaSuccess && plan->use_list) e = cudaMemsetAsync(acc, 0, sizeof(float) * n, st);
+    if (e == cudaSuccess) e = launch_fp_rays(plan->scan_dev(), plan->p_fp, p0, np, vol, vol_dtype, acc, nullptr, 0, st,
+                                              plan->ray_list());
     if (e == cudaSuccess) e = launch_convert(acc, CYL_F32, sino_out, sino_dtype, n, st);
     if (e == cudaSuccess) e = cudaEventRecord(plan->ev_out, st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(user, plan->ev_out, 0);

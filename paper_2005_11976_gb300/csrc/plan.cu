@@ -79,6 +79,22 @@ int cyl_plan::upload_pose(const cyl_pose &po, cudaStream_t st)
     PL_CUDA(cudaMemcpyAsync(d_geo, h_geo, sizeof(ProjGeom) * geo.size(), cudaMemcpyHostToDevice, st));
     PL_CUDA(cudaEventRecord(ev_geo, st));
     PL_CUDA(launch_rays(g, d_geo, geom.n_proj, d_ray[0], d_ray[1], d_ray[2], st));
+    // list the rays that meet the grid when a quarter or more surely miss it: the list
+    // spares the projector and back-projector the empty rays but costs every task a load.
+    // Its buffers are made on the first pose that needs them (the list holds 32-bit ray
+    // indices, so plans of 2^32 rays or more never list).
+    const size_t n_rays = (size_t)geom.n_proj * n_pix;
+    const bool list = n_rays < ((size_t)1 << 32) && hit_fraction_bound(grid, geom, geo) < 0.75;
+    if (list && !d_act) {
+        const size_t cpv = ((size_t)n_pix + kActChunk - 1) / kActChunk;
+        int rc;
+        if ((rc = alloc(&d_act, sizeof(uint32_t) * n_rays))) return rc;
+        if ((rc = alloc(&d_act_off, sizeof(int64_t) * (geom.n_proj + 1)))) return rc;
+        if ((rc = alloc(&d_act_chunk, sizeof(int64_t) * cpv * geom.n_proj))) return rc;
+    }
+    if (list != use_list) drop_graphs();   // captured launches name the other kernels
+    use_list = list;
+    if (use_list) PL_CUDA(launch_active(scan_dev(), geom.n_proj, d_act_chunk, d_act, d_act_off, st));
     PL_CUDA(launch_split(scan_dev(), geom.n_proj, d_split, st));
     pose = po;
     return CYL_OK;
@@ -165,9 +181,9 @@ int cyl_plan::queue_sweep(const SolveState &s, cudaStream_t st, bool timed, int 
         cudaEvent_t *ev = timed ? next_events(4) : nullptr;
         if (timed && !ev) return set_error(CYL_EDEVICE, "event creation failed");
         if (ev) PL_CUDA(cudaEventRecordWithFlags(ev[0], st, rec_flags));
-        PL_CUDA(launch_fp_rays(sd, p_fp, p0, np, s.x_proj, s.x_proj_t, d_q, d_nd[b ^ 1], n_vox, st));
+        PL_CUDA(launch_fp_rays(sd, p_fp, p0, np, s.x_proj, s.x_proj_t, d_q, d_nd[b ^ 1], n_vox, st, ray_list()));
         if (ev) PL_CUDA(cudaEventRecordWithFlags(ev[1], st, rec_flags));
-        PL_CUDA(launch_bp_rays(sd, p_bp, p0, np, sino_p, s.sino_t, d_q, d_nd[b], nullptr, nullptr, st));
+        PL_CUDA(launch_bp_rays(sd, p_bp, p0, np, sino_p, s.sino_t, d_q, d_nd[b], nullptr, nullptr, st, ray_list()));
         if (ev) PL_CUDA(cudaEventRecordWithFlags(ev[2], st, rec_flags));
         PL_CUDA(launch_update_nd(n_vox, d_nd[b], upd, st));
         if (ev) PL_CUDA(cudaEventRecordWithFlags(ev[3], st, rec_flags));
@@ -349,9 +365,9 @@ int cyl_plan::tune(cudaStream_t st)
             for (int rep = 0; rep < 3; ++rep) {
                 PL_CUDA(cudaEventRecord(e[0], st));
                 if (kind == 0)
-                    PL_CUDA(launch_fp_rays(sd, P, 0, 1, d_x32, CYL_F32, d_q, nullptr, 0, st));
+                    PL_CUDA(launch_fp_rays(sd, P, 0, 1, d_x32, CYL_F32, d_q, nullptr, 0, st, ray_list()));
                 else
-                    PL_CUDA(launch_bp_rays(sd, P, 0, 1, d_q, CYL_F32, d_q, d_nd[0], nullptr, nullptr, st));
+                    PL_CUDA(launch_bp_rays(sd, P, 0, 1, d_q, CYL_F32, d_q, d_nd[0], nullptr, nullptr, st, ray_list()));
                 PL_CUDA(cudaEventRecord(e[1], st));
                 PL_CUDA(cudaEventSynchronize(e[1]));
                 float ms = 0.f;

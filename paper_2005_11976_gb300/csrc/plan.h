@@ -17,6 +17,9 @@ void alignment_matrix(const cyl_pose &pose, double R[3][3]);   // X' = R (X - T)
 int validate_scan(const cyl_grid *grid, const cyl_geom *geom, const cyl_pose *pose);
 void build_grid(const cyl_grid &grid, const cyl_geom &geom, GridDev &g, std::vector<float2> &trig);
 void build_views(const cyl_geom &geom, const cyl_pose &pose, std::vector<ProjGeom> &geo);
+// Upper bound on the fraction of a scan's rays that meet the grid cylinder: per view the
+// detector bounding box of the projected rim circles (the cylinder is their convex hull).
+double hit_fraction_bound(const cyl_grid &grid, const cyl_geom &geom, const std::vector<ProjGeom> &geo);
 
 // batch.cu: per round, the (scan, subset) items of a batched solve
 void batch_rounds(const std::vector<int> &n_proj, int subset, int n_iter,
@@ -64,6 +67,10 @@ struct cyl_plan {
     float4 *d_ray[3] = {nullptr, nullptr, nullptr};
     uint16_t *d_split = nullptr;   // [view][pixel][kSplit] cuts of each ray (per pose)
     int *d_sched = nullptr;        // work counters of the persistent kernels (kSched)
+    uint32_t *d_act = nullptr;     // rays of positive chord per view (ScanDev::act), or null
+    bool use_list = false;         // this pose's tasks come from d_act (many rays miss)
+    int64_t *d_act_off = nullptr;  // [n_proj + 1]
+    int64_t *d_act_chunk = nullptr; // chunk counts / offsets of the list's construction
     float *d_wscale = nullptr;
     float *d_q = nullptr;          // forward projections of one subset (FP32)
     size_t q_cap = 0;
@@ -109,6 +116,7 @@ struct cyl_plan {
         sd.sched = d_sched;
         return sd;
     }
+    cylct::RayList ray_list() const { return cylct::RayList{use_list ? d_act : nullptr, d_act_off}; }
 
     template <class T> int alloc(T **p, size_t nbytes)
     {

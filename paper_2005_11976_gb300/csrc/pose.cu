@@ -373,18 +373,20 @@ __device__ int track_lm(const ViewLM *__restrict__ vw, int64_t view0, int n, con
         const double Xn[3] = {X[0] + d[0], X[1] + d[1], X[2] + d[2]};
         double accn[10];
         normal_eqs(vw, view0, n, obs, Xn, accn);     // the trial's cost and, if kept, its equations
-        if (accn[9] < cost) {
+        const bool keep = accn[9] < cost;
+        const double *Xr = keep ? Xn : X;
+        const bool small = sqrt(dot3(d, d)) <= 1e-10 * (1.0 + sqrt(dot3(Xr, Xr)));
+        if (keep) {
             X[0] = Xn[0];
             X[1] = Xn[1];
             X[2] = Xn[2];
             mu = fmax(mu / 10.0, 1e-15);
             for (int q = 0; q < 10; ++q) acc[q] = accn[q];
             cost = acc[9];
-            if (sqrt(dot3(d, d)) <= 1e-10 * (1.0 + sqrt(dot3(X, X)))) break;
         } else {
             mu *= 10.0;
-            if (mu > 1e15) break;
         }
+        if (small || mu > 1e15) break;
     }
     rms = sqrt(cost / nobs);
     return nobs;
@@ -1056,8 +1058,11 @@ extern "C" int cyl_estimate_gamma(cyl_plan *plan, const void *sino, cyl_dtype si
     default: k_theta_mean<<<nb, tb, 0, ws>>>(static_cast<const float *>(tmpl), g.n_h, g.n_t, g.n_r, mean);
     }
     PO_CUDA(cudaGetLastError());
-    PO_CUDA(launch_fp_rays(plan->scan_dev(), plan->p_fp, 0, n, tmpl, tmpl_dtype, q_tmpl, nullptr, 0, ws));
-    PO_CUDA(launch_fp_rays(plan->scan_dev(), plan->p_fp, 0, n, mean, CYL_F32, q_mean, nullptr, 0, ws));
+    PO_CUDA(cudaMemsetAsync(q_tmpl, 0, sizeof(float) * 2 * nq, ws));   // rays that miss the grid
+    PO_CUDA(launch_fp_rays(plan->scan_dev(), plan->p_fp, 0, n, tmpl, tmpl_dtype, q_tmpl, nullptr, 0, ws,
+                           plan->ray_list()));
+    PO_CUDA(launch_fp_rays(plan->scan_dev(), plan->p_fp, 0, n, mean, CYL_F32, q_mean, nullptr, 0, ws,
+                           plan->ray_list()));
     const float hw = (float)band->half_width_mm;
     PO_CUDA(launch_band(sino, sino_dtype, n, g.det_w, g.det_h, d_bv, hw, m, ws));
     PO_CUDA(launch_band(q_tmpl, CYL_F32, n, g.det_w, g.det_h, d_bv, hw, m + 2 * n, ws));

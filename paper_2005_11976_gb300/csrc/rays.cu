@@ -158,61 +158,160 @@ __global__ void __launch_bounds__(256) k_split(ScanDev sd, int64_t n_rays, uint1
     out[kSplit - 1] = (uint16_t)fminf(n_est, 65535.f);
 }
 
+// ------------------------------------------------------------------ active rays
+
+// Rays of positive chord (u_out > u_in), listed per pose in ray order: each block counts
+// one chunk of kActChunk rays of one view, one block scans the chunk counts, and each
+// block then writes its chunk's rays at the chunk's offset (ranks from warp ballots).
+__device__ __forceinline__ bool ray_active(const ScanDev &sd, int64_t rec)
+{
+    const float4 c = __ldg(sd.ray_c + rec);
+    return c.y > c.x;
+}
+
+__global__ void __launch_bounds__(256) k_act_count(ScanDev sd, int64_t npix, int cpv, int64_t *chunk)
+{
+    const int64_t p = blockIdx.y, j0 = (int64_t)blockIdx.x * kActChunk;
+    int n = 0;
+    for (int k = threadIdx.x; k < kActChunk; k += blockDim.x) {
+        const int64_t j = j0 + k;
+        n += __syncthreads_count(j < npix && ray_active(sd, p * npix + j));
+    }
+    if (threadIdx.x == 0) chunk[p * cpv + blockIdx.x] = n;
+}
+
+// Exclusive scan of the chunk counts in place (one block of 1024 threads), then the
+// per-view offsets: act_off[p] = offset of view p's first chunk, act_off[n_proj] = total.
+__global__ void __launch_bounds__(1024) k_act_scan(int64_t *chunk, int64_t n, int n_proj, int cpv, int64_t *act_off)
+{
+    __shared__ int64_t part[1024];
+    const int64_t per = (n + blockDim.x - 1) / blockDim.x;
+    const int64_t a = threadIdx.x * per, b = min(a + per, n);
+    int64_t s = 0;
+    for (int64_t i = a; i < b; ++i) s += chunk[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t run = 0;
+        for (int t = 0; t < (int)blockDim.x; ++t) {
+            const int64_t v = part[t];
+            part[t] = run;
+            run += v;
+        }
+        act_off[n_proj] = run;
+    }
+    __syncthreads();
+    int64_t run = part[threadIdx.x];
+    for (int64_t i = a; i < b; ++i) {
+        const int64_t v = chunk[i];
+        chunk[i] = run;
+        run += v;
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < n_proj; p += blockDim.x) act_off[p] = chunk[(int64_t)p * cpv];
+}
+
+__global__ void __launch_bounds__(256) k_act_fill(ScanDev sd, int64_t npix, int cpv, const int64_t *chunk,
+                                                  uint32_t *act)
+{
+    __shared__ int warp_n[8];
+    const int64_t p = blockIdx.y, j0 = (int64_t)blockIdx.x * kActChunk;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int64_t pos = chunk[p * cpv + blockIdx.x];
+    for (int k = 0; k < kActChunk; k += blockDim.x) {
+        const int64_t j = j0 + k + threadIdx.x;
+        const bool on = j < npix && ray_active(sd, p * npix + j);
+        const unsigned m = __ballot_sync(0xffffffffu, on);
+        if (lane == 0) warp_n[w] = __popc(m);
+        __syncthreads();
+        int before = 0, total = 0;
+        for (int q = 0; q < 8; ++q) {
+            before += q < w ? warp_n[q] : 0;
+            total += warp_n[q];
+        }
+        if (on) act[pos + before + __popc(m & ((1u << lane) - 1u))] = (uint32_t)(p * npix + j);
+        pos += total;
+        __syncthreads();
+    }
+}
+
+// Tasks of a launch over the rays of views p0 .. : with LIST, the launch's part
+// [a0, a0 + n_task) of the list of rays of positive chord; else every ray.
+template <bool LIST>
+__device__ __forceinline__ void launch_tasks(const RayList &rl, int p0, int64_t npix, int64_t n_rays, int64_t &a0,
+                                             int64_t &n_task)
+{
+    a0 = 0;
+    n_task = n_rays;
+    if (LIST) {
+        a0 = rl.act_off[p0];
+        n_task = rl.act_off[p0 + n_rays / npix] - a0;
+    }
+}
+
 // ------------------------------------------------------------------ single scan
 
-// Rays j in [0, n_rays) are rays p0 * H * W + j of the plan; lgP = log2(P).
-template <class T>
+// Rays j in [0, n_rays) are rays p0 * H * W + j of the plan; lgP = log2(P).  With LIST
+// only the rays of positive chord are tasks and only their q is written.
+template <class T, bool LIST>
 __global__ void __launch_bounds__(256)
 k_fp(ScanDev sd, int lgP, int p0, int64_t n_rays, const T *__restrict__ x, float *__restrict__ q,
-     float2 *zero_buf, int64_t zero_len)
+     float2 *zero_buf, int64_t zero_len, RayList rl)
 {
     extern __shared__ float2 s_trig[];
     stage_trig_smem(sd.trig, sd.g.n_t, s_trig);
     zero_slice(zero_buf, zero_len, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
                (int64_t)gridDim.x * blockDim.x);
     const int P = 1 << lgP, lane = threadIdx.x & 31;
-    const int64_t base = (int64_t)p0 * sd.g.det_w * sd.g.det_h;
-    const int64_t n_wt = ((n_rays << lgP) + 31) >> 5, span = task_span(n_wt);
+    const int64_t npix = (int64_t)sd.g.det_w * sd.g.det_h, base = (int64_t)p0 * npix;
+    int64_t a0, n_task;
+    launch_tasks<LIST>(rl, p0, npix, n_rays, a0, n_task);
+    const int64_t n_wt = ((n_task << lgP) + 31) >> 5, span = task_span(n_wt);
     for (;;) {
         const int f = fetch_task(sd.sched);
         if (f >= span) break;
         const int64_t wt = task_of(f, n_wt);
         if (wt < 0) continue;
-        const int64_t t = wt * 32 + lane, r = t >> lgP;
+        const int64_t t = wt * 32 + lane, i = t >> lgP;
         const int piece = (int)(t & (P - 1));
         float acc = 0.f;
-        if (r < n_rays) {
+        int64_t r = -1;
+        if (i < n_task) {
+            r = LIST ? (int64_t)__ldg(rl.act + a0 + i) - base : i;
             const RayRec rr = ray_at(sd, base + r);
             float ua, ub;
             if (piece_bounds(rr, sd.split + (base + r) * kSplit, piece, P, ua, ub))
                 acc = fp_walk<T>(sd.g, s_trig, rr, ua, ub, x);
         }
         acc = ray_sum(acc, P);
-        if (piece == 0 && r < n_rays) q[r] = acc;
+        if (piece == 0 && r >= 0) q[r] = acc;
     }
     retire(sd.sched);
 }
 
 // y, q: the launch's rays (indexed like r); SART: residual (y - q) / L, else y
-template <class S, bool SART>
+template <class S, bool SART, bool LIST>
 __global__ void __launch_bounds__(256)
 k_bp(ScanDev sd, int lgP, int p0, int64_t n_rays, const S *__restrict__ y, const float *__restrict__ q,
-     float2 *nd, float *num, float *den)
+     float2 *nd, float *num, float *den, RayList rl)
 {
     extern __shared__ float2 s_trig[];
     stage_trig_smem(sd.trig, sd.g.n_t, s_trig);
     const int P = 1 << lgP, lane = threadIdx.x & 31;
-    const int64_t base = (int64_t)p0 * sd.g.det_w * sd.g.det_h;
-    const int64_t n_wt = ((n_rays + 31) >> 5) << lgP, span = task_span(n_wt);
+    const int64_t npix = (int64_t)sd.g.det_w * sd.g.det_h, base = (int64_t)p0 * npix;
+    int64_t a0, n_task;
+    launch_tasks<LIST>(rl, p0, npix, n_rays, a0, n_task);
+    const int64_t n_wt = ((n_task + 31) >> 5) << lgP, span = task_span(n_wt);
     int *sched = sd.sched + 2;
     for (;;) {
         const int f = fetch_task(sched);
         if (f >= span) break;
         const int64_t wt = task_of(f, n_wt);
         if (wt < 0) continue;
-        const int64_t r = (wt >> lgP) * 32 + lane;
+        const int64_t i = (wt >> lgP) * 32 + lane;
         const int piece = (int)(wt & (P - 1));
-        if (r >= n_rays) continue;
+        if (i >= n_task) continue;
+        const int64_t r = LIST ? (int64_t)__ldg(rl.act + a0 + i) - base : i;
         const RayRec rr = ray_at(sd, base + r);
         float ua, ub;
         if (!piece_bounds(rr, sd.split + (base + r) * kSplit, piece, P, ua, ub)) continue;
@@ -458,8 +557,21 @@ cudaError_t launch_split(const ScanDev &sd, int n_proj, uint16_t *split, cudaStr
     return cudaGetLastError();
 }
 
+cudaError_t launch_active(const ScanDev &sd, int n_proj, int64_t *chunk, uint32_t *act, int64_t *act_off,
+                          cudaStream_t st)
+{
+    const int64_t npix = (int64_t)sd.g.det_w * sd.g.det_h;
+    const int cpv = (int)((npix + kActChunk - 1) / kActChunk);
+    if (n_proj <= 0 || npix <= 0) return cudaSuccess;
+    const dim3 grid((unsigned)cpv, (unsigned)n_proj);
+    k_act_count<<<grid, 256, 0, st>>>(sd, npix, cpv, chunk);
+    k_act_scan<<<1, 1024, 0, st>>>(chunk, (int64_t)n_proj * cpv, n_proj, cpv, act_off);
+    k_act_fill<<<grid, 256, 0, st>>>(sd, npix, cpv, chunk, act);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fp_rays(const ScanDev &sd, int P, int p0, int np, const void *x, cyl_dtype xt,
-                           float *q, float2 *zero_buf, int64_t zero_len, cudaStream_t st)
+                           float *q, float2 *zero_buf, int64_t zero_len, cudaStream_t st, const RayList &rl)
 {
     if (np <= 0) return cudaSuccess;
     const int lgP = log2_pieces(P, kPiecesFp);
@@ -468,14 +580,19 @@ cudaError_t launch_fp_rays(const ScanDev &sd, int P, int p0, int np, const void 
     const size_t smem = trig_smem(sd.g.n_t);
     return dispatch_t(xt, [&](auto *tx) {
         using T = std::remove_pointer_t<decltype(tx)>;
-        const unsigned blocks = persistent_blocks((const void *)k_fp<T>, smem);
-        k_fp<T><<<blocks, 256, smem, st>>>(sd, lgP, p0, n_rays, (const T *)x, q, zero_buf, zero_len);
+        if (rl.act) {
+            const unsigned blocks = persistent_blocks((const void *)k_fp<T, true>, smem);
+            k_fp<T, true><<<blocks, 256, smem, st>>>(sd, lgP, p0, n_rays, (const T *)x, q, zero_buf, zero_len, rl);
+        } else {
+            const unsigned blocks = persistent_blocks((const void *)k_fp<T, false>, smem);
+            k_fp<T, false><<<blocks, 256, smem, st>>>(sd, lgP, p0, n_rays, (const T *)x, q, zero_buf, zero_len, rl);
+        }
         return cudaGetLastError();
     });
 }
 
 cudaError_t launch_bp_rays(const ScanDev &sd, int P, int p0, int np, const void *y, cyl_dtype yt,
-                           const float *q, float2 *nd, float *num, float *den, cudaStream_t st)
+                           const float *q, float2 *nd, float *num, float *den, cudaStream_t st, const RayList &rl)
 {
     if (np <= 0) return cudaSuccess;
     const int lgP = log2_pieces(P, kPiecesBp);
@@ -484,12 +601,16 @@ cudaError_t launch_bp_rays(const ScanDev &sd, int P, int p0, int np, const void 
     const size_t smem = trig_smem(sd.g.n_t);
     return dispatch_t(yt, [&](auto *ty) {
         using S = std::remove_pointer_t<decltype(ty)>;
+        auto go = [&](auto kern) {
+            const unsigned blocks = persistent_blocks((const void *)kern, smem);
+            kern<<<blocks, 256, smem, st>>>(sd, lgP, p0, n_rays, (const S *)y, q, nd, num, den, rl);
+        };
         if (q) {
-            const unsigned blocks = persistent_blocks((const void *)k_bp<S, true>, smem);
-            k_bp<S, true><<<blocks, 256, smem, st>>>(sd, lgP, p0, n_rays, (const S *)y, q, nd, num, den);
+            if (rl.act) go(k_bp<S, true, true>);
+            else go(k_bp<S, true, false>);
         } else {
-            const unsigned blocks = persistent_blocks((const void *)k_bp<S, false>, smem);
-            k_bp<S, false><<<blocks, 256, smem, st>>>(sd, lgP, p0, n_rays, (const S *)y, q, nd, num, den);
+            if (rl.act) go(k_bp<S, false, true>);
+            else go(k_bp<S, false, false>);
         }
         return cudaGetLastError();
     });

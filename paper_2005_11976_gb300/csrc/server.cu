@@ -145,6 +145,8 @@ size_t cyl_server::scan_footprint(const Part &pt, int n_proj) const
                + 2 * (size_t)subset * npix * sizeof(float)         // projection buffers
                + 2 * (size_t)pt.n_vox * sizeof(float2)            // (num, den) accumulators
                + (size_t)n_proj * npix * kSplit * sizeof(uint16_t)  // ray cuts
+               + (size_t)n_proj * npix * sizeof(uint32_t)          // list of rays of positive chord (if made)
+               + ((size_t)n_proj * ((npix + kActChunk - 1) / kActChunk) + n_proj + 1) * sizeof(int64_t)
                + (size_t)n_proj * sizeof(ProjGeom)
                + 64 * 1024;                                        // small tables
     if (cfg.storage != CYL_F32) b += (size_t)pt.n_vox * sizeof(float);

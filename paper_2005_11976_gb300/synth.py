@@ -31,7 +31,8 @@ import math
 import numpy as np
 
 BASE_SEED = 20051197
-WORKLOAD_INDEX = {"tiny": 0, "medium": 1, "precision": 2, "batched": 3, "serving": 4, "pose": 5}
+WORKLOAD_INDEX = {"tiny": 0, "medium": 1, "precision": 2, "batched": 3, "serving": 4, "pose": 5,
+                  "table1": 6}
 
 
 @dataclasses.dataclass
