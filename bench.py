@@ -592,7 +592,9 @@ def run_table1(args):
         "rays_per_sweep": n_pix * scan.n_proj, "rays_hitting_the_grid": rays_hit, "segments_per_sweep": segs,
         "grays_per_s": 2 * sweeps * n_pix * scan.n_proj / tp / 1e9,
         "rel_err_vs_oracle_one_subset": parity, "clocks": clk,
-        "gpu_launches": args.steps * 2 * (2 + sweeps * scan.n_proj * 3),
+        # per step: projector, back-projector and update per view and sweep in both solves,
+        # and the weight maximum and scale of the weighted one
+        "gpu_launches": args.steps * (2 * sweeps * scan.n_proj * 3 + 2),
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
