@@ -186,6 +186,31 @@ def test_small_part_on_a_wide_detector(lib, orc):
     assert gu.rel_l2(xs, orc.sart(o, p, x0=x, n_iter=2, lam=0.5)) <= TOL_FP32
 
 
+def test_sart_update_fallbacks(lib, orc):
+    """The FP32 update takes 16-byte vectors when the voxel count is a multiple of 4 and
+    the arrays are aligned; an odd grid and a misaligned output take the scalar path.
+    Both give the oracle's iterate."""
+    import torch
+    s = synth.Scan(5, 9, 7, 6.0, 8.0, 60.0, 200.0, 23, 19, 1.3, 1.3, synth.full_circle(4) + 0.1)
+    s.alpha, s.beta, s.tx = 0.3, 0.15, 0.4
+    assert (s.n_h * s.n_theta * s.n_r) % 4 != 0
+    rng = np.random.default_rng(31)
+    x0 = rng.uniform(0.0, 0.05, size=s.vol_shape)
+    p = rng.uniform(0.0, 1.0, size=s.sino_shape)
+    want = orc.sart(osetup(orc, s), p, x0=x0, n_iter=2, lam=0.5)
+    with cylct.Plan(s) as plan:
+        assert gu.rel_l2(gu.sart(plan, p, x0=x0, n_iter=2, lam=0.5), want) <= TOL_FP32
+    s2 = dataclasses.replace(s, n_r=8)                      # 360 voxels: the vector path ...
+    want2 = orc.sart(osetup(orc, s2), p, x0=np.zeros(s2.vol_shape), n_iter=2, lam=0.5)
+    with cylct.Plan(s2) as plan:
+        buf = torch.zeros(s2.n_vox + 1, device="cuda")
+        out = buf[1:].view(s2.vol_shape)                     # ... unless the output is misaligned
+        plan.cyl_sart_solve(gu.to_dev(p), cylct.CYL_F32, None, None,
+                            cylct.sart_params(n_iter=2, lam=0.5), out, cylct.CYL_F32)
+        assert gu.rel_l2(gu.to_np(out), want2) <= TOL_FP32
+        assert gu.rel_l2(gu.sart(plan, p, n_iter=2, lam=0.5), want2) <= TOL_FP32
+
+
 def test_empty_projection_range(lib):
     import torch
     s = tilted_scan(n_proj=2)
