@@ -35,6 +35,16 @@ int orc_num_threads(void)
 #endif
 }
 
+/* Threads of the following parallel loops (timing the oracle on one core). */
+void orc_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* Sec. 2, Eq. 1: the pose's three intrinsic zxz Euler angles give the object's
  * orientation O = Rz(alpha) Rx(beta) Rz(gamma), so gamma is the spin about the object's
  * own axis (the "internal rotation" of Sec. 2.1, azimuthal phase).  The alignment

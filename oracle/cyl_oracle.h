@@ -87,6 +87,7 @@ int orc_sart(const orc_setup *s, const double *p, const double *x0, const double
 void orc_log_transform(const double *I, double I0, long n, double *p);
 
 int orc_num_threads(void);
+void orc_set_num_threads(int n);
 
 #ifdef __cplusplus
 }

@@ -81,6 +81,8 @@ def load():
             lib.orc_sart.restype = ctypes.c_int
             lib.orc_log_transform.argtypes = [_D, ctypes.c_double, ctypes.c_long, _D]
             lib.orc_num_threads.restype = ctypes.c_int
+            lib.orc_set_num_threads.argtypes = [ctypes.c_int]
+            lib.orc_set_num_threads.restype = None
             _lib = lib
     return _lib
 
@@ -146,6 +148,11 @@ def _f64(a):
 
 def num_threads() -> int:
     return int(load().orc_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's parallel loops from now on (n >= 1)."""
+    load().orc_set_num_threads(int(n))
 
 
 def pose_matrix(alpha, beta, gamma) -> np.ndarray:
