@@ -459,18 +459,23 @@ int cyl_gamma_from_phase(double phi_p, double phi_p_ref, double alpha, double be
                          double gamma_ref, double *gamma_out);
 
 /* Spin of the scanned part relative to a template (the initial volume of Sec. 2.2).  The
- * plan must be posed with the part's alpha, beta and T (from cyl_estimate_pose) and the
- * template's reference spin as gamma; its geometry must be circular.  The call projects,
+ * plan must be posed with the part's alpha, beta and T (from cyl_estimate_pose) and a
+ * starting reference spin as gamma; its geometry must be circular.  The call projects,
  * at the plan's pose, the template and its azimuthal mean (the axisymmetric part, whose
  * centroid signal holds the geometric terms of an off-centre part); takes the phases of
  * (c_scan - c_mean) and (c_template - c_mean); and converts them by cyl_gamma_from_phase.
- * sino: device [n_proj][H][W] of sino_dtype; tmpl: device volume of tmpl_dtype.
- * gamma_out: HOST double, the part's gamma.  diag_out: HOST double[4] = phi_P, amplitude,
- * phi_P_ref, reference amplitude (amplitudes in mm), or NULL.  Uses the plan's scratch;
- * synchronises `stream`.  Errors: CYL_EINVAL (frames geometry, band), CYL_ENOMEM,
- * CYL_EDEVICE. */
+ * Each further pass (passes > 1) re-poses the template at the current estimate and
+ * repeats: on a partial arc (Table 1: 200 deg) the first-harmonic fits of two signals of
+ * different phase pick up different shares of their higher harmonics, and the bias
+ * vanishes as the reference's phase approaches the scan's.  On return the plan is posed
+ * with the estimated gamma (no change for passes = 1 when the estimate equals the
+ * starting spin).  sino: device [n_proj][H][W] of sino_dtype; tmpl: device volume of
+ * tmpl_dtype; passes: 1 .. 16.  gamma_out: HOST double, the part's gamma.  diag_out: HOST
+ * double[4] = phi_P, amplitude, phi_P_ref, reference amplitude of the last pass
+ * (amplitudes in mm), or NULL.  Uses the plan's scratch; synchronises `stream`.  Errors:
+ * CYL_EINVAL (frames geometry, band, passes), CYL_ENOMEM, CYL_EDEVICE. */
 int cyl_estimate_gamma(cyl_plan *plan, const void *sino, cyl_dtype sino_dtype, const void *tmpl,
-                       cyl_dtype tmpl_dtype, const cyl_band *band, double *gamma_out,
+                       cyl_dtype tmpl_dtype, const cyl_band *band, int32_t passes, double *gamma_out,
                        double *diag_out, void *stream);
 
 #ifdef __cplusplus

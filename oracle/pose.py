@@ -311,21 +311,29 @@ def azimuthal_mean(x):
     return np.broadcast_to(x.mean(axis=1, keepdims=True), x.shape).copy()
 
 
-def estimate_gamma(s: _orc.Setup, sino, tmpl, h_lo: float, h_hi: float, half_width: float):
+def estimate_gamma(s: _orc.Setup, sino, tmpl, h_lo: float, h_hi: float, half_width: float,
+                   passes: int = 1):
     """Spin of the scanned part relative to a template.  ``s`` carries the part's alpha,
-    beta and T and the template's spin as gamma.  The template and its azimuthal mean are
-    projected at that pose; the centroid signal of the mean (the geometric part, present
-    in all three) is subtracted from those of the scan and the template before their
-    phases are taken.  Returns (gamma, (phi_P, amplitude, phi_P_ref, reference
-    amplitude))."""
+    beta and T and the template's starting spin as gamma.  The template and its azimuthal
+    mean are projected at that pose; the centroid signal of the mean (the geometric part,
+    present in all three) is subtracted from those of the scan and the template before
+    their phases are taken.  Every further pass projects the template at the current
+    estimate and repeats.  Returns (gamma, (phi_P, amplitude, phi_P_ref, reference
+    amplitude) of the last pass)."""
+    import dataclasses
     pose = (s.alpha, s.beta, s.gamma, s.tx, s.ty, s.tz)
-    q_tmpl = _orc.project(s, tmpl)
     q_mean = _orc.project(s, azimuthal_mean(tmpl))
-    c_scan, c_tmpl, c_mean = (band_signal(s, pose, q, h_lo, h_hi, half_width)
-                              for q in (sino, q_tmpl, q_mean))
+    c_scan = band_signal(s, pose, sino, h_lo, h_hi, half_width)
+    c_mean = band_signal(s, pose, q_mean, h_lo, h_hi, half_width)
     ph, amp = phase(s.angles, c_scan - c_mean)
-    ph_ref, amp_ref = phase(s.angles, c_tmpl - c_mean)
-    return gamma_from_phase(ph, ph_ref, s.alpha, s.beta, s.gamma), (ph, amp, ph_ref, amp_ref)
+    gamma, diag = s.gamma, None
+    for _ in range(passes):
+        sr = dataclasses.replace(s, gamma=gamma)
+        c_tmpl = band_signal(sr, pose, _orc.project(sr, tmpl), h_lo, h_hi, half_width)
+        ph_ref, amp_ref = phase(s.angles, c_tmpl - c_mean)
+        gamma = gamma_from_phase(ph, ph_ref, s.alpha, s.beta, gamma)
+        diag = (ph, amp, ph_ref, amp_ref)
+    return gamma, diag
 
 
 def eq5_printed(phi_p: float, phi_g: float, alpha: float, beta: float) -> float:

@@ -1005,13 +1005,14 @@ extern "C" int cyl_gamma_from_phase(double phi_p, double phi_p_ref, double alpha
 }
 
 extern "C" int cyl_estimate_gamma(cyl_plan *plan, const void *sino, cyl_dtype sino_dtype, const void *tmpl,
-                                  cyl_dtype tmpl_dtype, const cyl_band *band, double *gamma_out,
+                                  cyl_dtype tmpl_dtype, const cyl_band *band, int32_t passes, double *gamma_out,
                                   double *diag_out, void *stream)
 {
     if (!plan || !band || !gamma_out) return set_error(CYL_EINVAL, "null plan, band or gamma_out");
     if (plan->geom.frames_mm) return set_error(CYL_EINVAL, "the phase needs a circular geometry");
     if (!valid_dt(sino_dtype) || !valid_dt(tmpl_dtype)) return set_error(CYL_EINVAL, "bad dtype");
     if (!sino || !tmpl) return set_error(CYL_EINVAL, "null array");
+    if (passes < 1 || passes > 16) return set_error(CYL_EINVAL, "passes must be in 1 .. 16");
     if (!(band->h_lo_mm < band->h_hi_mm) || !std::isfinite(band->h_lo_mm) || !std::isfinite(band->h_hi_mm) ||
         !(band->half_width_mm > 0.0) || !std::isfinite(band->half_width_mm))
         return set_error(CYL_EINVAL, "band needs finite h_lo < h_hi and half_width > 0");
@@ -1028,7 +1029,7 @@ extern "C" int cyl_estimate_gamma(cyl_plan *plan, const void *sino, cyl_dtype si
     std::lock_guard<std::mutex> lock(plan->mu);
     const int n = plan->geom.n_proj;
     const size_t nq = (size_t)n * plan->n_pix;
-    std::vector<BandView> bv;
+    std::vector<BandView> bv;   // the band follows the axis, which a spin leaves in place
     band_table(plan->geom, plan->pose, *band, bv);
     const size_t o_mean = 0, o_q = align_up(sizeof(float) * plan->n_vox);
     const size_t o_m = align_up(o_q + sizeof(float) * 2 * nq), o_ang = align_up(o_m + sizeof(double) * 6 * n);
@@ -1058,25 +1059,45 @@ extern "C" int cyl_estimate_gamma(cyl_plan *plan, const void *sino, cyl_dtype si
     default: k_theta_mean<<<nb, tb, 0, ws>>>(static_cast<const float *>(tmpl), g.n_h, g.n_t, g.n_r, mean);
     }
     PO_CUDA(cudaGetLastError());
-    PO_CUDA(cudaMemsetAsync(q_tmpl, 0, sizeof(float) * 2 * nq, ws));   // rays that miss the grid
-    PO_CUDA(launch_fp_rays(plan->scan_dev(), plan->p_fp, 0, n, tmpl, tmpl_dtype, q_tmpl, nullptr, 0, ws,
-                           plan->ray_list()));
+    const float hw = (float)band->half_width_mm;
+    // spin-independent: the scan's moments and the azimuthal mean's projection
+    PO_CUDA(cudaMemsetAsync(q_mean, 0, sizeof(float) * nq, ws));   // rays that miss the grid stay 0
     PO_CUDA(launch_fp_rays(plan->scan_dev(), plan->p_fp, 0, n, mean, CYL_F32, q_mean, nullptr, 0, ws,
                            plan->ray_list()));
-    const float hw = (float)band->half_width_mm;
     PO_CUDA(launch_band(sino, sino_dtype, n, g.det_w, g.det_h, d_bv, hw, m, ws));
-    PO_CUDA(launch_band(q_tmpl, CYL_F32, n, g.det_w, g.det_h, d_bv, hw, m + 2 * n, ws));
     PO_CUDA(launch_band(q_mean, CYL_F32, n, g.det_w, g.det_h, d_bv, hw, m + 4 * n, ws));
-    k_phase<<<1, 32, 0, ws>>>(m, m + 2 * n, m + 4 * n, reinterpret_cast<const double *>(b + o_ang), n,
-                              reinterpret_cast<double *>(b + o_out));
-    PO_CUDA(cudaGetLastError());
-    double out[4];
-    PO_CUDA(cudaMemcpyAsync(out, b + o_out, sizeof out, cudaMemcpyDeviceToHost, ws));
-    PO_CUDA(cudaStreamSynchronize(ws));
+    double out[4] = {0, 0, 0, 0}, gamma = plan->pose.gamma;
+    for (int pass = 0; pass < passes; ++pass) {
+        if (pass > 0) {   // the template's spin moves to the current estimate
+            cyl_pose ps = plan->pose;
+            ps.gamma = gamma;
+            if ((rc = plan->upload_pose(ps, ws))) return rc;
+        }
+        PO_CUDA(cudaMemsetAsync(q_tmpl, 0, sizeof(float) * nq, ws));
+        PO_CUDA(cudaMemsetAsync(m + 2 * n, 0, sizeof(double) * 2 * n, ws));
+        PO_CUDA(launch_fp_rays(plan->scan_dev(), plan->p_fp, 0, n, tmpl, tmpl_dtype, q_tmpl, nullptr, 0, ws,
+                               plan->ray_list()));
+        PO_CUDA(launch_band(q_tmpl, CYL_F32, n, g.det_w, g.det_h, d_bv, hw, m + 2 * n, ws));
+        k_phase<<<1, 32, 0, ws>>>(m, m + 2 * n, m + 4 * n, reinterpret_cast<const double *>(b + o_ang), n,
+                                  reinterpret_cast<double *>(b + o_out));
+        PO_CUDA(cudaGetLastError());
+        PO_CUDA(cudaMemcpyAsync(out, b + o_out, sizeof out, cudaMemcpyDeviceToHost, ws));
+        PO_CUDA(cudaStreamSynchronize(ws));
+        double next;
+        if ((rc = cyl_gamma_from_phase(out[0], out[2], plan->pose.alpha, plan->pose.beta, plan->pose.gamma, &next)))
+            return rc;
+        gamma = next;
+    }
+    if (passes > 1 || gamma != plan->pose.gamma) {   // leave the plan posed with the estimate
+        cyl_pose ps = plan->pose;
+        ps.gamma = gamma;
+        if ((rc = plan->upload_pose(ps, ws))) return rc;
+    }
     PO_CUDA(cudaEventRecord(plan->ev_out, ws));
     PO_CUDA(cudaStreamWaitEvent(user, plan->ev_out, 0));
     if (diag_out) memcpy(diag_out, out, sizeof out);
-    return cyl_gamma_from_phase(out[0], out[2], plan->pose.alpha, plan->pose.beta, plan->pose.gamma, gamma_out);
+    *gamma_out = gamma;
+    return CYL_OK;
 }
 
 extern "C" int cyl_pose_set_timing(int enable)

@@ -166,7 +166,7 @@ SIGNATURES = {
     "cyl_pose_set_timing": (ctypes.c_int, [ctypes.c_int]),
     "cyl_pose_kernel_time": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
     "cyl_estimate_gamma": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, ctypes.c_int,
-                                          ctypes.POINTER(cyl_band), ctypes.POINTER(_D), _VP, _VP]),
+                                          ctypes.POINTER(cyl_band), _I32, ctypes.POINTER(_D), _VP, _VP]),
 }
 
 _lock = threading.Lock()
@@ -337,12 +337,13 @@ class Plan:
     def cyl_plan_set_timing(self, enable: bool):
         _check(load().cyl_plan_set_timing(self.h, int(enable)), "cyl_plan_set_timing")
 
-    def cyl_estimate_gamma(self, sino, sino_dtype, tmpl, tmpl_dtype, band_, stream=None):
-        """(gamma, (phi_P, amplitude, phi_P_ref, reference amplitude))."""
+    def cyl_estimate_gamma(self, sino, sino_dtype, tmpl, tmpl_dtype, band_, passes=1, stream=None):
+        """(gamma, (phi_P, amplitude, phi_P_ref, reference amplitude) of the last pass)."""
         g = ctypes.c_double()
         diag = (ctypes.c_double * 4)()
         _check(load().cyl_estimate_gamma(self.h, ptr(sino), sino_dtype, ptr(tmpl), tmpl_dtype,
-                                         ctypes.byref(band_), ctypes.byref(g), diag, stream_ptr(stream)),
+                                         ctypes.byref(band_), int(passes), ctypes.byref(g), diag,
+                                         stream_ptr(stream)),
                "cyl_estimate_gamma")
         return g.value, tuple(diag)
 

@@ -32,7 +32,7 @@ import numpy as np
 
 BASE_SEED = 20051197
 WORKLOAD_INDEX = {"tiny": 0, "medium": 1, "precision": 2, "batched": 3, "serving": 4, "pose": 5,
-                  "table1": 6}
+                  "table1": 6, "phase": 7}
 
 
 @dataclasses.dataclass
@@ -328,6 +328,20 @@ def part_phantom(scan: Scan, azimuths: np.ndarray, removed: int = -1,
         f = _disk_fraction(scan, rc * math.cos(phi), rc * math.sin(phi), rad)
         # the insert replaces the shell material it occupies
         x += hf[:, None, None] * f[None, :, :] * (insert_mu - radial[None, None, :])
+    return x
+
+
+def pinned_tube(scan: Scan, r_in: float = 3.0, pin_r: float = 0.8, pin_c: float = 5.5,
+                pin_az: float = 0.0, pin_h=(-16.0, 16.0), mu_wall: float = 0.05,
+                mu_pin: float = 0.3) -> np.ndarray:
+    """A tube (wall r_in .. R) with one metal pin off the axis: radius pin_r, centred at
+    radius pin_c and azimuth pin_az, over heights pin_h.  The pin gives the part an
+    azimuthal phase (Sec. 2.1)."""
+    wall = mu_wall * _annulus_fraction(scan, r_in, scan.radius)
+    x = np.broadcast_to(wall, scan.vol_shape).copy()
+    f = _disk_fraction(scan, pin_c * math.cos(pin_az), pin_c * math.sin(pin_az), pin_r)
+    hf = _slab_fraction(scan, pin_h[0], pin_h[1])
+    x += hf[:, None, None] * f[None, :, :] * (mu_pin - wall[None, None, :])
     return x
 
 

@@ -142,7 +142,7 @@ def test_pose_calls_validate_on_the_host(lib, orc):
     for b in (cylct.band(1.0, 1.0, 2.0), cylct.band(-1.0, 1.0, 0.0), cylct.band(float("nan"), 1.0, 1.0)):
         assert lib.cyl_band_moments(ctypes.byref(geom), ctypes.byref(cp), 1, 0, ctypes.byref(b), 1,
                                     None) == cylct.CYL_EINVAL
-    assert lib.cyl_estimate_gamma(None, None, 0, None, 0, None, None, None, None) == cylct.CYL_EINVAL
+    assert lib.cyl_estimate_gamma(None, None, 0, None, 0, None, 1, None, None, None) == cylct.CYL_EINVAL
     # Eq. 5 is host arithmetic: the library and the oracle agree
     rng = np.random.default_rng(0)
     for _ in range(20):

@@ -184,7 +184,8 @@ def test_band_moments_match_oracle(lib, orc, op, code):
     assert np.all(np.abs(got[:, 1] - want[:, 1]) <= 1e-11 * scale)
 
 
-def test_estimate_gamma_matches_oracle(lib, orc, op):
+@pytest.mark.parametrize("passes", [1, 2])
+def test_estimate_gamma_matches_oracle(lib, orc, op, passes):
     rng = np.random.default_rng(5)
     for trial in range(2):
         s = insert_part()
@@ -194,11 +195,18 @@ def test_estimate_gamma_matches_oracle(lib, orc, op):
         g_true, g_ref = rng.uniform(-3, 3), rng.uniform(-1, 1)
         sino = orc.project(orc.Setup(**dataclasses.replace(s, gamma=g_true).fields()), x)
         sref = dataclasses.replace(s, gamma=g_ref)
-        want, wdiag = op.estimate_gamma(orc.Setup(**sref.fields()), sino, x, -5.0, 5.0, 100.0)
+        want, wdiag = op.estimate_gamma(orc.Setup(**sref.fields()), sino, x, -5.0, 5.0, 100.0, passes=passes)
         with cylct.Plan(sref) as plan:
             g, diag = plan.cyl_estimate_gamma(gu.to_dev(sino), cylct.CYL_F32, gu.to_dev(x), cylct.CYL_F32,
-                                              cylct.band(-5.0, 5.0, 100.0))
+                                              cylct.band(-5.0, 5.0, 100.0), passes=passes)
+            # the plan is left posed with the estimate: its projection of the template
+            # equals the oracle's at that spin
+            q = gu.project(plan, x, 0, 2)
         assert abs(op.wrap(g - want)) < 1e-4
         np.testing.assert_allclose(np.array(diag)[[1, 3]], np.array(wdiag)[[1, 3]], rtol=1e-4)
         assert abs(math.degrees(op.wrap(g - g_true))) < 0.6
-        assert cylct.cyl_gamma_from_phase(wdiag[0], wdiag[2], s.alpha, s.beta, g_ref) == pytest.approx(want, abs=1e-12)
+        q_want = orc.project(orc.Setup(**dataclasses.replace(s, gamma=g).fields()), x, 0, 2)
+        assert gu.rel_l2(q, q_want) <= 1e-5
+        if passes == 1:
+            assert cylct.cyl_gamma_from_phase(wdiag[0], wdiag[2], s.alpha, s.beta, g_ref) == \
+                pytest.approx(want, abs=1e-12)
