@@ -211,6 +211,34 @@ def test_sart_update_fallbacks(lib, orc):
         assert gu.rel_l2(gu.sart(plan, p, n_iter=2, lam=0.5), want2) <= TOL_FP32
 
 
+def test_dense_and_listed_poses_alternate(lib, orc):
+    """Re-posing moves a plan between dense tasks (the grid fills the detector) and the
+    list of rays that meet the grid (the part moved sideways, most rays miss); captured
+    sweeps follow the switch.  Every pose matches the oracle."""
+    s = synth.Scan(5, 16, 6, 6.0, 10.0, 60.0, 240.0, 28, 24, 1.6, 1.6, synth.full_circle(3) + 0.2)
+    poses = [(0.2, 0.1, 0.3, 0.0, 0.0, 0.0), (0.2, 0.1, 0.3, 14.0, 7.0, 0.0), (0.2, 0.1, 0.3, 0.5, -0.5, 0.0),
+             (0.2, 0.1, 0.3, -14.0, 7.0, 1.0)]
+    rng = np.random.default_rng(41)
+    x = rng.uniform(0.0, 0.05, size=s.vol_shape)
+    p = rng.uniform(0.0, 1.0, size=s.sino_shape)
+    s0 = dataclasses.replace(s, alpha=0.2, beta=0.1, gamma=0.3)
+    with cylct.Plan(s0) as plan:
+        bytes_dense = plan.sizes()[3]
+        for i, pose in enumerate(poses):
+            if i:
+                plan.cyl_plan_set_pose(pose)
+            sp = dataclasses.replace(s, alpha=pose[0], beta=pose[1], gamma=pose[2], tx=pose[3], ty=pose[4], tz=pose[5])
+            o = osetup(orc, sp)
+            want = orc.project(o, x)
+            got = gu.project(plan, x)
+            assert np.all(got[want == 0] == 0)
+            assert np.abs(got - want).max() <= TOL_FP32 * max(np.abs(want).max(), 1.0)
+            xs = gu.sart(plan, p, x0=x, n_iter=2, lam=0.5)
+            assert gu.rel_l2(xs, orc.sart(o, p, x0=x, n_iter=2, lam=0.5)) <= TOL_FP32
+            if i == 1:
+                assert plan.sizes()[3] > bytes_dense      # the list was made for this pose
+
+
 def test_empty_projection_range(lib):
     import torch
     s = tilted_scan(n_proj=2)
