@@ -126,6 +126,7 @@ int batch_run(int32_t n, cyl_plan *const *plans, const void *const *sinos, cyl_d
     int rc;
     int64_t max_vox = 0;
     std::vector<BatchScan> scans(n);
+    bool lists = false;   // some scan takes its tasks from its list of rays
     std::vector<int> n_proj(n);
     for (int i = 0; i < n; ++i) {
         cyl_plan *pl = plans[i];
@@ -140,6 +141,8 @@ int batch_run(int32_t n, cyl_plan *const *plans, const void *const *sinos, cyl_d
         if (!tune && !x0) BT_CUDA(cudaMemsetAsync(xo, 0, xb * pl->n_vox, bs));
         BatchScan &sc = scans[i];
         sc.sd = pl->scan_dev();
+        sc.rl = pl->ray_list();
+        lists = lists || pl->use_list;
         sc.sino = sinos[i];
         sc.x_proj = xo;
         sc.q[0] = pl->d_q;
@@ -211,7 +214,8 @@ int batch_run(int32_t n, cyl_plan *const *plans, const void *const *sinos, cyl_d
                         ce = cudaEventRecord(e[0], bs);
                         if (ce == cudaSuccess)
                             ce = launch_batch_round(d_scans, d_items, d_n, n, 0, max_vox, P, P,
-                                                    part ? kRoundBp : kRoundFp, d_sched, xt, sino_dtype, x16t, bs);
+                                                    part ? kRoundBp : kRoundFp, d_sched, xt, sino_dtype, x16t, bs,
+                                                    lists);
                         if (ce == cudaSuccess) ce = cudaEventRecord(e[1], bs);
                         if (ce == cudaSuccess) ce = cudaEventSynchronize(e[1]);
                         float ms = 0.f;
@@ -234,7 +238,7 @@ int batch_run(int32_t n, cyl_plan *const *plans, const void *const *sinos, cyl_d
             cudaError_t ce = cudaSuccess;
             for (int r = 0; r < rounds && ce == cudaSuccess; ++r)
                 ce = launch_batch_round(d_scans, d_items, d_n, n, r, max_vox, Pf, Pb, kRoundAll, d_sched,
-                                        xt, sino_dtype, x16t, bs);
+                                        xt, sino_dtype, x16t, bs, lists);
             cudaError_t ee = cudaStreamEndCapture(bs, &graph);
             if (ce != cudaSuccess) {
                 if (graph) cudaGraphDestroy(graph);
@@ -250,7 +254,7 @@ int batch_run(int32_t n, cyl_plan *const *plans, const void *const *sinos, cyl_d
         } else {
             for (int r = 0; r < rounds; ++r)
                 BT_CUDA(launch_batch_round(d_scans, d_items, d_n, n, r, max_vox, Pf, Pb, kRoundAll, d_sched,
-                                           xt, sino_dtype, x16t, bs));
+                                           xt, sino_dtype, x16t, bs, lists));
         }
         BT_CUDA(cudaFreeAsync(d_blob, bs));
     }

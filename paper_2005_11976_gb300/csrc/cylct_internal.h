@@ -71,6 +71,7 @@ struct UpdateArgs {
 // One scan of a batched solve (static for the whole solve).
 struct BatchScan {
     ScanDev sd;
+    RayList rl;             // the scan's list of rays that meet its grid (act = null: dense)
     const void *sino;       // [N_p][H][W] of the batch's sinogram dtype
     const void *x_proj;     // volume the projector reads (batch's projector dtype)
     UpdateArgs upd;         // fused update (16-bit dtype of the batch)
@@ -122,7 +123,8 @@ cudaError_t launch_count_rays(const ScanDev &sd, int p0, int np, unsigned long l
 constexpr int kRoundFp = 1, kRoundBp = 2, kRoundUpdate = 4, kRoundAll = 7;
 cudaError_t launch_batch_round(const BatchScan *scans, const BatchItem *items, const int *n_items,
                                int max_items, int round, int64_t max_vox, int Pf, int Pb, int parts,
-                               int *sched, cyl_dtype xt, cyl_dtype yt, cyl_dtype x16t, cudaStream_t st);
+                               int *sched, cyl_dtype xt, cyl_dtype yt, cyl_dtype x16t, cudaStream_t st,
+                               bool lists = false);
 cudaError_t launch_log(const void *in, cyl_dtype it, double i0, void *out, cyl_dtype ot,
                        int64_t n, cudaStream_t st);
 cudaError_t launch_convert(const void *in, cyl_dtype it, void *out, cyl_dtype ot,

@@ -413,7 +413,19 @@ k_count(ScanDev sd, int p0, int64_t n_rays, unsigned long long *counts)
 // s_pre[k] = first warp task of item k, s_pre[n] = total.  Thread 0 fills it.  An item
 // of `rays` rays has ceil(rays P / 32) ray-major warp tasks (forward) or
 // ceil(rays / 32) P piece-major ones (backward).
-template <bool PIECE_MAJOR>
+// rays of item `it` that are tasks, and the first of them in the scan's list
+template <bool LIST>
+__device__ __forceinline__ int64_t item_rays(const BatchScan &sc, const BatchItem &it, int64_t &a0)
+{
+    a0 = 0;
+    if (LIST && sc.rl.act) {
+        a0 = sc.rl.act_off[it.p0];
+        return sc.rl.act_off[it.p0 + it.np] - a0;
+    }
+    return (int64_t)it.np * sc.sd.g.det_w * sc.sd.g.det_h;
+}
+
+template <bool PIECE_MAJOR, bool LIST>
 __device__ __forceinline__ int round_prefix(const BatchScan *__restrict__ scans,
                                             const BatchItem *__restrict__ its, int n, int lgP,
                                             int *s_pre)
@@ -423,7 +435,8 @@ __device__ __forceinline__ int round_prefix(const BatchScan *__restrict__ scans,
         for (int k = 0; k < n; ++k) {
             s_pre[k] = acc;
             const BatchScan &sc = scans[its[k].scan];
-            const int64_t rays = (int64_t)its[k].np * sc.sd.g.det_w * sc.sd.g.det_h;
+            int64_t a0;
+            const int64_t rays = item_rays<LIST>(sc, its[k], a0);
             acc += PIECE_MAJOR ? (int)(((rays + 31) >> 5) << lgP) : (int)(((rays << lgP) + 31) >> 5);
         }
         s_pre[n] = acc;
@@ -443,7 +456,7 @@ __device__ __forceinline__ int item_of(const int *s_pre, int n, int wt)
     return lo;
 }
 
-template <class T>
+template <class T, bool LIST>
 __global__ void __launch_bounds__(256)
 k_fp_batch(const BatchScan *__restrict__ scans, const BatchItem *__restrict__ items,
            const int *__restrict__ n_items, int max_items, int round, int lgP, int *sched)
@@ -451,7 +464,7 @@ k_fp_batch(const BatchScan *__restrict__ scans, const BatchItem *__restrict__ it
     extern __shared__ int s_pre[];
     const int n = n_items[round];
     const BatchItem *its = items + (int64_t)round * max_items;
-    const int total = round_prefix<false>(scans, its, n, lgP, s_pre);
+    const int total = round_prefix<false, LIST>(scans, its, n, lgP, s_pre);
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
     for (int k = 0; k < n; ++k) {   // spare accumulators of every item's scan
         const BatchScan &sc = scans[its[k].scan];
@@ -464,24 +477,28 @@ k_fp_batch(const BatchScan *__restrict__ scans, const BatchItem *__restrict__ it
         const int k = item_of(s_pre, n, wt);
         const BatchItem it = its[k];
         const BatchScan &sc = scans[it.scan];
-        const int64_t npix = (int64_t)sc.sd.g.det_w * sc.sd.g.det_h, n_rays = it.np * npix;
+        const int64_t npix = (int64_t)sc.sd.g.det_w * sc.sd.g.det_h;
         const int64_t base = it.p0 * npix;
-        const int64_t t = (int64_t)(wt - s_pre[k]) * 32 + lane, r = t >> lgP;
+        int64_t a0;
+        const int64_t n_task = item_rays<LIST>(sc, it, a0);
+        const int64_t t = (int64_t)(wt - s_pre[k]) * 32 + lane, i = t >> lgP;
         const int piece = (int)(t & (P - 1));
         float acc = 0.f;
-        if (r < n_rays) {
+        int64_t r = -1;
+        if (i < n_task) {
+            r = (LIST && sc.rl.act) ? (int64_t)__ldg(sc.rl.act + a0 + i) - base : i;
             const RayRec rr = ray_at(sc.sd, base + r);
             float ua, ub;
             if (piece_bounds(rr, sc.sd.split + (base + r) * kSplit, piece, P, ua, ub))
                 acc = fp_walk<T>(sc.sd.g, sc.sd.trig, rr, ua, ub, static_cast<const T *>(sc.x_proj));
         }
         acc = ray_sum(acc, P);
-        if (piece == 0 && r < n_rays) sc.q[it.buf][r] = acc;
+        if (piece == 0 && r >= 0) sc.q[it.buf][r] = acc;
     }
     retire(sched);
 }
 
-template <class S>
+template <class S, bool LIST>
 __global__ void __launch_bounds__(256)
 k_bp_batch(const BatchScan *__restrict__ scans, const BatchItem *__restrict__ items,
            const int *__restrict__ n_items, int max_items, int round, int lgP, int *sched)
@@ -489,7 +506,7 @@ k_bp_batch(const BatchScan *__restrict__ scans, const BatchItem *__restrict__ it
     extern __shared__ int s_pre[];
     const int n = n_items[round];
     const BatchItem *its = items + (int64_t)round * max_items;
-    const int total = round_prefix<true>(scans, its, n, lgP, s_pre);
+    const int total = round_prefix<true, LIST>(scans, its, n, lgP, s_pre);
     const int P = 1 << lgP, lane = threadIdx.x & 31;
     for (;;) {
         const int wt = fetch_task(sched + 2);
@@ -497,12 +514,15 @@ k_bp_batch(const BatchScan *__restrict__ scans, const BatchItem *__restrict__ it
         const int k = item_of(s_pre, n, wt);
         const BatchItem it = its[k];
         const BatchScan &sc = scans[it.scan];
-        const int64_t npix = (int64_t)sc.sd.g.det_w * sc.sd.g.det_h, n_rays = it.np * npix;
+        const int64_t npix = (int64_t)sc.sd.g.det_w * sc.sd.g.det_h;
         const int64_t base = it.p0 * npix;
+        int64_t a0;
+        const int64_t n_task = item_rays<LIST>(sc, it, a0);
         const int wl = wt - s_pre[k];
-        const int64_t r = (int64_t)(wl >> lgP) * 32 + lane;
+        const int64_t i = (int64_t)(wl >> lgP) * 32 + lane;
         const int piece = wl & (P - 1);
-        if (r >= n_rays) continue;
+        if (i >= n_task) continue;
+        const int64_t r = (LIST && sc.rl.act) ? (int64_t)__ldg(sc.rl.act + a0 + i) - base : i;
         const RayRec rr = ray_at(sc.sd, base + r);
         float ua, ub;
         if (!piece_bounds(rr, sc.sd.split + (base + r) * kSplit, piece, P, ua, ub)) continue;
@@ -685,7 +705,8 @@ cudaError_t launch_count_rays(const ScanDev &sd, int p0, int np, unsigned long l
 
 cudaError_t launch_batch_round(const BatchScan *scans, const BatchItem *items, const int *n_items,
                                int max_items, int round, int64_t max_vox, int Pf, int Pb, int parts,
-                               int *sched, cyl_dtype xt, cyl_dtype yt, cyl_dtype x16t, cudaStream_t st)
+                               int *sched, cyl_dtype xt, cyl_dtype yt, cyl_dtype x16t, cudaStream_t st,
+                               bool lists)
 {
     const int lgPf = log2_pieces(Pf, kPiecesFp), lgPb = log2_pieces(Pb, kPiecesBp);
     if (lgPf < 0 || lgPb < 0 || max_items < 1) return cudaErrorInvalidValue;
@@ -694,16 +715,24 @@ cudaError_t launch_batch_round(const BatchScan *scans, const BatchItem *items, c
     if (parts & kRoundFp)
         e = dispatch_t(xt, [&](auto *tx) {
             using T = std::remove_pointer_t<decltype(tx)>;
-            const unsigned blocks = persistent_blocks((const void *)k_fp_batch<T>, smem);
-            k_fp_batch<T><<<blocks, 256, smem, st>>>(scans, items, n_items, max_items, round, lgPf, sched);
+            auto go = [&](auto kern) {
+                const unsigned blocks = persistent_blocks((const void *)kern, smem);
+                kern<<<blocks, 256, smem, st>>>(scans, items, n_items, max_items, round, lgPf, sched);
+            };
+            if (lists) go(k_fp_batch<T, true>);
+            else go(k_fp_batch<T, false>);
             return cudaGetLastError();
         });
     if (e != cudaSuccess) return e;
     if (parts & kRoundBp)
         e = dispatch_t(yt, [&](auto *ty) {
             using S = std::remove_pointer_t<decltype(ty)>;
-            const unsigned blocks = persistent_blocks((const void *)k_bp_batch<S>, smem);
-            k_bp_batch<S><<<blocks, 256, smem, st>>>(scans, items, n_items, max_items, round, lgPb, sched);
+            auto go = [&](auto kern) {
+                const unsigned blocks = persistent_blocks((const void *)kern, smem);
+                kern<<<blocks, 256, smem, st>>>(scans, items, n_items, max_items, round, lgPb, sched);
+            };
+            if (lists) go(k_bp_batch<S, true>);
+            else go(k_bp_batch<S, false>);
             return cudaGetLastError();
         });
     if (e != cudaSuccess || !(parts & kRoundUpdate)) return e;

@@ -276,6 +276,7 @@ int cyl_server::run_round()
     std::vector<BatchItem> items;
     std::vector<std::shared_ptr<Scan>> members;
     int Pf = 0, Pb = 0, have_p = 0;
+    bool lists = false;   // some member takes its tasks from its list of rays
     int64_t max_vox = 0;
     for (auto &s : active) {
         if (s->state != 1 || s->rounds_done >= s->rounds_total) continue;
@@ -286,6 +287,8 @@ int cyl_server::run_round()
         const int p0 = (r % s->n_sub) * subset;
         BatchScan sc{};
         sc.sd = pl->scan_dev();
+        sc.rl = pl->ray_list();
+        lists = lists || pl->use_list;
         sc.sino = s->d_sino;
         sc.x_proj = cfg.storage == CYL_F32 ? s->d_x : s->d_x32;   // the FP32 iterate
         sc.q[0] = pl->d_q;
@@ -329,7 +332,7 @@ int cyl_server::run_round()
     if (cudaEventRecord(slot_ev[slot], st) != cudaSuccess) return set_error(CYL_EDEVICE, "event");
     cudaError_t e = launch_batch_round(reinterpret_cast<BatchScan *>(d), reinterpret_cast<BatchItem *>(d + b_scans),
                                        reinterpret_cast<int *>(d + b_scans + b_items), n, 0, max_vox, Pf, Pb,
-                                       kRoundAll, d_sched, CYL_F32, cfg.storage, CYL_F32, st);
+                                       kRoundAll, d_sched, CYL_F32, cfg.storage, CYL_F32, st, lists);
     if (e != cudaSuccess) return cuda_error(e, "round launch");
     ++stats.rounds;
     for (auto &s : members) {

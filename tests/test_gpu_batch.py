@@ -115,3 +115,34 @@ def test_batch_autotuner_keeps_results(lib, orc):
         for p in plans:
             p.close()
 
+
+
+def test_batch_with_listed_and_dense_scans(lib, orc):
+    """Scans whose rays mostly miss their grid take their tasks from their ray lists
+    inside the batched rounds, next to a dense scan; every result equals its own solve
+    and the oracle."""
+    small = synth.Scan(6, 16, 5, 3.0, 6.0, 100.0, 400.0, 41, 37, 1.6, 1.6, synth.full_circle(5) + 0.2)
+    ss = []
+    for i, pose in enumerate([(0.3, 0.1, 0.5, 1.5, -2.0, 0.4), (1.2, 0.05, -0.7, -1.0, 1.0, -0.3)]):
+        s = dataclasses.replace(small, angles=synth.full_circle(5 + i) + 0.2)
+        s.alpha, s.beta, s.gamma, s.tx, s.ty, s.tz = pose
+        ss.append(s)
+    ss.append(scans()[0])                                   # a dense scan of another part
+    rng = np.random.default_rng(17)
+    data = [(rng.uniform(0.0, 1.0, size=s.sino_shape), rng.uniform(0.0, 0.05, size=s.vol_shape)) for s in ss]
+    plans = [cylct.Plan(s) for s in ss]
+    try:
+        import torch
+        outs = [torch.empty(s.vol_shape, device="cuda") for s in ss]
+        prm = cylct.sart_params(n_iter=2, lam=0.5)
+        cylct.cyl_sart_solve_batch(plans, [gu.to_dev(d[0]) for d in data], cylct.CYL_F32,
+                                   [gu.to_dev(d[1]) for d in data], None, prm, outs, cylct.CYL_F32)
+        for i, s in enumerate(ss):
+            got = gu.to_np(outs[i])
+            single = gu.sart(plans[i], data[i][0], x0=data[i][1], n_iter=2, lam=0.5)
+            assert gu.rel_l2(got, single) <= 1e-6, i
+            ref = orc.sart(orc.Setup(**s.fields()), data[i][0], x0=data[i][1], n_iter=2, lam=0.5)
+            assert gu.rel_l2(got, ref) <= 1e-5, i
+    finally:
+        for p in plans:
+            p.close()
