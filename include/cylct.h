@@ -335,7 +335,9 @@ int cyl_plan_sizes(const cyl_plan *plan, int64_t *n_vox, int64_t *n_pix, int32_t
  *
  * Axis tracking.  In every projection the segment is the set of pixels with p > threshold
  * inside a detector window, dilated with the (2k+1) x (2k+1) square (clipped to the
- * window).  Its four corner pixels are the extremes along the detector diagonals:
+ * window).  The test is exact: the stored value (FP32, FP16 or BF16) against the double
+ * threshold, as if both were FP64 (the kernel compares in FP32 against the largest float
+ * at or below the threshold, which decides every float alike).  Its four corner pixels are the extremes along the detector diagonals:
  * top-left maximises -iu + iv, top-right iu + iv, bottom-left -iu - iv, bottom-right
  * iu - iv (ties go to the larger iv for the top corners and the smaller iv for the
  * bottom ones).  The centre of the two top corners and the centre of the two bottom
