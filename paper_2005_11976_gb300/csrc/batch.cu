@@ -105,6 +105,15 @@ int batch_run(int32_t n, cyl_plan *const *plans, const void *const *sinos, cyl_d
         if (!on_device(sinos[i], dev) || !on_device(x_outs[i], dev) ||
             !on_device(x0s ? x0s[i] : nullptr, dev) || !on_device(ws ? ws[i] : nullptr, dev))
             return set_error(CYL_EINVAL, "batched solves take device arrays on the plans' device");
+    {   // a round counts its warp tasks in 32 bits (bound: 16 pieces per ray)
+        int64_t tasks = 0;
+        for (int i = 0; i < n; ++i) {
+            const int64_t sub = std::min<int64_t>(prm->subset_size, plans[i]->geom.n_proj);
+            tasks += ((sub * plans[i]->n_pix + 31) / 32) * kSplit + kSplit;
+        }
+        if (tasks >= ((int64_t)1 << 31) - 1)
+            return set_error(CYL_EINVAL, "batch too large: one round would exceed 2^31 warp tasks");
+    }
 
     // lock the plans in address order
     std::vector<cyl_plan *> order(plans, plans + n);

@@ -500,6 +500,12 @@ extern "C" int cyl_server_add_part(cyl_server *srv, const cyl_grid *grid, const 
     const cyl_pose p0{0, 0, 0, 0, 0, 0};
     int rc = validate_scan(grid, &g1, &p0);
     if (rc) return rc;
+    {   // a round of max_active scans counts its warp tasks in 32 bits (16 pieces per ray)
+        const int64_t sub = srv->cfg.subset_size;
+        const int64_t per = ((sub * geom->det_w * geom->det_h + 31) / 32) * kSplit + kSplit;
+        if (per * srv->cfg.max_active >= ((int64_t)1 << 31) - 1)
+            return set_error(CYL_EINVAL, "part too large for rounds of max_active scans (2^31 warp tasks)");
+    }
     Part pt;
     pt.grid = *grid;
     pt.geom = g1;
