@@ -634,25 +634,43 @@ cudaError_t launch_active(const ScanDev &sd, int n_proj, int64_t *chunk, uint32_
     return cudaGetLastError();
 }
 
+// Views per launch: a launch counts its warp tasks in 32 bits (at most H W / 2 per view
+// with 16 pieces per ray), so very long view ranges go out as several launches.
+static int views_per_launch(const ScanDev &sd)
+{
+    const int64_t per_view = (int64_t)sd.g.det_w * sd.g.det_h / 2 + 1;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)1 << 30) / per_view, 1 << 30));
+}
+
 cudaError_t launch_fp_rays(const ScanDev &sd, int P, int p0, int np, const void *x, cyl_dtype xt,
                            float *q, float2 *zero_buf, int64_t zero_len, cudaStream_t st, const RayList &rl)
 {
     if (np <= 0) return cudaSuccess;
     const int lgP = log2_pieces(P, kPiecesFp);
     if (lgP < 0) return cudaErrorInvalidValue;
-    const int64_t n_rays = (int64_t)np * sd.g.det_w * sd.g.det_h;
+    const int64_t npix = (int64_t)sd.g.det_w * sd.g.det_h;
     const size_t smem = trig_smem(sd.g.n_t);
-    return dispatch_t(xt, [&](auto *tx) {
-        using T = std::remove_pointer_t<decltype(tx)>;
-        if (rl.act) {
-            const unsigned blocks = persistent_blocks((const void *)k_fp<T, true>, smem);
-            k_fp<T, true><<<blocks, 256, smem, st>>>(sd, lgP, p0, n_rays, (const T *)x, q, zero_buf, zero_len, rl);
-        } else {
-            const unsigned blocks = persistent_blocks((const void *)k_fp<T, false>, smem);
-            k_fp<T, false><<<blocks, 256, smem, st>>>(sd, lgP, p0, n_rays, (const T *)x, q, zero_buf, zero_len, rl);
-        }
-        return cudaGetLastError();
-    });
+    const int vmax = views_per_launch(sd);
+    for (int c0 = 0; c0 < np; c0 += vmax) {
+        const int cn = std::min(vmax, np - c0);
+        const int64_t n_rays = (int64_t)cn * npix;
+        float *qc = q + (int64_t)c0 * npix;
+        float2 *zb = c0 == 0 ? zero_buf : nullptr;
+        const int64_t zl = c0 == 0 ? zero_len : 0;
+        const cudaError_t e = dispatch_t(xt, [&](auto *tx) {
+            using T = std::remove_pointer_t<decltype(tx)>;
+            if (rl.act) {
+                const unsigned blocks = persistent_blocks((const void *)k_fp<T, true>, smem);
+                k_fp<T, true><<<blocks, 256, smem, st>>>(sd, lgP, p0 + c0, n_rays, (const T *)x, qc, zb, zl, rl);
+            } else {
+                const unsigned blocks = persistent_blocks((const void *)k_fp<T, false>, smem);
+                k_fp<T, false><<<blocks, 256, smem, st>>>(sd, lgP, p0 + c0, n_rays, (const T *)x, qc, zb, zl, rl);
+            }
+            return cudaGetLastError();
+        });
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_bp_rays(const ScanDev &sd, int P, int p0, int np, const void *y, cyl_dtype yt,
@@ -661,23 +679,32 @@ cudaError_t launch_bp_rays(const ScanDev &sd, int P, int p0, int np, const void 
     if (np <= 0) return cudaSuccess;
     const int lgP = log2_pieces(P, kPiecesBp);
     if (lgP < 0) return cudaErrorInvalidValue;
-    const int64_t n_rays = (int64_t)np * sd.g.det_w * sd.g.det_h;
+    const int64_t npix = (int64_t)sd.g.det_w * sd.g.det_h;
     const size_t smem = trig_smem(sd.g.n_t);
-    return dispatch_t(yt, [&](auto *ty) {
-        using S = std::remove_pointer_t<decltype(ty)>;
-        auto go = [&](auto kern) {
-            const unsigned blocks = persistent_blocks((const void *)kern, smem);
-            kern<<<blocks, 256, smem, st>>>(sd, lgP, p0, n_rays, (const S *)y, q, nd, num, den, rl);
-        };
-        if (q) {
-            if (rl.act) go(k_bp<S, true, true>);
-            else go(k_bp<S, true, false>);
-        } else {
-            if (rl.act) go(k_bp<S, false, true>);
-            else go(k_bp<S, false, false>);
-        }
-        return cudaGetLastError();
-    });
+    const int vmax = views_per_launch(sd);
+    for (int c0 = 0; c0 < np; c0 += vmax) {
+        const int cn = std::min(vmax, np - c0);
+        const int64_t n_rays = (int64_t)cn * npix;
+        const float *qc = q ? q + (int64_t)c0 * npix : nullptr;
+        const cudaError_t e = dispatch_t(yt, [&](auto *ty) {
+            using S = std::remove_pointer_t<decltype(ty)>;
+            const S *yc = static_cast<const S *>(y) + (int64_t)c0 * npix;
+            auto go = [&](auto kern) {
+                const unsigned blocks = persistent_blocks((const void *)kern, smem);
+                kern<<<blocks, 256, smem, st>>>(sd, lgP, p0 + c0, n_rays, yc, qc, nd, num, den, rl);
+            };
+            if (qc) {
+                if (rl.act) go(k_bp<S, true, true>);
+                else go(k_bp<S, true, false>);
+            } else {
+                if (rl.act) go(k_bp<S, false, true>);
+                else go(k_bp<S, false, false>);
+            }
+            return cudaGetLastError();
+        });
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_update_nd(int64_t n_vox, const float2 *nd, const UpdateArgs &u, cudaStream_t st)
@@ -697,10 +724,17 @@ cudaError_t launch_update_nd(int64_t n_vox, const float2 *nd, const UpdateArgs &
 cudaError_t launch_count_rays(const ScanDev &sd, int p0, int np, unsigned long long *counts, cudaStream_t st)
 {
     if (np <= 0) return cudaSuccess;
-    const int64_t n_rays = (int64_t)np * sd.g.det_w * sd.g.det_h;
+    const int64_t npix = (int64_t)sd.g.det_w * sd.g.det_h;
     const size_t smem = trig_smem(sd.g.n_t);
-    k_count<<<persistent_blocks((const void *)k_count, smem), 256, smem, st>>>(sd, p0, n_rays, counts);
-    return cudaGetLastError();
+    const int vmax = views_per_launch(sd);
+    for (int c0 = 0; c0 < np; c0 += vmax) {
+        const int cn = std::min(vmax, np - c0);
+        k_count<<<persistent_blocks((const void *)k_count, smem), 256, smem, st>>>(sd, p0 + c0, (int64_t)cn * npix,
+                                                                                   counts + c0);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_batch_round(const BatchScan *scans, const BatchItem *items, const int *n_items,
