@@ -592,6 +592,7 @@ def run_table1(args):
             xg = xg.cpu().numpy().astype(np.float64)
         parity = float(np.linalg.norm(xg - x1_or) / np.linalg.norm(x1_or))
     n_pix = scan.det_w * scan.det_h
+    plan_bytes = plan.sizes()[3]
     line = {
         "metric": "SART sweeps/s on the paper's Table 1 reconstruction workload", "value": sweeps / tp,
         "unit": "SART iters/s", "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup),
@@ -607,7 +608,7 @@ def run_table1(args):
         "weighted_over_plain": tw / tp,
         "rays_per_sweep": n_pix * scan.n_proj, "rays_hitting_the_grid": rays_hit, "segments_per_sweep": segs,
         "grays_per_s": 2 * sweeps * n_pix * scan.n_proj / tp / 1e9,
-        "rel_err_vs_oracle_one_subset": parity, "clocks": clk,
+        "rel_err_vs_oracle_one_subset": parity, "plan_device_bytes": plan_bytes, "clocks": clk,
         # per step: projector, back-projector and update per view and sweep in both solves,
         # and the weight maximum and scale of the weighted one
         "gpu_launches": args.steps * (2 * sweeps * scan.n_proj * 3 + 2),

@@ -171,7 +171,7 @@ extern "C" int cyl_row_sums(cyl_plan *plan, int32_t p0, int32_t np, float *L_out
     if (np == 0) return CYL_OK;
     if (!L_out) return set_error(CYL_EINVAL, "L_out is null");
     DeviceGuard dg(plan->device);
-    cudaError_t e = launch_row_sums(plan->scan_dev(), p0, np, L_out, (cudaStream_t)stream);
+    cudaError_t e = launch_row_sums(plan->scan_dev(), p0, np, L_out, (cudaStream_t)stream, plan->ray_list());
     return e == cudaSuccess ? CYL_OK : cuda_error(e, "row sums");
 }
 
@@ -254,7 +254,7 @@ extern "C" int cyl_count_segments(cyl_plan *plan, int32_t p0, int32_t np, int64_
     CYL_CUDA(ps.begin());
     CYL_CUDA(cudaMemsetAsync(counts_out, 0, sizeof(int64_t) * np, plan->ws));
     CYL_CUDA(launch_count_rays(plan->scan_dev(), p0, np, reinterpret_cast<unsigned long long *>(counts_out),
-                               plan->ws));
+                               plan->ws, plan->ray_list()));
     CYL_CUDA(ps.end());
     return CYL_OK;
 }

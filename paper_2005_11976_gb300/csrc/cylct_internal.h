@@ -44,9 +44,10 @@ struct ScanDev {
     int *sched;             // two self-resetting work counters per kernel kind (kSched)
 };
 
-// Per pose, the rays of positive chord, view by view in ray order (plan ray index), made
-// where many rays miss the grid; act = null: every ray is a task.  Passed to the ray
-// kernels as their last argument.
+// The rays of positive chord of a compact plan's pose, view by view in ray order (plan ray
+// index); their records and cuts sit at their list positions.  act = null: a dense plan
+// (every ray a task, records indexed by ray).  Passed to the ray kernels as their last
+// argument.
 struct RayList {
     const uint32_t *act;
     const int64_t *act_off;   // [n_proj + 1]: start of each view's rays in act
@@ -91,20 +92,24 @@ struct BatchItem {
 // kernels.cu: ray records, row sums, elementwise kernels.
 cudaError_t launch_rays(const GridDev &g, const ProjGeom *geo, int n_proj, float4 *ra,
                         float4 *rb, float4 *rc, cudaStream_t st);
-cudaError_t launch_row_sums(const ScanDev &sd, int p0, int np, float *L, cudaStream_t st);
+cudaError_t launch_row_sums(const ScanDev &sd, int p0, int np, float *L, cudaStream_t st,
+                            const RayList &rl = RayList{nullptr, nullptr});
 
 // Ray-piece kernels (rays.cu).  P = pieces per ray: 1, 2, 4, 8 or 16 (a divisor of
 // kSplit); P <= 0 means the kernel's default (kPiecesFp, kPiecesBp).
 int valid_pieces(int P);
 int default_pieces(int kind /* 0 forward, 1 back */);
 // Cut every ray of all views into kSplit pieces of equal step counts (once per pose).
-cudaError_t launch_split(const ScanDev &sd, int n_proj, uint16_t *split, cudaStream_t st);
-// The list of rays of positive chord (ScanDev::act) of every view, in ray order.
+cudaError_t launch_split(const ScanDev &sd, int64_t n_rays, uint16_t *split, cudaStream_t st);   // n_rays records
+// Compact plans: the rays of positive chord of every view, in ray order, with their
+// records at their list positions.  Count (and scan into act_off), then fill.
 constexpr int kActChunk = 1024;   // rays per block of the list's count and fill passes
-cudaError_t launch_active(const ScanDev &sd, int n_proj, int64_t *chunk, uint32_t *act, int64_t *act_off,
-                          cudaStream_t st);
-// q[v][pix] = (A x)_j for views p0 .. p0+np-1 (overwritten); zero_buf (if not null) is
-// cleared on the way.
+cudaError_t launch_list_count(const GridDev &g, const ProjGeom *geo, int n_proj, int64_t *chunk, int64_t *act_off,
+                              cudaStream_t st);
+cudaError_t launch_list_fill(const GridDev &g, const ProjGeom *geo, int n_proj, const int64_t *chunk, int64_t cap,
+                             uint32_t *act, float4 *ra, float4 *rb, float4 *rc, cudaStream_t st);
+// q[v][pix] = (A x)_j for views p0 .. p0+np-1 (overwritten; in compact plans only the listed
+// rays); zero_buf (if not null) is cleared on the way.
 cudaError_t launch_fp_rays(const ScanDev &sd, int P, int p0, int np, const void *x, cyl_dtype xt,
                            float *q, float2 *zero_buf, int64_t zero_len, cudaStream_t st,
                            const RayList &rl = RayList{nullptr, nullptr});
@@ -115,7 +120,8 @@ cudaError_t launch_bp_rays(const ScanDev &sd, int P, int p0, int np, const void 
                            const RayList &rl = RayList{nullptr, nullptr});
 cudaError_t launch_update_nd(int64_t n_vox, const float2 *nd, const UpdateArgs &u, cudaStream_t st);
 cudaError_t launch_count_rays(const ScanDev &sd, int p0, int np, unsigned long long *counts,
-                              cudaStream_t st);
+                              cudaStream_t st,
+                              const RayList &rl = RayList{nullptr, nullptr});
 // One round of a batched solve: forward projection, back-projection and update of every
 // item of the round (the kernels selected by `parts`).  Pf, Pb: pieces per ray of the
 // two kernels (<= 0: their defaults).  sched: the batch's scheduler state (kSched ints,

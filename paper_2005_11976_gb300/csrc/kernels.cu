@@ -108,10 +108,27 @@ cudaError_t launch_rays(const GridDev &g, const ProjGeom *geo, int n_proj, float
     return cudaGetLastError();
 }
 
-cudaError_t launch_row_sums(const ScanDev &sd, int p0, int np, float *L, cudaStream_t st)
+// compact plans: L of the listed rays of views p0 .. p0+np-1 (the rest are 0)
+__global__ void k_row_sums_list(ScanDev sd, RayList rl, int p0, int np, float *L)
+{
+    const int64_t npix = (int64_t)sd.g.det_w * sd.g.det_h, base = (int64_t)p0 * npix;
+    const int64_t a0 = rl.act_off[p0], n = rl.act_off[p0 + np] - a0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 c = __ldg(sd.ray_c + a0 + i);
+        L[(int64_t)rl.act[a0 + i] - base] = c.y > c.x ? c.z : 0.f;
+    }
+}
+
+cudaError_t launch_row_sums(const ScanDev &sd, int p0, int np, float *L, cudaStream_t st, const RayList &rl)
 {
     if (np <= 0) return cudaSuccess;
     const int64_t npix = (int64_t)sd.g.det_w * sd.g.det_h;
+    if (rl.act) {
+        cudaError_t e = cudaMemsetAsync(L, 0, sizeof(float) * (size_t)np * npix, st);
+        if (e != cudaSuccess) return e;
+        k_row_sums_list<<<152 * 8, 256, 0, st>>>(sd, rl, p0, np, L);
+        return cudaGetLastError();
+    }
     k_row_sums<<<dim3((unsigned)((npix + 255) / 256), np), 256, 0, st>>>(sd, p0, L);
     return cudaGetLastError();
 }

@@ -50,9 +50,20 @@ int cyl_plan::init(const cyl_grid &gr, const cyl_geom &ge, const cyl_pose &po, i
     const size_t n_rays = (size_t)geom.n_proj * n_pix;
     if ((rc = alloc(&d_geo, sizeof(ProjGeom) * geom.n_proj))) return rc;
     if ((rc = alloc(&d_trig, sizeof(float2) * trig.size()))) return rc;
-    for (int k = 0; k < 3; ++k)
-        if ((rc = alloc(&d_ray[k], sizeof(float4) * n_rays))) return rc;
-    if ((rc = alloc(&d_split, sizeof(uint16_t) * kSplit * n_rays))) return rc;
+    {   // compact or dense, fixed for the plan's life: the first pose decides
+        std::vector<ProjGeom> geo;
+        build_views(geom, pose, geo);
+        use_list = n_rays < ((size_t)1 << 32) && hit_fraction_bound(grid, geom, geo) < 0.75;
+    }
+    if (use_list) {
+        const size_t cpv = ((size_t)n_pix + kActChunk - 1) / kActChunk;
+        if ((rc = alloc(&d_act_off, sizeof(int64_t) * (geom.n_proj + 1)))) return rc;
+        if ((rc = alloc(&d_act_chunk, sizeof(int64_t) * cpv * geom.n_proj))) return rc;
+    } else {
+        for (int k = 0; k < 3; ++k)
+            if ((rc = alloc(&d_ray[k], sizeof(float4) * n_rays))) return rc;
+        if ((rc = alloc(&d_split, sizeof(uint16_t) * kSplit * n_rays))) return rc;
+    }
     if ((rc = alloc(&d_sched, sizeof(int) * kSched))) return rc;
     for (int k = 0; k < 2; ++k)
         if ((rc = alloc(&d_nd[k], sizeof(float2) * n_vox))) return rc;
@@ -78,24 +89,29 @@ int cyl_plan::upload_pose(const cyl_pose &po, cudaStream_t st)
     std::memcpy(h_geo, geo.data(), sizeof(ProjGeom) * geo.size());
     PL_CUDA(cudaMemcpyAsync(d_geo, h_geo, sizeof(ProjGeom) * geo.size(), cudaMemcpyHostToDevice, st));
     PL_CUDA(cudaEventRecord(ev_geo, st));
-    PL_CUDA(launch_rays(g, d_geo, geom.n_proj, d_ray[0], d_ray[1], d_ray[2], st));
-    // list the rays that meet the grid when a quarter or more surely miss it: the list
-    // spares the projector and back-projector the empty rays but costs every task a load.
-    // Its buffers are made on the first pose that needs them (the list holds 32-bit ray
-    // indices, so plans of 2^32 rays or more never list).
-    const size_t n_rays = (size_t)geom.n_proj * n_pix;
-    const bool list = n_rays < ((size_t)1 << 32) && hit_fraction_bound(grid, geom, geo) < 0.75;
-    if (list && !d_act) {
-        const size_t cpv = ((size_t)n_pix + kActChunk - 1) / kActChunk;
-        int rc;
-        if ((rc = alloc(&d_act, sizeof(uint32_t) * n_rays))) return rc;
-        if ((rc = alloc(&d_act_off, sizeof(int64_t) * (geom.n_proj + 1)))) return rc;
-        if ((rc = alloc(&d_act_chunk, sizeof(int64_t) * cpv * geom.n_proj))) return rc;
+    if (!use_list) {
+        PL_CUDA(launch_rays(g, d_geo, geom.n_proj, d_ray[0], d_ray[1], d_ray[2], st));
+        PL_CUDA(launch_split(scan_dev(), (int64_t)geom.n_proj * n_pix, d_split, st));
+    } else {
+        // count this pose's rays of positive chord, size the compact buffers, then list
+        // them with their records and cut them
+        PL_CUDA(launch_list_count(g, d_geo, geom.n_proj, d_act_chunk, d_act_off, st));
+        int64_t n = 0;
+        PL_CUDA(cudaMemcpyAsync(&n, d_act_off + geom.n_proj, sizeof n, cudaMemcpyDeviceToHost, st));
+        PL_CUDA(cudaStreamSynchronize(st));
+        const size_t want = (size_t)std::max<int64_t>(n, 1);
+        if (want * sizeof(uint32_t) > act_cap) {
+            const size_t room = want + want / 8 + 64;   // re-posed parts vary a little
+            int rc;
+            for (int k = 0; k < 3; ++k)
+                if ((rc = ensure((void **)&d_ray[k], ray_cap[k], sizeof(float4) * room))) return rc;
+            if ((rc = ensure((void **)&d_split, split_cap, sizeof(uint16_t) * kSplit * room))) return rc;
+            if ((rc = ensure((void **)&d_act, act_cap, sizeof(uint32_t) * room))) return rc;
+        }
+        n_listed = n;
+        PL_CUDA(launch_list_fill(g, d_geo, geom.n_proj, d_act_chunk, n, d_act, d_ray[0], d_ray[1], d_ray[2], st));
+        PL_CUDA(launch_split(scan_dev(), n, d_split, st));
     }
-    if (list != use_list) drop_graphs();   // captured launches name the other kernels
-    use_list = list;
-    if (use_list) PL_CUDA(launch_active(scan_dev(), geom.n_proj, d_act_chunk, d_act, d_act_off, st));
-    PL_CUDA(launch_split(scan_dev(), geom.n_proj, d_split, st));
     pose = po;
     return CYL_OK;
 }

@@ -67,10 +67,15 @@ struct cyl_plan {
     float4 *d_ray[3] = {nullptr, nullptr, nullptr};
     uint16_t *d_split = nullptr;   // [view][pixel][kSplit] cuts of each ray (per pose)
     int *d_sched = nullptr;        // work counters of the persistent kernels (kSched)
-    uint32_t *d_act = nullptr;     // rays of positive chord per view (ScanDev::act), or null
-    bool use_list = false;         // this pose's tasks come from d_act (many rays miss)
-    int64_t *d_act_off = nullptr;  // [n_proj + 1]
+    // Compact plans (chosen at creation, where the grid surely leaves a quarter or more of
+    // the detector dark) list each pose's rays of positive chord and keep records and cuts
+    // for those rays only, at their list positions.
+    bool use_list = false;
+    uint32_t *d_act = nullptr;     // the list (plan ray indices), or null
+    int64_t *d_act_off = nullptr;  // [n_proj + 1]: each view's start in the list
     int64_t *d_act_chunk = nullptr; // chunk counts / offsets of the list's construction
+    int64_t n_listed = 0;          // rays listed for the current pose
+    size_t ray_cap[3] = {0, 0, 0}, split_cap = 0, act_cap = 0;
     float *d_wscale = nullptr;
     float *d_q = nullptr;          // forward projections of one subset (FP32)
     size_t q_cap = 0;

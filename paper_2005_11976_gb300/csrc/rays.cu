@@ -158,24 +158,28 @@ __global__ void __launch_bounds__(256) k_split(ScanDev sd, int64_t n_rays, uint1
     out[kSplit - 1] = (uint16_t)fminf(n_est, 65535.f);
 }
 
-// ------------------------------------------------------------------ active rays
+// ------------------------------------------------------------------ listed rays
 
-// Rays of positive chord (u_out > u_in), listed per pose in ray order: each block counts
-// one chunk of kActChunk rays of one view, one block scans the chunk counts, and each
-// block then writes its chunk's rays at the chunk's offset (ranks from warp ballots).
-__device__ __forceinline__ bool ray_active(const ScanDev &sd, int64_t rec)
+// A compact plan keeps, per pose, only the rays of positive chord (u_out > u_in): listed
+// view by view in ray order, with their records and cuts stored at their list positions.
+// Each block sets up one chunk of kActChunk rays of one view (FP64, setup_ray) and counts
+// the ones that meet the grid; one block scans the chunk counts; the fill pass sets the
+// chunk up again and writes each listed ray's index and record at its position (ranks
+// from warp ballots).
+__global__ void __launch_bounds__(256) k_act_count(GridDev g, const ProjGeom *__restrict__ geo, int cpv,
+                                                   int64_t *chunk)
 {
-    const float4 c = __ldg(sd.ray_c + rec);
-    return c.y > c.x;
-}
-
-__global__ void __launch_bounds__(256) k_act_count(ScanDev sd, int64_t npix, int cpv, int64_t *chunk)
-{
+    const int64_t npix = (int64_t)g.det_w * g.det_h;
     const int64_t p = blockIdx.y, j0 = (int64_t)blockIdx.x * kActChunk;
     int n = 0;
     for (int k = threadIdx.x; k < kActChunk; k += blockDim.x) {
         const int64_t j = j0 + k;
-        n += __syncthreads_count(j < npix && ray_active(sd, p * npix + j));
+        bool on = false;
+        if (j < npix) {
+            const RayRec rr = setup_ray(g, geo[p], (int)(j % g.det_w), (int)(j / g.det_w));
+            on = rr.c.y > rr.c.x;
+        }
+        n += __syncthreads_count(on);
     }
     if (threadIdx.x == 0) chunk[p * cpv + blockIdx.x] = n;
 }
@@ -211,16 +215,24 @@ __global__ void __launch_bounds__(1024) k_act_scan(int64_t *chunk, int64_t n, in
     for (int p = threadIdx.x; p < n_proj; p += blockDim.x) act_off[p] = chunk[(int64_t)p * cpv];
 }
 
-__global__ void __launch_bounds__(256) k_act_fill(ScanDev sd, int64_t npix, int cpv, const int64_t *chunk,
-                                                  uint32_t *act)
+// cap: entries the list and record buffers hold (the scan's total, read by the host)
+__global__ void __launch_bounds__(256) k_act_fill(GridDev g, const ProjGeom *__restrict__ geo, int cpv,
+                                                  const int64_t *chunk, int64_t cap, uint32_t *act, float4 *ra,
+                                                  float4 *rb, float4 *rc)
 {
     __shared__ int warp_n[8];
+    const int64_t npix = (int64_t)g.det_w * g.det_h;
     const int64_t p = blockIdx.y, j0 = (int64_t)blockIdx.x * kActChunk;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int64_t pos = chunk[p * cpv + blockIdx.x];
     for (int k = 0; k < kActChunk; k += blockDim.x) {
         const int64_t j = j0 + k + threadIdx.x;
-        const bool on = j < npix && ray_active(sd, p * npix + j);
+        RayRec rr{};
+        bool on = false;
+        if (j < npix) {
+            rr = setup_ray(g, geo[p], (int)(j % g.det_w), (int)(j / g.det_w));
+            on = rr.c.y > rr.c.x;
+        }
         const unsigned m = __ballot_sync(0xffffffffu, on);
         if (lane == 0) warp_n[w] = __popc(m);
         __syncthreads();
@@ -229,7 +241,13 @@ __global__ void __launch_bounds__(256) k_act_fill(ScanDev sd, int64_t npix, int 
             before += q < w ? warp_n[q] : 0;
             total += warp_n[q];
         }
-        if (on) act[pos + before + __popc(m & ((1u << lane) - 1u))] = (uint32_t)(p * npix + j);
+        const int64_t e = pos + before + __popc(m & ((1u << lane) - 1u));
+        if (on && e < cap) {
+            act[e] = (uint32_t)(p * npix + j);
+            ra[e] = rr.a;
+            rb[e] = rr.b;
+            rc[e] = rr.c;
+        }
         pos += total;
         __syncthreads();
     }
@@ -277,10 +295,12 @@ k_fp(ScanDev sd, int lgP, int p0, int64_t n_rays, const T *__restrict__ x, float
         float acc = 0.f;
         int64_t r = -1;
         if (i < n_task) {
+            // a listed ray's record and cuts sit at its list position
             r = LIST ? (int64_t)__ldg(rl.act + a0 + i) - base : i;
-            const RayRec rr = ray_at(sd, base + r);
+            const int64_t rec = LIST ? a0 + i : base + r;
+            const RayRec rr = ray_at(sd, rec);
             float ua, ub;
-            if (piece_bounds(rr, sd.split + (base + r) * kSplit, piece, P, ua, ub))
+            if (piece_bounds(rr, sd.split + rec * kSplit, piece, P, ua, ub))
                 acc = fp_walk<T>(sd.g, s_trig, rr, ua, ub, x);
         }
         acc = ray_sum(acc, P);
@@ -312,9 +332,10 @@ k_bp(ScanDev sd, int lgP, int p0, int64_t n_rays, const S *__restrict__ y, const
         const int piece = (int)(wt & (P - 1));
         if (i >= n_task) continue;
         const int64_t r = LIST ? (int64_t)__ldg(rl.act + a0 + i) - base : i;
-        const RayRec rr = ray_at(sd, base + r);
+        const int64_t rec = LIST ? a0 + i : base + r;
+        const RayRec rr = ray_at(sd, rec);
         float ua, ub;
-        if (!piece_bounds(rr, sd.split + (base + r) * kSplit, piece, P, ua, ub)) continue;
+        if (!piece_bounds(rr, sd.split + rec * kSplit, piece, P, ua, ub)) continue;
         float yv;
         if (SART) {
             const float L = rr.c.z;
@@ -375,8 +396,9 @@ __global__ void k_update_nd(int64_t n, const float2 *__restrict__ nd, UpdateArgs
 }
 
 // Segments of positive length per view; a cut inside a segment is not counted twice.
+template <bool LIST>
 __global__ void __launch_bounds__(256)
-k_count(ScanDev sd, int p0, int64_t n_rays, unsigned long long *counts)
+k_count(ScanDev sd, int p0, int64_t n_rays, unsigned long long *counts, RayList rl)
 {
     extern __shared__ float2 s_trig[];
     stage_trig_smem(sd.trig, sd.g.n_t, s_trig);
@@ -384,17 +406,21 @@ k_count(ScanDev sd, int p0, int64_t n_rays, unsigned long long *counts)
     const int64_t npix = (int64_t)sd.g.det_w * sd.g.det_h, base = p0 * npix;
     constexpr int lgP = 4;   // kSplit pieces
     static_assert(kSplit == 1 << lgP, "kSplit is 2^4");
-    const int64_t n_wt = ((n_rays << lgP) + 31) >> 5;
+    int64_t a0, n_task;
+    launch_tasks<LIST>(rl, p0, npix, n_rays, a0, n_task);
+    const int64_t n_wt = ((n_task << lgP) + 31) >> 5;
     int *sched = sd.sched + 4;
     for (;;) {
         const int wt = fetch_task(sched);
         if (wt >= n_wt) break;
-        const int64_t t = (int64_t)wt * 32 + lane, r = t >> lgP;
+        const int64_t t = (int64_t)wt * 32 + lane, i = t >> lgP;
         const int piece = (int)(t & (kSplit - 1));
-        if (r >= n_rays) continue;
-        const RayRec rr = ray_at(sd, base + r);
+        if (i >= n_task) continue;
+        const int64_t r = LIST ? (int64_t)__ldg(rl.act + a0 + i) - base : i;
+        const int64_t rec = LIST ? a0 + i : base + r;
+        const RayRec rr = ray_at(sd, rec);
         float ua, ub;
-        if (!piece_bounds(rr, sd.split + (base + r) * kSplit, piece, kSplit, ua, ub)) continue;
+        if (!piece_bounds(rr, sd.split + rec * kSplit, piece, kSplit, ua, ub)) continue;
         Walker w;
         w.init(sd.g, s_trig, rr, ua, ub);
         unsigned int n = 0;
@@ -486,10 +512,12 @@ k_fp_batch(const BatchScan *__restrict__ scans, const BatchItem *__restrict__ it
         float acc = 0.f;
         int64_t r = -1;
         if (i < n_task) {
-            r = (LIST && sc.rl.act) ? (int64_t)__ldg(sc.rl.act + a0 + i) - base : i;
-            const RayRec rr = ray_at(sc.sd, base + r);
+            const bool listed = LIST && sc.rl.act;
+            r = listed ? (int64_t)__ldg(sc.rl.act + a0 + i) - base : i;
+            const int64_t rec = listed ? a0 + i : base + r;
+            const RayRec rr = ray_at(sc.sd, rec);
             float ua, ub;
-            if (piece_bounds(rr, sc.sd.split + (base + r) * kSplit, piece, P, ua, ub))
+            if (piece_bounds(rr, sc.sd.split + rec * kSplit, piece, P, ua, ub))
                 acc = fp_walk<T>(sc.sd.g, sc.sd.trig, rr, ua, ub, static_cast<const T *>(sc.x_proj));
         }
         acc = ray_sum(acc, P);
@@ -522,10 +550,12 @@ k_bp_batch(const BatchScan *__restrict__ scans, const BatchItem *__restrict__ it
         const int64_t i = (int64_t)(wl >> lgP) * 32 + lane;
         const int piece = wl & (P - 1);
         if (i >= n_task) continue;
-        const int64_t r = (LIST && sc.rl.act) ? (int64_t)__ldg(sc.rl.act + a0 + i) - base : i;
-        const RayRec rr = ray_at(sc.sd, base + r);
+        const bool listed = LIST && sc.rl.act;
+        const int64_t r = listed ? (int64_t)__ldg(sc.rl.act + a0 + i) - base : i;
+        const int64_t rec = listed ? a0 + i : base + r;
+        const RayRec rr = ray_at(sc.sd, rec);
         float ua, ub;
-        if (!piece_bounds(rr, sc.sd.split + (base + r) * kSplit, piece, P, ua, ub)) continue;
+        if (!piece_bounds(rr, sc.sd.split + rec * kSplit, piece, P, ua, ub)) continue;
         const float L = rr.c.z;
         const S *y = static_cast<const S *>(sc.sino) + base;
         const float yv = L > 0.f ? (as_f32<S>(y[r]) - sc.q[it.buf][r]) / L : 0.f;
@@ -613,24 +643,31 @@ static unsigned persistent_blocks(const void *kernel, size_t smem)
 int valid_pieces(int P) { return log2_pieces(P, kSplit) >= 0; }
 int default_pieces(int kind) { return kind == 0 ? kPiecesFp : kPiecesBp; }
 
-cudaError_t launch_split(const ScanDev &sd, int n_proj, uint16_t *split, cudaStream_t st)
+cudaError_t launch_split(const ScanDev &sd, int64_t n_rays, uint16_t *split, cudaStream_t st)
 {
-    const int64_t n_rays = (int64_t)n_proj * sd.g.det_w * sd.g.det_h;
     if (n_rays <= 0) return cudaSuccess;
     k_split<<<(unsigned)((n_rays + 255) / 256), 256, 0, st>>>(sd, n_rays, split);
     return cudaGetLastError();
 }
 
-cudaError_t launch_active(const ScanDev &sd, int n_proj, int64_t *chunk, uint32_t *act, int64_t *act_off,
-                          cudaStream_t st)
+cudaError_t launch_list_count(const GridDev &g, const ProjGeom *geo, int n_proj, int64_t *chunk, int64_t *act_off,
+                              cudaStream_t st)
 {
-    const int64_t npix = (int64_t)sd.g.det_w * sd.g.det_h;
+    const int64_t npix = (int64_t)g.det_w * g.det_h;
     const int cpv = (int)((npix + kActChunk - 1) / kActChunk);
     if (n_proj <= 0 || npix <= 0) return cudaSuccess;
-    const dim3 grid((unsigned)cpv, (unsigned)n_proj);
-    k_act_count<<<grid, 256, 0, st>>>(sd, npix, cpv, chunk);
+    k_act_count<<<dim3((unsigned)cpv, (unsigned)n_proj), 256, 0, st>>>(g, geo, cpv, chunk);
     k_act_scan<<<1, 1024, 0, st>>>(chunk, (int64_t)n_proj * cpv, n_proj, cpv, act_off);
-    k_act_fill<<<grid, 256, 0, st>>>(sd, npix, cpv, chunk, act);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_list_fill(const GridDev &g, const ProjGeom *geo, int n_proj, const int64_t *chunk, int64_t cap,
+                             uint32_t *act, float4 *ra, float4 *rb, float4 *rc, cudaStream_t st)
+{
+    const int64_t npix = (int64_t)g.det_w * g.det_h;
+    const int cpv = (int)((npix + kActChunk - 1) / kActChunk);
+    if (n_proj <= 0 || npix <= 0) return cudaSuccess;
+    k_act_fill<<<dim3((unsigned)cpv, (unsigned)n_proj), 256, 0, st>>>(g, geo, cpv, chunk, cap, act, ra, rb, rc);
     return cudaGetLastError();
 }
 
@@ -721,7 +758,8 @@ cudaError_t launch_update_nd(int64_t n_vox, const float2 *nd, const UpdateArgs &
     });
 }
 
-cudaError_t launch_count_rays(const ScanDev &sd, int p0, int np, unsigned long long *counts, cudaStream_t st)
+cudaError_t launch_count_rays(const ScanDev &sd, int p0, int np, unsigned long long *counts, cudaStream_t st,
+                              const RayList &rl)
 {
     if (np <= 0) return cudaSuccess;
     const int64_t npix = (int64_t)sd.g.det_w * sd.g.det_h;
@@ -729,8 +767,12 @@ cudaError_t launch_count_rays(const ScanDev &sd, int p0, int np, unsigned long l
     const int vmax = views_per_launch(sd);
     for (int c0 = 0; c0 < np; c0 += vmax) {
         const int cn = std::min(vmax, np - c0);
-        k_count<<<persistent_blocks((const void *)k_count, smem), 256, smem, st>>>(sd, p0 + c0, (int64_t)cn * npix,
-                                                                                   counts + c0);
+        auto go = [&](auto kern) {
+            kern<<<persistent_blocks((const void *)kern, smem), 256, smem, st>>>(sd, p0 + c0, (int64_t)cn * npix,
+                                                                                 counts + c0, rl);
+        };
+        if (rl.act) go(k_count<true>);
+        else go(k_count<false>);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

@@ -180,6 +180,11 @@ def test_small_part_on_a_wide_detector(lib, orc):
         bp = gu.backproject(plan, y)
         p = want + 0.01 * rng.standard_normal(want.shape)
         xs = gu.sart(plan, p, x0=x, n_iter=2, lam=0.5)
+        L_gpu = gu.row_sums(plan)
+        segs = gu.count_segments(plan)
+    np.testing.assert_allclose(L_gpu, L, rtol=1e-6, atol=1e-6)
+    ref = orc.row_nnz(o).reshape(s.n_proj, -1).sum(axis=1)
+    assert np.all(np.abs(segs - ref) <= 4 + 2e-3 * ref), (segs, ref)
     assert np.all(got[L == 0] == 0) and np.all(got_na[L == 0] == 0)
     assert per_projection_rel(got, want) <= TOL_FP32 and per_projection_rel(got_na, want) <= TOL_FP32
     assert gu.rel_l2(bp, orc.backproject(o, y)) <= TOL_FP32
@@ -211,32 +216,37 @@ def test_sart_update_fallbacks(lib, orc):
         assert gu.rel_l2(gu.sart(plan, p, n_iter=2, lam=0.5), want2) <= TOL_FP32
 
 
-def test_dense_and_listed_poses_alternate(lib, orc):
-    """Re-posing moves a plan between dense tasks (the grid fills the detector) and the
-    list of rays that meet the grid (the part moved sideways, most rays miss); captured
-    sweeps follow the switch.  Every pose matches the oracle."""
+def test_dense_and_compact_plans_through_all_poses(lib, orc):
+    """A plan is dense (records for every ray) or compact (each pose lists the rays that
+    meet the grid and keeps records for those only), decided by its first pose.  Both
+    kinds re-posed through poses where the grid fills the detector and where the part sits
+    mostly off it give the oracle's projections and SART iterates (captured sweeps
+    included), and the compact plan holds far less."""
     s = synth.Scan(5, 16, 6, 6.0, 10.0, 60.0, 240.0, 28, 24, 1.6, 1.6, synth.full_circle(3) + 0.2)
     poses = [(0.2, 0.1, 0.3, 0.0, 0.0, 0.0), (0.2, 0.1, 0.3, 14.0, 7.0, 0.0), (0.2, 0.1, 0.3, 0.5, -0.5, 0.0),
              (0.2, 0.1, 0.3, -14.0, 7.0, 1.0)]
     rng = np.random.default_rng(41)
     x = rng.uniform(0.0, 0.05, size=s.vol_shape)
     p = rng.uniform(0.0, 1.0, size=s.sino_shape)
-    s0 = dataclasses.replace(s, alpha=0.2, beta=0.1, gamma=0.3)
-    with cylct.Plan(s0) as plan:
-        bytes_dense = plan.sizes()[3]
-        for i, pose in enumerate(poses):
-            if i:
+
+    def posed(pose):
+        return dataclasses.replace(s, alpha=pose[0], beta=pose[1], gamma=pose[2], tx=pose[3], ty=pose[4], tz=pose[5])
+
+    sizes = []
+    for first in (0, 1):                         # dense first pose, then mostly-off first pose
+        with cylct.Plan(posed(poses[first])) as plan:
+            sizes.append(plan.sizes()[3])
+            for pose in poses[first:] + poses[:first]:
                 plan.cyl_plan_set_pose(pose)
-            sp = dataclasses.replace(s, alpha=pose[0], beta=pose[1], gamma=pose[2], tx=pose[3], ty=pose[4], tz=pose[5])
-            o = osetup(orc, sp)
-            want = orc.project(o, x)
-            got = gu.project(plan, x)
-            assert np.all(got[want == 0] == 0)
-            assert np.abs(got - want).max() <= TOL_FP32 * max(np.abs(want).max(), 1.0)
-            xs = gu.sart(plan, p, x0=x, n_iter=2, lam=0.5)
-            assert gu.rel_l2(xs, orc.sart(o, p, x0=x, n_iter=2, lam=0.5)) <= TOL_FP32
-            if i == 1:
-                assert plan.sizes()[3] > bytes_dense      # the list was made for this pose
+                o = osetup(orc, posed(pose))
+                want = orc.project(o, x)
+                got = gu.project(plan, x)
+                assert np.all(got[want == 0] == 0)
+                assert np.abs(got - want).max() <= TOL_FP32 * max(np.abs(want).max(), 1.0)
+                np.testing.assert_allclose(gu.row_sums(plan), orc.row_sums(o), rtol=1e-6, atol=1e-6)
+                xs = gu.sart(plan, p, x0=x, n_iter=2, lam=0.5)
+                assert gu.rel_l2(xs, orc.sart(o, p, x0=x, n_iter=2, lam=0.5)) <= TOL_FP32
+    assert sizes[1] < sizes[0]
 
 
 def test_empty_projection_range(lib):
