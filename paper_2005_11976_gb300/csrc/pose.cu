@@ -568,8 +568,8 @@ k_phase(const double *__restrict__ m_scan, const double *__restrict__ m_tmpl,
 struct PoseTiming {
     std::mutex mu;
     bool on = false;
-    double ms[3] = {0, 0, 0};
-    int64_t n[3] = {0, 0, 0};
+    double ms[2] = {0, 0};      // 0: corner pass, 1: Levenberg-Marquardt pass
+    int64_t n[2] = {0, 0};
 } g_timing;
 
 struct KernelTimer {
@@ -1104,7 +1104,7 @@ extern "C" int cyl_pose_set_timing(int enable)
 {
     std::lock_guard<std::mutex> l(g_timing.mu);
     g_timing.on = enable != 0;
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < 2; ++k) {
         g_timing.ms[k] = 0.0;
         g_timing.n[k] = 0;
     }
@@ -1113,7 +1113,7 @@ extern "C" int cyl_pose_set_timing(int enable)
 
 extern "C" int cyl_pose_kernel_time(int kind, double *ms_total, int64_t *launches)
 {
-    if (kind < 0 || kind > 2) return set_error(CYL_EINVAL, "kind must be 0, 1 or 2");
+    if (kind < 0 || kind > 1) return set_error(CYL_EINVAL, "kind must be 0 or 1");
     std::lock_guard<std::mutex> l(g_timing.mu);
     if (ms_total) *ms_total = g_timing.ms[kind];
     if (launches) *launches = g_timing.n[kind];
