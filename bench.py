@@ -355,6 +355,16 @@ def main():
         t_view = sum(avg_ms) / 1e3
         compulsory = {"bytes_per_subset": comp, "achieved": comp / t_view / 1e9, "frac": comp / t_view / 1e9 / hbm,
                       "unit": "GB/s", "subset_ms": t_view * 1e3}
+        # the segment-touch figures of the path's specification: forward S b_v + H W (b_s + 4);
+        # back-projection and update together S 4 + 2 V_hit b_v + V_hit b_w (V_hit = V here:
+        # every voxel of the grid is crossed by some ray of a medium view)
+        st_fp = S * 4 + n_pix * 8
+        st_bu = S * 4 + 2 * n_vox * 4 + n_vox * 4
+        t_fp, t_bu = avg_ms[0] / 1e3, (avg_ms[1] + avg_ms[2]) / 1e3
+        spec_model = {"forward": {"bytes": st_fp, "achieved": st_fp / t_fp / 1e9, "frac": st_fp / t_fp / 1e9 / hbm},
+                      "back_and_update": {"bytes": st_bu, "achieved": st_bu / t_bu / 1e9,
+                                          "frac": st_bu / t_bu / 1e9 / hbm},
+                      "unit": "GB/s"}
         roof = {"bound": "hbm", "achieved": ach[dom], "peak": hbm, "unit": "GB/s",
                 "frac": ach[dom] / hbm, "traffic": TRAFFIC.get(kinds[dom].split("(")[-1][:-1]),
                 "kernel": kinds[dom], "peak_source": peak_kind,
@@ -364,7 +374,7 @@ def main():
                 "kernel_gbs": {kinds[k]: ach[k] for k in range(3)},
                 "kernel_frac": {kinds[k]: ach[k] / hbm for k in range(3)},
                 "kernel_share": {kinds[k]: k_ms[k] / sum(k_ms) for k in range(3)},
-                "segments_per_view": S, "compulsory_model": compulsory}
+                "segments_per_view": S, "compulsory_model": compulsory, "spec_segment_touch_model": spec_model}
 
     # --- CPU oracle on a bounded sample, and a live parity check on that sample
     cpu = None
