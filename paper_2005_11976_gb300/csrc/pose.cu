@@ -618,6 +618,49 @@ struct DevBlob {
 
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Device scratch and pinned staging of the synchronous pose calls, one set per host
+// thread, grown on demand (freed at thread exit).
+struct PoseScratch {
+    int dev = -1;
+    void *d = nullptr, *h = nullptr;
+    size_t dcap = 0, hcap = 0;
+    int reserve(int device, size_t dbytes, size_t hbytes)
+    {
+        if (device != dev) release();
+        dev = device;
+        if (dcap < dbytes) {
+            if (d) cudaFree(d);
+            d = nullptr;
+            dcap = 0;
+            if (cudaMalloc(&d, dbytes) != cudaSuccess) {
+                cudaGetLastError();
+                return set_error(CYL_ENOMEM, "pose scratch");
+            }
+            dcap = dbytes;
+        }
+        if (hcap < hbytes) {
+            if (h) cudaFreeHost(h);
+            h = nullptr;
+            hcap = 0;
+            if (cudaMallocHost(&h, hbytes) != cudaSuccess) {
+                cudaGetLastError();
+                return set_error(CYL_ENOMEM, "pose staging");
+            }
+            hcap = hbytes;
+        }
+        return CYL_OK;
+    }
+    void release()
+    {
+        if (d) cudaFree(d);
+        if (h) cudaFreeHost(h);
+        d = h = nullptr;
+        dcap = hcap = 0;
+    }
+    ~PoseScratch() { release(); }
+};
+thread_local PoseScratch t_scratch;
+
 int persistent_warps()
 {
     static int warps = 0;
@@ -830,18 +873,20 @@ int estimate_poses(int n, const cyl_geom *geoms, const void *const *sinos, cyl_d
     const size_t o_ts = align_up(o_cs + sizeof(CornerScan) * n), o_vw = align_up(o_ts + sizeof(TrackScan) * n);
     const size_t o_out = align_up(o_vw + sizeof(ViewLM) * nviews);
     const size_t total = align_up(o_out + sizeof(double) * kOutPose * n);
-    std::vector<char> host(total - o_cs);
-    memcpy(host.data(), cscans.data(), sizeof(CornerScan) * n);
-    memcpy(host.data() + (o_ts - o_cs), tscans.data(), sizeof(TrackScan) * n);
-    memcpy(host.data() + (o_vw - o_cs), views.data(), sizeof(ViewLM) * nviews);
-    DevBlob blob;
-    blob.st = st;
-    PO_CUDA(cudaMallocAsync(&blob.p, total, st));
-    char *b = static_cast<char *>(blob.p);
+    // this thread's cached scratch: the call ends synchronised, so the next call may reuse it
+    int dev = 0;
+    PO_CUDA(cudaGetDevice(&dev));
+    int rc = t_scratch.reserve(dev, total, total - o_cs);
+    if (rc) return rc;
+    char *host = static_cast<char *>(t_scratch.h);   // pinned: tables in, results out
+    memcpy(host, cscans.data(), sizeof(CornerScan) * n);
+    memcpy(host + (o_ts - o_cs), tscans.data(), sizeof(TrackScan) * n);
+    memcpy(host + (o_vw - o_cs), views.data(), sizeof(ViewLM) * nviews);
+    char *b = static_cast<char *>(t_scratch.d);
     auto *keys = reinterpret_cast<unsigned long long *>(b + o_keys);
     auto *cnts = reinterpret_cast<unsigned long long *>(b + o_cnt);
     PO_CUDA(cudaMemsetAsync(b, 0, o_cs, st));
-    PO_CUDA(cudaMemcpyAsync(b + o_cs, host.data(), o_out - o_cs, cudaMemcpyHostToDevice, st));
+    PO_CUDA(cudaMemcpyAsync(b + o_cs, host, o_out - o_cs, cudaMemcpyHostToDevice, st));
     KernelTimer tc(0, st);
     PO_CUDA(launch_corners(reinterpret_cast<const CornerScan *>(b + o_cs), n, rows, t, keys, cnts, st));
     tc.stop();
@@ -851,13 +896,14 @@ int estimate_poses(int n, const cyl_geom *geoms, const void *const *sinos, cyl_d
                                    reinterpret_cast<double *>(b + o_out));
     PO_CUDA(cudaGetLastError());
     tt.stop();
-    std::vector<double> out((size_t)kOutPose * n);
-    PO_CUDA(cudaMemcpyAsync(out.data(), b + o_out, sizeof(double) * out.size(), cudaMemcpyDeviceToHost, st));
+    const double *out = reinterpret_cast<const double *>(host + (o_out - o_cs));   // after the tables
+    PO_CUDA(cudaMemcpyAsync(host + (o_out - o_cs), b + o_out, sizeof(double) * kOutPose * n, cudaMemcpyDeviceToHost,
+                            st));
     PO_CUDA(cudaStreamSynchronize(st));
     tc.collect();
     tt.collect();
     for (int i = 0; i < n; ++i) {
-        const double *o = out.data() + (size_t)kOutPose * i;
+        const double *o = out + (size_t)kOutPose * i;
         if (poses) poses[i] = cyl_pose{o[12], o[13], o[14], o[15], o[16], o[17]};
         if (infos) {
             cyl_pose_info &f = infos[i];
