@@ -108,6 +108,9 @@ cudaError_t launch_list_count(const GridDev &g, const ProjGeom *geo, int n_proj,
                               cudaStream_t st);
 cudaError_t launch_list_fill(const GridDev &g, const ProjGeom *geo, int n_proj, const int64_t *chunk, int64_t cap,
                              uint32_t *act, float4 *ra, float4 *rb, float4 *rc, cudaStream_t st);
+// Records of the n listed rays for a pose that differs from the list's pose by a spin only.
+cudaError_t launch_list_refill(const GridDev &g, const ProjGeom *geo, const uint32_t *act, int64_t n, float4 *ra,
+                               float4 *rb, float4 *rc, cudaStream_t st);
 // q[v][pix] = (A x)_j for views p0 .. p0+np-1 (overwritten; in compact plans only the listed
 // rays); zero_buf (if not null) is cleared on the way.
 cudaError_t launch_fp_rays(const ScanDev &sd, int P, int p0, int np, const void *x, cyl_dtype xt,

@@ -92,6 +92,11 @@ int cyl_plan::upload_pose(const cyl_pose &po, cudaStream_t st)
     if (!use_list) {
         PL_CUDA(launch_rays(g, d_geo, geom.n_proj, d_ray[0], d_ray[1], d_ray[2], st));
         PL_CUDA(launch_split(scan_dev(), (int64_t)geom.n_proj * n_pix, d_split, st));
+    } else if (d_act && po.alpha == pose.alpha && po.beta == pose.beta && po.tx == pose.tx &&
+               po.ty == pose.ty && po.tz == pose.tz) {
+        // a spin about the part's axis: the grid cylinder, and so the list, stay as they are
+        PL_CUDA(launch_list_refill(g, d_geo, d_act, n_listed, d_ray[0], d_ray[1], d_ray[2], st));
+        PL_CUDA(launch_split(scan_dev(), n_listed, d_split, st));
     } else {
         // count this pose's rays of positive chord, size the compact buffers, then list
         // them with their records and cut them

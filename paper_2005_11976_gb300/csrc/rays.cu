@@ -650,6 +650,30 @@ cudaError_t launch_split(const ScanDev &sd, int64_t n_rays, uint16_t *split, cud
     return cudaGetLastError();
 }
 
+// A spin of the part about its own axis leaves the grid cylinder, and so the list, as it
+// is: only the listed rays' records are set up again.
+__global__ void k_act_refill(GridDev g, const ProjGeom *__restrict__ geo, const uint32_t *__restrict__ act,
+                             int64_t n, float4 *ra, float4 *rb, float4 *rc)
+{
+    const int64_t npix = (int64_t)g.det_w * g.det_h;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = act[e], p = j / npix, pix = j - p * npix;
+        const RayRec rr = setup_ray(g, geo[p], (int)(pix % g.det_w), (int)(pix / g.det_w));
+        ra[e] = rr.a;
+        rb[e] = rr.b;
+        rc[e] = rr.c;
+    }
+}
+
+cudaError_t launch_list_refill(const GridDev &g, const ProjGeom *geo, const uint32_t *act, int64_t n, float4 *ra,
+                               float4 *rb, float4 *rc, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 16);
+    k_act_refill<<<(unsigned)blocks, 256, 0, st>>>(g, geo, act, n, ra, rb, rc);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_list_count(const GridDev &g, const ProjGeom *geo, int n_proj, int64_t *chunk, int64_t *act_off,
                               cudaStream_t st)
 {

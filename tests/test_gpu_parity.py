@@ -223,8 +223,9 @@ def test_dense_and_compact_plans_through_all_poses(lib, orc):
     mostly off it give the oracle's projections and SART iterates (captured sweeps
     included), and the compact plan holds far less."""
     s = synth.Scan(5, 16, 6, 6.0, 10.0, 60.0, 240.0, 28, 24, 1.6, 1.6, synth.full_circle(3) + 0.2)
-    poses = [(0.2, 0.1, 0.3, 0.0, 0.0, 0.0), (0.2, 0.1, 0.3, 14.0, 7.0, 0.0), (0.2, 0.1, 0.3, 0.5, -0.5, 0.0),
-             (0.2, 0.1, 0.3, -14.0, 7.0, 1.0)]
+    # the third pose spins the second about the part's axis (a compact plan keeps its list)
+    poses = [(0.2, 0.1, 0.3, 0.0, 0.0, 0.0), (0.2, 0.1, 0.3, 14.0, 7.0, 0.0), (0.2, 0.1, 1.7, 14.0, 7.0, 0.0),
+             (0.2, 0.1, 0.3, 0.5, -0.5, 0.0), (0.2, 0.1, 0.3, -14.0, 7.0, 1.0)]
     rng = np.random.default_rng(41)
     x = rng.uniform(0.0, 0.05, size=s.vol_shape)
     p = rng.uniform(0.0, 1.0, size=s.sino_shape)
