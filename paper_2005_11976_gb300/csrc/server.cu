@@ -125,7 +125,8 @@ struct cyl_server {
     int next_slot = 0;
     int *d_sched = nullptr;            // work counters of the round kernels (kSched)
 
-    size_t scan_footprint(const Part &pt, int n_proj) const;
+    void footprint(const Part &pt, int n_proj, const double *angles, const cyl_pose &pose, size_t &plan_b,
+                   size_t &scan_b) const;
     int admit(const std::shared_ptr<Scan> &s);
     void release(const std::shared_ptr<Scan> &s);
     void finish(const std::shared_ptr<Scan> &s, int status);
@@ -134,23 +135,37 @@ struct cyl_server {
     void loop();
 };
 
-size_t cyl_server::scan_footprint(const Part &pt, int n_proj) const
+// Device bytes of one scan: its plan, dense (records and cuts of every ray) or compact (of
+// the rays that can meet the grid, bounded from the pose exactly as the plan decides), and
+// the scan's own buffers.
+void cyl_server::footprint(const Part &pt, int n_proj, const double *angles, const cyl_pose &pose,
+                           size_t &plan_b, size_t &scan_b) const
 {
-    const size_t npix = (size_t)pt.geom.det_w * pt.geom.det_h;
+    const size_t npix = (size_t)pt.geom.det_w * pt.geom.det_h, n_rays = (size_t)n_proj * npix;
     const size_t sb = dtype_size(cfg.storage);
     const int subset = std::min(cfg.subset_size, n_proj);
-    size_t b = (size_t)n_proj * npix * 3 * sizeof(float4)        // ray records
-               + (size_t)n_proj * npix * sb                       // sinogram
-               + (size_t)pt.n_vox * sb                             // iterate / output
-               + 2 * (size_t)subset * npix * sizeof(float)         // projection buffers
-               + 2 * (size_t)pt.n_vox * sizeof(float2)            // (num, den) accumulators
-               + (size_t)n_proj * npix * kSplit * sizeof(uint16_t)  // ray cuts
-               + (size_t)n_proj * npix * sizeof(uint32_t)          // list of rays of positive chord (if made)
-               + ((size_t)n_proj * ((npix + kActChunk - 1) / kActChunk) + n_proj + 1) * sizeof(int64_t)
-               + (size_t)n_proj * sizeof(ProjGeom)
-               + 64 * 1024;                                        // small tables
-    if (cfg.storage != CYL_F32) b += (size_t)pt.n_vox * sizeof(float);
-    return b;
+    cyl_geom g = pt.geom;
+    g.n_proj = n_proj;
+    g.angles_rad = angles;
+    std::vector<ProjGeom> geo;
+    build_views(g, pose, geo);
+    const double bound = hit_fraction_bound(pt.grid, g, geo);
+    const size_t per_ray = 3 * sizeof(float4) + kSplit * sizeof(uint16_t);   // records, cuts
+    size_t rays_b;
+    if (n_rays < ((size_t)1 << 32) && bound < 0.75) {
+        const size_t listed = (size_t)std::ceil(bound * (double)n_rays);
+        const size_t room = listed + listed / 8 + 64;
+        rays_b = room * (per_ray + sizeof(uint32_t)) +
+                 ((size_t)n_proj * ((npix + kActChunk - 1) / kActChunk) + n_proj + 1) * sizeof(int64_t);
+    } else {
+        rays_b = n_rays * per_ray;
+    }
+    plan_b = rays_b + 2 * (size_t)subset * npix * sizeof(float)   // projection buffers
+             + 2 * (size_t)pt.n_vox * sizeof(float2)               // (num, den) accumulators
+             + (size_t)n_proj * sizeof(ProjGeom) + 64 * 1024;       // small tables
+    scan_b = n_rays * sb                                             // sinogram
+             + (size_t)pt.n_vox * sb                                 // iterate / output
+             + (cfg.storage != CYL_F32 ? (size_t)pt.n_vox * sizeof(float) : 0);
 }
 
 bool cyl_server::wait_event(cudaEvent_t e)
@@ -358,12 +373,14 @@ void cyl_server::loop()
         while (!queue.empty() && (int)active.size() < cfg.max_active) {
             auto s = queue.front();
             const Part &pt = parts[s->req.part];
-            const size_t fp = scan_footprint(pt, s->req.n_proj);
+            size_t plan_b = 0, scan_b = 0;
+            footprint(pt, s->req.n_proj, s->angles.data(), s->req.pose, plan_b, scan_b);
             // an idle plan of the same part and views is reused: its bytes are counted
             const PlanKey key{s->req.part, s->req.n_proj, hash_angles(s->angles)};
             auto reuse = idle_plans.find(key);
             int64_t reuse_bytes = 0;
             if (reuse != idle_plans.end()) cyl_plan_sizes(reuse->second, nullptr, nullptr, nullptr, &reuse_bytes);
+            const size_t fp = scan_b + std::max(plan_b, (size_t)reuse_bytes);
             if (hbm_in_use - reuse_bytes + (int64_t)fp > cfg.hbm_budget_bytes) {
                 // evict another idle plan, or wait for running scans to finish
                 auto it = idle_plans.begin();
@@ -561,7 +578,9 @@ extern "C" int cyl_submit(cyl_server *srv, const cyl_request *req, uint64_t *tic
         if (rc) return rc;
         int64_t part_bytes = 0;
         for (const Part &p : srv->parts) part_bytes += (int64_t)p.bytes;
-        if (part_bytes + (int64_t)srv->scan_footprint(pt, req->n_proj) > srv->cfg.hbm_budget_bytes)
+        size_t plan_b = 0, scan_b = 0;
+        srv->footprint(pt, req->n_proj, req->angles_rad, req->pose, plan_b, scan_b);
+        if (part_bytes + (int64_t)(plan_b + scan_b) > srv->cfg.hbm_budget_bytes)
             return set_error(CYL_EADMIT, "the scan can never fit the HBM budget");
         s->angles.assign(req->angles_rad, req->angles_rad + req->n_proj);
         s->req.angles_rad = s->angles.data();
