@@ -1102,6 +1102,26 @@ def run_precision(args):
                 storage[key][k] = rel(out, same[k])
                 if k == kmax:
                     rates[key] = kmax / t
+    # kernel times of one FP32 sweep (a CUDA event between launches) and the rooflines of a
+    # grid that no longer fits in L2 (268 MB)
+    plan.cyl_plan_set_timing(True)
+    solve(sino32, x0_32, F32, 1)
+    plan.cyl_plan_set_timing(False)
+    k_ms, k_n = zip(*[plan.cyl_plan_kernel_time(k) for k in range(3)])
+    cnt = torch.empty(scan.n_proj, dtype=torch.int64, device=dev)
+    plan.cyl_count_segments(0, scan.n_proj, cnt)
+    S = float(cnt.float().mean().item())
+    n_pix, n_vox = scan.det_w * scan.det_h, scan.n_vox
+    avg = [k_ms[k] / k_n[k] / 1e3 for k in range(3)]
+    hbm, peak_kind = peaks()
+    own = [S * 4 + n_pix * 52 + n_vox * 8, S * 8 + n_pix * 56, n_vox * 20]
+    spec_fp, spec_bu = S * 4 + n_pix * 8, S * 4 + 3 * n_vox * 4
+    roof = {"bound": "hbm", "peak": hbm, "peak_source": peak_kind, "unit": "GB/s", "segments_per_view": S,
+            "kernel_us_avg": {"k_fp": avg[0] * 1e6, "k_bp": avg[1] * 1e6, "k_update_nd4": avg[2] * 1e6},
+            "kernel_frac": {"k_fp": own[0] / avg[0] / 1e9 / hbm, "k_bp": own[1] / avg[1] / 1e9 / hbm,
+                            "k_update_nd4": own[2] / avg[2] / 1e9 / hbm},
+            "spec_segment_touch_model": {"forward_frac": spec_fp / avg[0] / 1e9 / hbm,
+                                         "back_and_update_frac": spec_bu / (avg[1] + avg[2]) / 1e9 / hbm}}
     clk = clocks.stop()
     line = {
         "metric": METRIC, "value": rates["bf16"], "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 0,
@@ -1114,6 +1134,7 @@ def run_precision(args):
         "storage_rel_l2_per_sweep": storage,
         "inputs_rel_l2_per_sweep": inputs,
         "bound": "storage_rel_l2 <= 2e-3 (default mode)",
+        "roofline_fp32_sweep": roof,
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)
