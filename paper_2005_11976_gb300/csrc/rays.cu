@@ -52,20 +52,19 @@ __device__ __forceinline__ void bp_walk(const GridDev &g, const float2 *__restri
     w.init(g, trig, rr, ua, ub);
     if (nd) {
         // a segment waits one step: if the next one lands in the other half of the same
-        // 16-byte voxel pair, both go out as one 4 x FP32 reduction
+        // 16-byte voxel pair (idx ^ pidx == 1; never with pidx = -1), both go out as one
+        // 4 x FP32 reduction.  A zero-length segment (a tie of two crossings) adds zeros.
         int pidx = -1;
         float pa = 0.f, pl = 0.f;
         auto op = [&](int idx, float len) {
             const float a = len * yv;
-            const bool has = len > 0.f;
-            const bool pair = has && pidx >= 0 && idx != pidx && (idx >> 1) == (pidx >> 1);
+            const bool pair = (idx ^ pidx) == 1;
             const bool lo = (idx & 1) == 0;
             red_add4_if(pair, nd + (idx & ~1), lo ? a : pa, lo ? len : pl, lo ? pa : a, lo ? pl : len);
-            red_add2_if(has && !pair && pidx >= 0, nd + (pidx < 0 ? 0 : pidx), pa, pl);
-            const bool take = has && !pair;
-            pidx = pair ? -1 : (take ? idx : pidx);
-            pa = take ? a : pa;
-            pl = take ? len : pl;
+            red_add2_if(!pair && pidx >= 0, nd + (pidx < 0 ? 0 : pidx), pa, pl);
+            pidx = pair ? -1 : idx;
+            pa = a;
+            pl = len;
         };
         while (w.step(g, trig, op)) {
         }
