@@ -44,7 +44,7 @@ LAMBDA = 0.5
 I0 = 1.0e4
 CONFIG_MEDIUM = {
     "workload": "medium plain SART: grid (128,512,128) R25 H50, 180 views over 360 deg, 256x256 det "
-                "0.8 mm, SOD 200 SDD 800, 20 sweeps lambda 0.5, warm start, ROI weights 4x, Poisson I0 1e4",
+                "0.8 mm, SOD 200 SDD 800, 20 sweeps lambda 0.5, warm start, ROI weights 4x (U8 class map), Poisson I0 1e4",
     "l2": "flushed (256 MB write) before every timed step",
 }
 
@@ -242,11 +242,11 @@ def main():
     counts = torch.poisson(I0 * torch.exp(-p_clean), generator=gen)
     del xp
     x0 = torch.from_numpy(x_warm.astype(np.float32)).to(dev)
-    wd = torch.from_numpy(w.astype(np.float32)).to(dev)
+    wd = torch.from_numpy(_class_map(w)).to(dev)
     p = torch.empty_like(counts)
     x_out = torch.empty(scan.vol_shape, dtype=torch.float32, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
-    prm = cylct.sart_params(n_iter=N_ITER, lam=LAMBDA, use_graph=bool(args.graph))
+    prm = cylct.sart_params(n_iter=N_ITER, lam=LAMBDA, use_graph=bool(args.graph), weight_dtype=cylct.CYL_U8)
     plan.cyl_plan_set_timing(True)
 
     def step(st):
@@ -342,16 +342,16 @@ def main():
         #   forward: one volume value per segment, the ray records, the projections written,
         #            and the spare (num, den) accumulator cleared for the next subset
         #   back:    one 8-byte (num, den) update per segment, the ray records, y and q read
-        #   update:  (num, den), x read and written, the weight map read
+        #   update:  (num, den), x read and written, the U8 weight class map read
         per = [S * 4 + n_pix * (ray_rec + 4) + n_vox * 8,
                S * 8 + n_pix * (ray_rec + 4 + 4),
-               n_vox * (8 + 4 + 4 + 4)]
+               n_vox * (8 + 4 + 4 + 1)]
         avg_ms = [k_ms[k] / k_n[k] for k in range(3)]
         dom = int(np.argmax(k_ms))
         ach = [per[k] / (avg_ms[k] / 1e3) / 1e9 for k in range(3)]
         # compulsory model: every array of a subset once (x read by the projector, read and
         # written by the update; w; p, q and the residual)
-        comp = 3 * n_vox * 4 + n_vox * 4 + 3 * n_pix * 4
+        comp = 3 * n_vox * 4 + n_vox * 1 + 3 * n_pix * 4
         t_view = sum(avg_ms) / 1e3
         compulsory = {"bytes_per_subset": comp, "achieved": comp / t_view / 1e9, "frac": comp / t_view / 1e9 / hbm,
                       "unit": "GB/s", "subset_ms": t_view * 1e3}
@@ -359,7 +359,7 @@ def main():
         # back-projection and update together S 4 + 2 V_hit b_v + V_hit b_w (V_hit = V here:
         # every voxel of the grid is crossed by some ray of a medium view)
         st_fp = S * 4 + n_pix * 8
-        st_bu = S * 4 + 2 * n_vox * 4 + n_vox * 4
+        st_bu = S * 4 + 2 * n_vox * 4 + n_vox * 1
         t_fp, t_bu = avg_ms[0] / 1e3, (avg_ms[1] + avg_ms[2]) / 1e3
         spec_model = {"forward": {"bytes": st_fp, "achieved": st_fp / t_fp / 1e9, "frac": st_fp / t_fp / 1e9 / hbm},
                       "back_and_update": {"bytes": st_bu, "achieved": st_bu / t_bu / 1e9,
@@ -401,7 +401,7 @@ def main():
             pv = torch.empty_like(cv)
             cylct.cyl_log_transform(cv, cylct.CYL_F32, I0, pv, cylct.CYL_F32, n_pix, stream)
             xg = torch.empty_like(x_out)
-            p1.cyl_sart_solve(pv, cylct.CYL_F32, x0, wd, cylct.sart_params(n_iter=1, lam=LAMBDA),
+            p1.cyl_sart_solve(pv, cylct.CYL_F32, x0, wd, cylct.sart_params(n_iter=1, lam=LAMBDA, weight_dtype=cylct.CYL_U8),
                               xg, cylct.CYL_F32, stream)
             torch.cuda.synchronize()
             xg = xg.cpu().numpy().astype(np.float64)
@@ -453,6 +453,13 @@ def _part_data(scan, rng):
     return synth.part_phantom(scan, az), synth.part_phantom(scan, az, removed=int(rng.integers(8)))
 
 
+def _class_map(w):
+    """The ROI weight map (weights 1 and 4) as a U8 class map: one byte per voxel."""
+    v = np.rint(w)
+    assert np.array_equal(v, w) and v.min() >= 0 and v.max() <= 255
+    return v.astype(np.uint8)
+
+
 def _sinogram(torch, cylct, plan, scan, x_part, i0, seed, dtype):
     """Line integrals of x_part projected on the GPU with Poisson counts at I0."""
     dev = torch.device("cuda")
@@ -480,20 +487,20 @@ def run_batched(args):
     w = synth.roi_weights(scans[0])
     dev = torch.device("cuda")
     x0 = torch.from_numpy(x_warm.astype(np.float32)).to(dev)
-    wd = torch.from_numpy(w.astype(np.float32)).to(dev)
+    wd = torch.from_numpy(_class_map(w)).to(dev)
     plans = [cylct.Plan(s) for s in scans]
     sinos = [_sinogram(torch, cylct, plans[i], s, x_part, I0, 100 + i, cylct.CYL_F32)
              for i, s in enumerate(scans)]
     outs_b = [torch.empty(s.vol_shape, device=dev) for s in scans]
     outs_p = [torch.empty(s.vol_shape, device=dev) for s in scans]
-    prm = cylct.sart_params(n_iter=10, lam=LAMBDA)
+    prm = cylct.sart_params(n_iter=10, lam=LAMBDA, weight_dtype=cylct.CYL_U8)
     # the batch autotuner times round 0 for every piece setting (the batch uses plans[0]'s)
     cylct.cyl_sart_tune_batch(plans, sinos, cylct.CYL_F32, [x0] * n, [wd] * n, prm, outs_b, cylct.CYL_F32)
     pieces = plans[0].cyl_plan_get_pieces()
     # warm-up: one small batched and one plain solve
     cylct.cyl_sart_solve_batch(plans[:2], sinos[:2], cylct.CYL_F32, [x0, x0], [wd, wd],
-                               cylct.sart_params(n_iter=1, lam=LAMBDA), outs_b[:2], cylct.CYL_F32)
-    plans[0].cyl_sart_solve(sinos[0], cylct.CYL_F32, x0, wd, cylct.sart_params(n_iter=1, lam=LAMBDA),
+                               cylct.sart_params(n_iter=1, lam=LAMBDA, weight_dtype=cylct.CYL_U8), outs_b[:2], cylct.CYL_F32)
+    plans[0].cyl_sart_solve(sinos[0], cylct.CYL_F32, x0, wd, cylct.sart_params(n_iter=1, lam=LAMBDA, weight_dtype=cylct.CYL_U8),
                             outs_p[0], cylct.CYL_F32)
     torch.cuda.synchronize()
     clocks = ClockSampler(0)
@@ -555,9 +562,9 @@ def run_table1(args):
     plan = cylct.Plan(scan)
     sino = _sinogram(torch, cylct, plan, scan, x_part, I0, 77, cylct.CYL_F32)
     x0 = torch.from_numpy(x_warm.astype(np.float32)).to(dev)
-    wd = torch.from_numpy(w.astype(np.float32)).to(dev)
+    wd = torch.from_numpy(_class_map(w)).to(dev)
     out = torch.empty(scan.vol_shape, device=dev)
-    plain = cylct.sart_params(n_iter=sweeps, lam=LAMBDA)
+    plain = cylct.sart_params(n_iter=sweeps, lam=LAMBDA, weight_dtype=cylct.CYL_U8)
     for _ in range(max(3, args.warmup)):
         plan.cyl_sart_solve(sino, cylct.CYL_F32, x0, None, cylct.sart_params(n_iter=1, lam=LAMBDA), out,
                             cylct.CYL_F32)
@@ -597,7 +604,7 @@ def run_table1(args):
             pv = torch.empty_like(cv)
             cylct.cyl_log_transform(cv, cylct.CYL_F32, I0, pv, cylct.CYL_F32, cv.numel())
             xg = torch.empty_like(out)
-            p1.cyl_sart_solve(pv, cylct.CYL_F32, x0, wd, cylct.sart_params(n_iter=1, lam=LAMBDA), xg, cylct.CYL_F32)
+            p1.cyl_sart_solve(pv, cylct.CYL_F32, x0, wd, cylct.sart_params(n_iter=1, lam=LAMBDA, weight_dtype=cylct.CYL_U8), xg, cylct.CYL_F32)
             torch.cuda.synchronize()
             xg = xg.cpu().numpy().astype(np.float64)
         parity = float(np.linalg.norm(xg - x1_or) / np.linalg.norm(x1_or))
@@ -964,12 +971,12 @@ def run_serving(args):
         reqs.append((t_arr, pt, scan, sino))
     torch.cuda.synchronize()
     # ---- served
-    srv = cylct.Server(150 << 30, max_active=64, n_iter=10, lam=LAMBDA, storage=bf16)
+    srv = cylct.Server(150 << 30, max_active=64, n_iter=10, lam=LAMBDA, storage=bf16, weight_dtype=cylct.CYL_U8)
     pid = {}
     keep = []
     for pt, (base, x_warm, az, w) in parts.items():
         x0 = torch.from_numpy(x_warm.astype(np.float32)).to(dev).to(torch.bfloat16)
-        wd = torch.from_numpy(w.astype(np.float32)).to(dev)
+        wd = torch.from_numpy(_class_map(w)).to(dev)
         keep += [x0, wd]
         pid[pt] = srv.cyl_server_add_part(base, x0, wd)
     outs = [torch.empty(s.vol_shape, dtype=torch.bfloat16, device=dev) for _, _, s, _ in reqs]
@@ -997,12 +1004,12 @@ def run_serving(args):
     for k, (t_arr, pt, s, sino) in enumerate(reqs):
         base, x_warm, az, w = parts[pt]
         x0 = torch.from_numpy(x_warm.astype(np.float32)).to(dev).to(torch.bfloat16)
-        wd = torch.from_numpy(w.astype(np.float32)).to(dev)
+        wd = torch.from_numpy(_class_map(w)).to(dev)
         out = torch.empty(s.vol_shape, dtype=torch.bfloat16, device=dev)
         with cylct.Plan(s) as pl:
             torch.cuda.synchronize()
             a = time.perf_counter()
-            pl.cyl_sart_solve(sino, bf16, x0, wd, cylct.sart_params(n_iter=10, lam=LAMBDA), out, bf16)
+            pl.cyl_sart_solve(sino, bf16, x0, wd, cylct.sart_params(n_iter=10, lam=LAMBDA, weight_dtype=cylct.CYL_U8), out, bf16)
             torch.cuda.synchronize()
             svc.append(time.perf_counter() - a)
         outs_p.append(out)

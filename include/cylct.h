@@ -56,7 +56,9 @@ extern "C" {
 #define CYL_EPENDING (-7)  /* result not ready yet (cyl_poll) */
 #define CYL_ECANCELLED (-8) /* request cancelled or server shut down */
 
-typedef enum { CYL_F32 = 0, CYL_F16 = 1, CYL_BF16 = 2 } cyl_dtype;
+/* Element types.  Sinograms and volumes: F32, F16 or BF16.  Weight maps (Sec. 2.2
+ * weighted back-projection) also U8: a class map whose byte values are the weights. */
+typedef enum { CYL_F32 = 0, CYL_F16 = 1, CYL_BF16 = 2, CYL_U8 = 3 } cyl_dtype;
 
 /* Cylindrical grid about the part's axis (Sec. 2, Eq. 2). */
 #define CYL_MAX_N_THETA 6144     /* the wedge (cos, sin) table is staged in 48 KB of shared memory */
@@ -98,6 +100,8 @@ typedef struct cyl_sart_params {
                               (rounded after every subset); 0 = FP32 working iterate with a
                               16-bit copy that the projector reads */
     int32_t use_graph;     /* 1: replay each sweep as a captured CUDA graph */
+    int32_t weight_dtype;  /* element type of the weight map: CYL_F32 (0), CYL_F16,
+                              CYL_BF16 or CYL_U8; weights must be >= 0 */
 } cyl_sart_params;
 
 typedef struct cyl_plan cyl_plan;
@@ -168,18 +172,19 @@ int cyl_backproject(cyl_plan *plan, const void *sino, cyl_dtype sino_dtype, int3
                     int32_t np, float *vol_out, float *colsum_out, void *stream);
 
 /* SART (Eq. 7) over all projections: x0 (warm start, Sec. 2.2 / 3.3 "initial volume";
- * NULL = zeros), weight map w (weighted back-projection, Sec. 2.2; NULL = none; FP32),
+ * NULL = zeros), weight map w (weighted back-projection, Sec. 2.2; NULL = none; of
+ * params->weight_dtype),
  * n_iter sweeps of ordered subsets in index order; the result goes to x_out.
  *   sino:  [N_p][H][W] line integrals of sino_dtype;
  *   x0:    [N_h][N_theta][N_r] of x_dtype, or NULL;
- *   w:     [N_h][N_theta][N_r] float, or NULL;
+ *   w:     [N_h][N_theta][N_r] of params->weight_dtype (>= 0), or NULL;
  *   x_out: [N_h][N_theta][N_r] of x_dtype (may equal x0).
  * Pointers may be device or host memory (each is checked); host arrays are staged
  * through plan-owned device buffers and the call then returns after x_out is written.
  * Rays with L_j = 0 contribute nothing; voxels no ray of a subset touches keep their
  * value.  Errors: CYL_EINVAL, CYL_ENOMEM, CYL_EDEVICE. */
 int cyl_sart_solve(cyl_plan *plan, const void *sino, cyl_dtype sino_dtype, const void *x0,
-                   const float *w, const cyl_sart_params *params, void *x_out,
+                   const void *w, const cyl_sart_params *params, void *x_out,
                    cyl_dtype x_dtype, void *stream);
 
 /* Batched SART: n scans (0 <= n <= CYL_MAX_BATCH; each its own plan: own pose,
@@ -190,12 +195,13 @@ int cyl_sart_solve(cyl_plan *plan, const void *sino, cyl_dtype sino_dtype, const
  * per scan; all rounds are queued as one CUDA graph (params->use_graph).  The plans'
  * piece settings are those of plans[0].
  * Arrays (per scan i, in plan i's layout): sinos[i] of sino_dtype, x0s[i] (x0s or its
- * entries NULL = zeros), ws[i] FP32 weights (ws or its entries NULL = none), x_outs[i] of
+ * entries NULL = zeros), ws[i] weights of params->weight_dtype (ws or its entries NULL =
+ * none), x_outs[i] of
  * x_dtype.  All DEVICE pointers on the plans' device; host arrays give CYL_EINVAL.
  * Asynchronous on `stream`.  Errors: CYL_EINVAL, CYL_ENOMEM, CYL_EDEVICE. */
 #define CYL_MAX_BATCH 4096
 int cyl_sart_solve_batch(int32_t n, cyl_plan *const *plans, const void *const *sinos,
-                         cyl_dtype sino_dtype, const void *const *x0s, const float *const *ws,
+                         cyl_dtype sino_dtype, const void *const *x0s, const void *const *ws,
                          const cyl_sart_params *params, void *const *x_outs, cyl_dtype x_dtype,
                          void *stream);
 
@@ -206,7 +212,7 @@ int cyl_sart_solve_batch(int32_t n, cyl_plan *const *plans, const void *const *s
  * and the iterate are not touched).  Synchronises the plans' work.  Errors as for
  * cyl_sart_solve_batch. */
 int cyl_sart_tune_batch(int32_t n, cyl_plan *const *plans, const void *const *sinos,
-                        cyl_dtype sino_dtype, const void *const *x0s, const float *const *ws,
+                        cyl_dtype sino_dtype, const void *const *x0s, const void *const *ws,
                         const cyl_sart_params *params, void *const *x_outs, cyl_dtype x_dtype,
                         void *stream);
 
@@ -233,6 +239,8 @@ typedef struct cyl_server_cfg {
     cyl_dtype storage;          /* dtype of sinograms and volumes (F32, F16 or BF16) */
     int32_t rounds_ahead;       /* rounds queued on the GPU before the scheduler waits,
                                    1 .. 64 (0 = 4) */
+    int32_t weight_dtype;       /* element type of the parts' weight maps (as in
+                                   cyl_sart_params; 0 = CYL_F32) */
 } cyl_server_cfg;
 
 /* A request: one scan of a registered part type.  sino ([n_proj][H][W] line integrals of
@@ -266,11 +274,11 @@ int cyl_server_create(const cyl_server_cfg *cfg, cyl_server **out);
 
 /* Register a part type: its grid, its acquisition geometry (geom->n_proj and
  * geom->angles_rad are ignored: every request brings its own), a warm-start volume x0
- * (storage dtype, NULL = zeros) and a weight map w (FP32, NULL = none), host or device
+ * (storage dtype, NULL = zeros) and a weight map w (cfg->weight_dtype, NULL = none), host or device
  * memory, copied into resident device memory.  *part receives the part id.  Errors:
  * CYL_EINVAL, CYL_EADMIT (the part alone exceeds the budget), CYL_ENOMEM, CYL_EDEVICE. */
 int cyl_server_add_part(cyl_server *srv, const cyl_grid *grid, const cyl_geom *geom,
-                        const void *x0, const float *w, int32_t *part);
+                        const void *x0, const void *w, int32_t *part);
 
 /* Queue a request; *ticket identifies it.  Never blocks on the GPU.  Errors: CYL_EINVAL,
  * CYL_EADMIT (the scan can never fit the budget next to the resident parts),

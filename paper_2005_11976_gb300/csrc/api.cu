@@ -310,7 +310,7 @@ extern "C" int cyl_plan_kernel_time(cyl_plan *plan, int kind, double *ms_total, 
 }
 
 extern "C" int cyl_sart_solve(cyl_plan *plan, const void *sino, cyl_dtype sino_dtype, const void *x0,
-                              const float *w, const cyl_sart_params *params, void *x_out,
+                              const void *w, const cyl_sart_params *params, void *x_out,
                               cyl_dtype x_dtype, void *stream)
 {
     if (!plan || !params) return set_error(CYL_EINVAL, "plan or params is null");
@@ -321,6 +321,7 @@ extern "C" int cyl_sart_solve(cyl_plan *plan, const void *sino, cyl_dtype sino_d
     if (!std::isfinite(params->lambda)) return set_error(CYL_EINVAL, "lambda must be finite");
     if (params->weight_mode != 0 && params->weight_mode != 1)
         return set_error(CYL_EINVAL, "weight_mode must be 0 or 1");
+    if (!valid_weight_dtype(params->weight_dtype)) return set_error(CYL_EINVAL, "bad weight dtype");
     DeviceGuard dg(plan->device);
     std::lock_guard<std::mutex> lock(plan->mu);
     return plan->solve(sino, sino_dtype, x0, w, *params, x_out, x_dtype, (cudaStream_t)stream);

@@ -75,7 +75,7 @@ namespace {
 // fastest of each is stored in plans[0], whose settings the batch uses.  Tuning writes
 // only the plans' scratch (projections and accumulators, cleared by every solve).
 int batch_run(int32_t n, cyl_plan *const *plans, const void *const *sinos, cyl_dtype sino_dtype,
-              const void *const *x0s, const float *const *ws, const cyl_sart_params *prm,
+              const void *const *x0s, const void *const *ws, const cyl_sart_params *prm,
               void *const *x_outs, cyl_dtype x_dtype, void *stream, bool tune)
 {
     if (n < 0 || (n > 0 && (!plans || !sinos || !x_outs)) || !prm)
@@ -85,7 +85,7 @@ int batch_run(int32_t n, cyl_plan *const *plans, const void *const *sinos, cyl_d
     if (sino_dtype < CYL_F32 || sino_dtype > CYL_BF16 || x_dtype < CYL_F32 || x_dtype > CYL_BF16)
         return set_error(CYL_EINVAL, "bad dtype");
     if (prm->n_iter < 0 || prm->subset_size < 1 || !std::isfinite(prm->lambda) ||
-        (prm->weight_mode != 0 && prm->weight_mode != 1))
+        (prm->weight_mode != 0 && prm->weight_mode != 1) || !valid_weight_dtype(prm->weight_dtype))
         return set_error(CYL_EINVAL, "bad SART parameters");
     const int dev = plans[0] ? plans[0]->device : -1;
     for (int i = 0; i < n; ++i) {
@@ -144,7 +144,7 @@ int batch_run(int32_t n, cyl_plan *const *plans, const void *const *sinos, cyl_d
         if ((rc = pl->ensure((void **)&pl->d_q, pl->q_cap, 2 * sizeof(float) * qlen))) return rc;
         for (int k = 0; k < 2; ++k) BT_CUDA(cudaMemsetAsync(pl->d_nd[k], 0, sizeof(float2) * pl->n_vox, bs));
         const void *x0 = x0s ? x0s[i] : nullptr;
-        const float *w = ws ? ws[i] : nullptr;
+        const void *w = ws ? ws[i] : nullptr;
         void *xo = x_outs[i];
         if (!tune && x0 && x0 != xo) BT_CUDA(cudaMemcpyAsync(xo, x0, xb * pl->n_vox, cudaMemcpyDeviceToDevice, bs));
         if (!tune && !x0) BT_CUDA(cudaMemsetAsync(xo, 0, xb * pl->n_vox, bs));
@@ -179,11 +179,13 @@ int batch_run(int32_t n, cyl_plan *const *plans, const void *const *sinos, cyl_d
             if (!tune) BT_CUDA(launch_convert(xo, x_dtype, pl->d_x32, CYL_F32, pl->n_vox, bs));
         }
         u.w = w;
+        u.w_t = (cyl_dtype)prm->weight_dtype;
         u.wscale = w ? pl->d_wscale : nullptr;
         u.lambda = (float)prm->lambda;
         u.clamp = prm->clamp_nonneg ? 1 : 0;
         if (w && !tune)
-            BT_CUDA(launch_weight_scale(w, pl->n_vox, prm->weight_mode, (float)prm->lambda, pl->d_wscale, bs));
+            BT_CUDA(launch_weight_scale(w, u.w_t, pl->n_vox, prm->weight_mode, (float)prm->lambda, pl->d_wscale,
+                                        bs));
         n_proj[i] = pl->geom.n_proj;
     }
     std::vector<BatchItem> items;
@@ -286,7 +288,7 @@ int batch_run(int32_t n, cyl_plan *const *plans, const void *const *sinos, cyl_d
 
 extern "C" int cyl_sart_solve_batch(int32_t n, cyl_plan *const *plans, const void *const *sinos,
                                     cyl_dtype sino_dtype, const void *const *x0s,
-                                    const float *const *ws, const cyl_sart_params *prm,
+                                    const void *const *ws, const cyl_sart_params *prm,
                                     void *const *x_outs, cyl_dtype x_dtype, void *stream)
 {
     return batch_run(n, plans, sinos, sino_dtype, x0s, ws, prm, x_outs, x_dtype, stream, false);
@@ -294,7 +296,7 @@ extern "C" int cyl_sart_solve_batch(int32_t n, cyl_plan *const *plans, const voi
 
 extern "C" int cyl_sart_tune_batch(int32_t n, cyl_plan *const *plans, const void *const *sinos,
                                    cyl_dtype sino_dtype, const void *const *x0s,
-                                   const float *const *ws, const cyl_sart_params *prm,
+                                   const void *const *ws, const cyl_sart_params *prm,
                                    void *const *x_outs, cyl_dtype x_dtype, void *stream)
 {
     return batch_run(n, plans, sinos, sino_dtype, x0s, ws, prm, x_outs, x_dtype, stream, true);

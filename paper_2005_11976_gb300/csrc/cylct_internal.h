@@ -63,7 +63,8 @@ struct UpdateArgs {
     void *x16;              // 16-bit copy / iterate (null in FP32 mode)
     cyl_dtype x16_t;
     int strict16;
-    const float *w;         // weight map or null
+    const void *w;          // weight map (w_t elements) or null
+    cyl_dtype w_t;
     const float *wscale;    // device scalar lambda / max(w) (or lambda), or null
     float lambda;
     int clamp;
@@ -138,9 +139,11 @@ cudaError_t launch_log(const void *in, cyl_dtype it, double i0, void *out, cyl_d
                        int64_t n, cudaStream_t st);
 cudaError_t launch_convert(const void *in, cyl_dtype it, void *out, cyl_dtype ot,
                            int64_t n, cudaStream_t st);
-cudaError_t launch_weight_scale(const float *w, int64_t n, int mode, float lambda,
+cudaError_t launch_weight_scale(const void *w, cyl_dtype w_t, int64_t n, int mode, float lambda,
                                 float *wscale, cudaStream_t st);
 
 size_t dtype_size(cyl_dtype t);
+// element types a weight map may have (sinograms and volumes: F32, F16, BF16 only)
+inline bool valid_weight_dtype(int t) { return t == CYL_F32 || t == CYL_F16 || t == CYL_BF16 || t == CYL_U8; }
 
 }  // namespace cylct

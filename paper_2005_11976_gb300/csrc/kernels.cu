@@ -6,7 +6,7 @@
 
 namespace cylct {
 
-size_t dtype_size(cyl_dtype t) { return t == CYL_F32 ? 4 : 2; }
+size_t dtype_size(cyl_dtype t) { return t == CYL_F32 ? 4 : (t == CYL_U8 ? 1 : 2); }
 
 template <class T> __device__ __forceinline__ float to_f32(T v);
 template <> __device__ __forceinline__ float to_f32<float>(float v) { return v; }
@@ -46,12 +46,13 @@ __global__ void k_row_sums(ScanDev sd, int p0, float *L)
 
 // ------------------------------------------------------------ elementwise kernels
 
-__global__ void k_wmax(const float *__restrict__ w, int64_t n, unsigned int *out)
+template <class W>
+__global__ void k_wmax(const W *__restrict__ w, int64_t n, unsigned int *out)
 {
     float v = 0.f;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
-        v = fmaxf(v, w[i]);
+        v = fmaxf(v, weight_f32(w[i]));
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_down_sync(0xffffffffu, v, o));
     if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(v));  // v >= 0: order-preserving
 }
@@ -161,7 +162,7 @@ cudaError_t launch_convert(const void *in, cyl_dtype it, void *out, cyl_dtype ot
     });
 }
 
-cudaError_t launch_weight_scale(const float *w, int64_t n, int mode, float lambda, float *wscale,
+cudaError_t launch_weight_scale(const void *w, cyl_dtype w_t, int64_t n, int mode, float lambda, float *wscale,
                                 cudaStream_t st)
 {
     // wscale[0] receives lambda / max(w) (mode 1) or lambda (mode 0); wscale[1] is the
@@ -170,7 +171,14 @@ cudaError_t launch_weight_scale(const float *w, int64_t n, int mode, float lambd
     cudaError_t e = cudaMemsetAsync(bits, 0, sizeof(unsigned int), st);
     if (e != cudaSuccess) return e;
     if (n > 0) {
-        k_wmax<<<elementwise_blocks(n), 256, 0, st>>>(w, n, bits);
+        const unsigned nb = elementwise_blocks(n);
+        switch (w_t) {
+        case CYL_F32: k_wmax<<<nb, 256, 0, st>>>(static_cast<const float *>(w), n, bits); break;
+        case CYL_F16: k_wmax<<<nb, 256, 0, st>>>(static_cast<const __half *>(w), n, bits); break;
+        case CYL_BF16: k_wmax<<<nb, 256, 0, st>>>(static_cast<const __nv_bfloat16 *>(w), n, bits); break;
+        case CYL_U8: k_wmax<<<nb, 256, 0, st>>>(static_cast<const uint8_t *>(w), n, bits); break;
+        default: return cudaErrorInvalidValue;
+        }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     k_wscale<<<1, 1, 0, st>>>(bits, mode, lambda, wscale);

@@ -187,6 +187,7 @@ int cyl_plan::queue_sweep(const SolveState &s, cudaStream_t st, bool timed, int 
     upd.x16_t = s.x16_t;
     upd.strict16 = s.strict16;
     upd.w = s.w;
+    upd.w_t = s.w_t;
     upd.wscale = s.w ? d_wscale : nullptr;
     upd.lambda = (float)s.lambda;
     upd.clamp = s.clamp;
@@ -212,7 +213,7 @@ int cyl_plan::queue_sweep(const SolveState &s, cudaStream_t st, bool timed, int 
     return CYL_OK;
 }
 
-int cyl_plan::solve(const void *sino, cyl_dtype sino_t, const void *x0, const float *w,
+int cyl_plan::solve(const void *sino, cyl_dtype sino_t, const void *x0, const void *w,
                     const cyl_sart_params &prm, void *x_out, cyl_dtype x_t, cudaStream_t user)
 {
     const PtrKind ks = kind_of(sino), kx0 = kind_of(x0), kw = kind_of(w), kxo = kind_of(x_out);
@@ -229,7 +230,9 @@ int cyl_plan::solve(const void *sino, cyl_dtype sino_t, const void *x0, const fl
 
     // stage host inputs
     const void *d_sino = sino, *d_x0 = x0;
-    const float *d_w = w;
+    const void *d_w = w;
+    const cyl_dtype w_t = (cyl_dtype)prm.weight_dtype;
+    const size_t wb = dtype_size(w_t);
     if (ks == kHost) {
         if ((rc = ensure(&d_stage[0], stage_cap[0], sino_bytes))) return rc;
         PL_CUDA(cudaMemcpyAsync(d_stage[0], sino, sino_bytes, cudaMemcpyHostToDevice, ws));
@@ -241,9 +244,9 @@ int cyl_plan::solve(const void *sino, cyl_dtype sino_t, const void *x0, const fl
         d_x0 = d_stage[1];
     }
     if (kw == kHost) {
-        if ((rc = ensure(&d_stage[2], stage_cap[2], sizeof(float) * n_vox))) return rc;
-        PL_CUDA(cudaMemcpyAsync(d_stage[2], w, sizeof(float) * n_vox, cudaMemcpyHostToDevice, ws));
-        d_w = (const float *)d_stage[2];
+        if ((rc = ensure(&d_stage[2], stage_cap[2], wb * n_vox))) return rc;
+        PL_CUDA(cudaMemcpyAsync(d_stage[2], w, wb * n_vox, cudaMemcpyHostToDevice, ws));
+        d_w = d_stage[2];
     }
     void *d_xo = x_out;
     if (kxo == kHost) {
@@ -256,6 +259,7 @@ int cyl_plan::solve(const void *sino, cyl_dtype sino_t, const void *x0, const fl
     s.sino = d_sino;
     s.sino_t = sino_t;
     s.w = d_w;
+    s.w_t = w_t;
     s.lambda = prm.lambda;
     s.clamp = prm.clamp_nonneg ? 1 : 0;
     s.subset = subset;
@@ -281,7 +285,7 @@ int cyl_plan::solve(const void *sino, cyl_dtype sino_t, const void *x0, const fl
         s.x_proj_t = CYL_F32;
         PL_CUDA(launch_convert(d_xo, x_t, d_x32, CYL_F32, n_vox, ws));
     }
-    if (d_w) PL_CUDA(launch_weight_scale(d_w, n_vox, prm.weight_mode, (float)prm.lambda, d_wscale, ws));
+    if (d_w) PL_CUDA(launch_weight_scale(d_w, w_t, n_vox, prm.weight_mode, (float)prm.lambda, d_wscale, ws));
     for (int k = 0; k < 2; ++k) PL_CUDA(cudaMemsetAsync(d_nd[k], 0, sizeof(float2) * n_vox, ws));
 
     const bool one_graph = !(n_sub & 1) || prm.n_iter == 1;

@@ -35,7 +35,8 @@ struct SolveState {
     void *x16 = nullptr;           // 16-bit copy / iterate (null in FP32 mode)
     cyl_dtype x16_t = CYL_F16;
     int strict16 = 0;
-    const float *w = nullptr;
+    const void *w = nullptr;
+    cyl_dtype w_t = CYL_F32;
     double lambda = 0.5;
     int clamp = 0;
     int subset = 1;
@@ -44,7 +45,7 @@ struct SolveState {
     {
         return sino == o.sino && sino_t == o.sino_t && x_proj == o.x_proj &&
                x_proj_t == o.x_proj_t && x32 == o.x32 && x16 == o.x16 && x16_t == o.x16_t &&
-               strict16 == o.strict16 && w == o.w && lambda == o.lambda && clamp == o.clamp &&
+               strict16 == o.strict16 && w == o.w && w_t == o.w_t && lambda == o.lambda && clamp == o.clamp &&
                subset == o.subset;
     }
 };
@@ -145,7 +146,7 @@ struct cyl_plan {
     int queue_sweep(const cylct::SolveState &s, cudaStream_t st, bool timed, int parity);
     void drop_graphs();
     int tune(cudaStream_t st);
-    int solve(const void *sino, cyl_dtype sino_t, const void *x0, const float *w,
+    int solve(const void *sino, cyl_dtype sino_t, const void *x0, const void *w,
               const cyl_sart_params &prm, void *x_out, cyl_dtype x_t, cudaStream_t user);
     ~cyl_plan();
 };

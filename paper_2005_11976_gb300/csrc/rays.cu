@@ -88,13 +88,51 @@ __device__ __forceinline__ float ray_sum(float v, int P)
     return v;
 }
 
+// weight of voxel m (1 without a map); the element type is uniform over a launch
+__device__ __forceinline__ float weight_at(const UpdateArgs &u, int64_t m)
+{
+    if (!u.w) return 1.f;
+    switch (u.w_t) {
+    case CYL_F16: return weight_f32(__ldg(static_cast<const __half *>(u.w) + m));
+    case CYL_BF16: return weight_f32(__ldg(static_cast<const __nv_bfloat16 *>(u.w) + m));
+    case CYL_U8: return weight_f32(__ldg(static_cast<const uint8_t *>(u.w) + m));
+    default: return __ldg(static_cast<const float *>(u.w) + m);
+    }
+}
+
+// weights of voxels 4i .. 4i + 3 in one aligned load (4, 8 or 16 bytes)
+__device__ __forceinline__ float4 weight4_at(const UpdateArgs &u, int64_t i)
+{
+    if (!u.w) return make_float4(1.f, 1.f, 1.f, 1.f);
+    switch (u.w_t) {
+    case CYL_F16: {
+        const uint2 r = __ldg(static_cast<const uint2 *>(u.w) + i);
+        const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&r.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&r.y));
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+    case CYL_BF16: {
+        const uint2 r = __ldg(static_cast<const uint2 *>(u.w) + i);
+        const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&r.x));
+        const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&r.y));
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+    case CYL_U8: {
+        const unsigned r = __ldg(static_cast<const unsigned *>(u.w) + i);
+        return make_float4((float)(r & 0xffu), (float)((r >> 8) & 0xffu), (float)((r >> 16) & 0xffu),
+                           (float)(r >> 24));
+    }
+    default: return __ldg(static_cast<const float4 *>(u.w) + i);
+    }
+}
+
 template <class X>
 __device__ __forceinline__ void update_voxel(const UpdateArgs &u, int64_t m, float2 v, float sc)
 {
     if (!(v.y > 0.f)) return;
     X *x16 = static_cast<X *>(u.x16);
     float xv = u.strict16 ? as_f32<X>(x16[m]) : u.x32[m];
-    const float wm = u.w ? __ldg(u.w + m) : 1.f;
+    const float wm = weight_at(u, m);
     xv = fmaf(sc * wm, v.x / v.y, xv);
     if (u.clamp) xv = fmaxf(xv, 0.f);
     if (!u.strict16) u.x32[m] = xv;
@@ -362,7 +400,7 @@ __device__ __forceinline__ void update4(const UpdateArgs &u, const float4 *__res
 {
     float4 *x = reinterpret_cast<float4 *>(u.x32);
     const float4 a = __ldg(nd + 2 * i), b = __ldg(nd + 2 * i + 1);
-    const float4 wv = u.w ? __ldg(reinterpret_cast<const float4 *>(u.w) + i) : make_float4(1.f, 1.f, 1.f, 1.f);
+    const float4 wv = weight4_at(u, i);
     float4 xv = x[i];
     xv.x = upd1(xv.x, a.x, a.y, wv.x, sc, u.clamp);
     xv.y = upd1(xv.y, a.z, a.w, wv.y, sc, u.clamp);
@@ -373,8 +411,9 @@ __device__ __forceinline__ void update4(const UpdateArgs &u, const float4 *__res
 
 __host__ __device__ inline bool update4_ok(const UpdateArgs &u, const void *nd, int64_t n)
 {
-    const auto a16 = [](const void *p) { return ((uintptr_t)p & 15) == 0; };
-    return !u.x16 && !u.strict16 && (n & 3) == 0 && a16(u.x32) && a16(u.w) && a16(nd);
+    const auto al = [](const void *p, uintptr_t b) { return ((uintptr_t)p & (b - 1)) == 0; };
+    const uintptr_t wb = u.w_t == CYL_F32 ? 16 : (u.w_t == CYL_U8 ? 4 : 8);
+    return !u.x16 && !u.strict16 && (n & 3) == 0 && al(u.x32, 16) && al(u.w, wb) && al(nd, 16);
 }
 
 __global__ void k_update_nd4(int64_t n4, const float4 *__restrict__ nd, UpdateArgs u)

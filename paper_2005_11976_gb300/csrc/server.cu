@@ -52,7 +52,7 @@ struct Part {
     cyl_grid grid{};
     cyl_geom geom{};
     void *d_x0 = nullptr;       // warm start, storage dtype
-    float *d_w = nullptr;       // weights or null
+    void *d_w = nullptr;        // weights (cfg.weight_dtype) or null
     float *d_wscale = nullptr;  // lambda / max(w) (or lambda)
     size_t bytes = 0;
     int64_t n_vox = 0;
@@ -317,6 +317,7 @@ int cyl_server::run_round()
         sc.upd.x16_t = cfg.storage;
         sc.upd.strict16 = 0;
         sc.upd.w = pt.d_w;
+        sc.upd.w_t = (cyl_dtype)cfg.weight_dtype;
         sc.upd.wscale = pt.d_w ? pt.d_wscale : nullptr;
         sc.upd.lambda = (float)cfg.lambda;
         sc.upd.clamp = cfg.clamp_nonneg;
@@ -462,7 +463,8 @@ extern "C" int cyl_server_create(const cyl_server_cfg *cfg, cyl_server **out)
     if (cfg->hbm_budget_bytes <= 0 || cfg->max_active < 1 || cfg->max_active > 1024 ||
         cfg->n_iter < 0 || cfg->subset_size < 1 || !std::isfinite(cfg->lambda) ||
         (cfg->weight_mode != 0 && cfg->weight_mode != 1) || cfg->storage < CYL_F32 ||
-        cfg->storage > CYL_BF16 || cfg->rounds_ahead < 0 || cfg->rounds_ahead > 64)
+        cfg->storage > CYL_BF16 || cfg->rounds_ahead < 0 || cfg->rounds_ahead > 64 ||
+        !valid_weight_dtype(cfg->weight_dtype))
         return set_error(CYL_EINVAL, "bad server configuration");
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) {
@@ -505,7 +507,7 @@ extern "C" int cyl_server_create(const cyl_server_cfg *cfg, cyl_server **out)
 }
 
 extern "C" int cyl_server_add_part(cyl_server *srv, const cyl_grid *grid, const cyl_geom *geom,
-                                   const void *x0, const float *w, int32_t *part)
+                                   const void *x0, const void *w, int32_t *part)
 {
     if (!srv || !grid || !geom || !part) return set_error(CYL_EINVAL, "null argument");
     if (geom->frames_mm) return set_error(CYL_EINVAL, "the server takes circular scans only");
@@ -529,7 +531,9 @@ extern "C" int cyl_server_add_part(cyl_server *srv, const cyl_grid *grid, const 
     pt.geom.angles_rad = nullptr;
     pt.n_vox = (int64_t)grid->n_h * grid->n_theta * grid->n_r;
     const size_t sb = dtype_size(srv->cfg.storage);
-    pt.bytes = (size_t)pt.n_vox * sb + (w ? (size_t)pt.n_vox * sizeof(float) : 0) + 2 * sizeof(float);
+    const cyl_dtype w_t = (cyl_dtype)srv->cfg.weight_dtype;
+    const size_t wb = dtype_size(w_t);
+    pt.bytes = (size_t)pt.n_vox * sb + (w ? (size_t)pt.n_vox * wb : 0) + 2 * sizeof(float);
     int prev = -1;
     cudaGetDevice(&prev);
     cudaSetDevice(srv->cfg.device);
@@ -541,14 +545,14 @@ extern "C" int cyl_server_add_part(cyl_server *srv, const cyl_grid *grid, const 
     if (srv->hbm_in_use + (int64_t)pt.bytes > srv->cfg.hbm_budget_bytes)
         return set_error(CYL_EADMIT, "part data exceeds the HBM budget");
     if (x0 && cudaMalloc(&pt.d_x0, (size_t)pt.n_vox * sb) != cudaSuccess) return set_error(CYL_ENOMEM, "warm start");
-    if (w && cudaMalloc(&pt.d_w, (size_t)pt.n_vox * sizeof(float)) != cudaSuccess) return set_error(CYL_ENOMEM, "weights");
+    if (w && cudaMalloc(&pt.d_w, (size_t)pt.n_vox * wb) != cudaSuccess) return set_error(CYL_ENOMEM, "weights");
     if (cudaMalloc(&pt.d_wscale, 2 * sizeof(float)) != cudaSuccess) return set_error(CYL_ENOMEM, "weight scale");
     if (x0 && cudaMemcpyAsync(pt.d_x0, x0, (size_t)pt.n_vox * sb, cudaMemcpyDefault, srv->st) != cudaSuccess)
         return set_error(CYL_EDEVICE, "warm start copy");
     if (w) {
-        if (cudaMemcpyAsync(pt.d_w, w, (size_t)pt.n_vox * sizeof(float), cudaMemcpyDefault, srv->st) != cudaSuccess)
+        if (cudaMemcpyAsync(pt.d_w, w, (size_t)pt.n_vox * wb, cudaMemcpyDefault, srv->st) != cudaSuccess)
             return set_error(CYL_EDEVICE, "weight copy");
-        if (launch_weight_scale(pt.d_w, pt.n_vox, srv->cfg.weight_mode, (float)srv->cfg.lambda, pt.d_wscale,
+        if (launch_weight_scale(pt.d_w, w_t, pt.n_vox, srv->cfg.weight_mode, (float)srv->cfg.lambda, pt.d_wscale,
                                 srv->st) != cudaSuccess)
             return set_error(CYL_EDEVICE, "weight scale");
     }

@@ -36,6 +36,13 @@ namespace cylct {
 constexpr float kInf = 3.0e38f;
 constexpr float kTwoPiF = 6.283185307179586f;
 
+// Weight-map elements as FP32 (Sec. 2.2 weighted back-projection): FP32, FP16, BF16, or
+// the byte values of a U8 class map.
+__device__ __forceinline__ float weight_f32(float v) { return v; }
+__device__ __forceinline__ float weight_f32(__half v) { return __half2float(v); }
+__device__ __forceinline__ float weight_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float weight_f32(uint8_t v) { return (float)v; }
+
 // FP32 ray record, computed once per plan and pose in FP64 (k_rays).
 //   a = (P*x, P*y, uref, utan)  uref: u of slab plane kref (or 0 for a ray with e_z = 0)
 //                               utan: |u| of shell boundary kstar

@@ -27,7 +27,7 @@ CYL_ENOTFOUND = -6
 CYL_EPENDING = -7
 CYL_ECANCELLED = -8
 
-CYL_F32, CYL_F16, CYL_BF16 = 0, 1, 2
+CYL_F32, CYL_F16, CYL_BF16, CYL_U8 = 0, 1, 2, 3   # CYL_U8: weight maps only
 CYL_MAX_BATCH = 4096
 CYL_MAX_DET_SIDE = 262143
 KIND_FORWARD, KIND_BACK, KIND_UPDATE = 0, 1, 2
@@ -62,7 +62,7 @@ class cyl_sart_params(ctypes.Structure):
     _fields_ = [("n_iter", ctypes.c_int32), ("subset_size", ctypes.c_int32),
                 ("lambda_", ctypes.c_double), ("clamp_nonneg", ctypes.c_int32),
                 ("weight_mode", ctypes.c_int32), ("strict_16bit", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32)]
+                ("use_graph", ctypes.c_int32), ("weight_dtype", ctypes.c_int32)]
 
 
 class cyl_server_cfg(ctypes.Structure):
@@ -70,7 +70,8 @@ class cyl_server_cfg(ctypes.Structure):
                 ("max_active", ctypes.c_int32), ("n_iter", ctypes.c_int32),
                 ("subset_size", ctypes.c_int32), ("lambda_", ctypes.c_double),
                 ("weight_mode", ctypes.c_int32), ("clamp_nonneg", ctypes.c_int32),
-                ("storage", ctypes.c_int), ("rounds_ahead", ctypes.c_int32)]
+                ("storage", ctypes.c_int), ("rounds_ahead", ctypes.c_int32),
+                ("weight_dtype", ctypes.c_int32)]
 
 
 class cyl_request(ctypes.Structure):
@@ -228,6 +229,8 @@ def dtype_code(t) -> int:
         return CYL_F16
     if "float32" in name:
         return CYL_F32
+    if "uint8" in name:
+        return CYL_U8
     raise TypeError(f"unsupported dtype {t}")
 
 
@@ -253,9 +256,9 @@ def structs_from_scan(scan):
 
 
 def sart_params(n_iter=10, subset_size=1, lam=0.5, clamp_nonneg=False, weight_mode=1,
-                strict_16bit=False, use_graph=True) -> cyl_sart_params:
+                strict_16bit=False, use_graph=True, weight_dtype=CYL_F32) -> cyl_sart_params:
     return cyl_sart_params(n_iter, subset_size, lam, int(clamp_nonneg), weight_mode,
-                           int(strict_16bit), int(use_graph))
+                           int(strict_16bit), int(use_graph), weight_dtype)
 
 
 class Plan:
@@ -469,10 +472,11 @@ class Server:
     """Owns a cyl_server; methods map one to one onto the serving entry points."""
 
     def __init__(self, hbm_budget_bytes, max_active=64, n_iter=10, subset_size=1, lam=0.5,
-                 weight_mode=1, clamp_nonneg=False, storage=CYL_F32, rounds_ahead=4, device=0):
+                 weight_mode=1, clamp_nonneg=False, storage=CYL_F32, rounds_ahead=4, device=0,
+                 weight_dtype=CYL_F32):
         lib = load()
         self.cfg = cyl_server_cfg(device, int(hbm_budget_bytes), max_active, n_iter, subset_size,
-                                  lam, weight_mode, int(clamp_nonneg), storage, rounds_ahead)
+                                  lam, weight_mode, int(clamp_nonneg), storage, rounds_ahead, weight_dtype)
         h = _VP()
         _check(lib.cyl_server_create(ctypes.byref(self.cfg), ctypes.byref(h)), "cyl_server_create")
         self.h = h

@@ -11,13 +11,27 @@ TORCH_DT = {}
 def torch_dtype(code):
     import torch
     return {cylct.CYL_F32: torch.float32, cylct.CYL_F16: torch.float16,
-            cylct.CYL_BF16: torch.bfloat16}[code]
+            cylct.CYL_BF16: torch.bfloat16, cylct.CYL_U8: torch.uint8}[code]
 
 
 def to_dev(a, code=cylct.CYL_F32):
+    """``a`` on the device in ``code`` (U8: a class map of integer values 0..255)."""
     import torch
+    if code == cylct.CYL_U8:
+        v = np.asarray(a)
+        assert np.all(v == np.rint(v)) and v.min() >= 0 and v.max() <= 255
+        return torch.from_numpy(np.ascontiguousarray(v, dtype=np.uint8)).to("cuda")
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(
         "cuda").to(torch_dtype(code)).contiguous()
+
+
+def stored(a, code):
+    """The values of ``a`` as ``code`` holds them (rounded on the host), as float64."""
+    import torch
+    if code == cylct.CYL_U8:
+        return np.asarray(a, dtype=np.uint8).astype(np.float64)
+    t = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(torch_dtype(code))
+    return t.float().numpy().astype(np.float64)
 
 
 def to_np(t):
@@ -67,14 +81,14 @@ def count_segments(plan, p0=0, np_=None):
 
 
 def sart(plan, p, x0=None, w=None, n_iter=1, x_dt=cylct.CYL_F32, sino_dt=cylct.CYL_F32,
-         **kw):
+         w_dt=cylct.CYL_F32, **kw):
     import torch
     s = plan.scan
     pd = to_dev(p, sino_dt)
     x0d = to_dev(x0, x_dt) if x0 is not None else None
-    wd = to_dev(w) if w is not None else None
+    wd = to_dev(w, w_dt) if w is not None else None
     out = torch.empty(s.vol_shape, dtype=torch_dtype(x_dt), device="cuda")
-    prm = cylct.sart_params(n_iter=n_iter, **kw)
+    prm = cylct.sart_params(n_iter=n_iter, weight_dtype=w_dt, **kw)
     plan.cyl_sart_solve(pd, sino_dt, x0d, wd, prm, out, x_dt)
     return to_np(out)
 

@@ -103,7 +103,8 @@ def test_binding_fails_loudly_without_library(tmp_path):
 
 def test_server_config_validation_without_gpu(lib):
     bad = [dict(hbm_budget_bytes=0), dict(max_active=0), dict(max_active=5000), dict(n_iter=-1),
-           dict(subset_size=0), dict(weight_mode=3), dict(storage=9), dict(rounds_ahead=99)]
+           dict(subset_size=0), dict(weight_mode=3), dict(storage=9), dict(rounds_ahead=99),
+           dict(storage=cylct.CYL_U8), dict(weight_dtype=4), dict(weight_dtype=-1)]
     for b in bad:
         cfg = dict(device=0, hbm_budget_bytes=1 << 30, max_active=8, n_iter=2, subset_size=1,
                    lambda_=0.5, weight_mode=1, clamp_nonneg=0, storage=0, rounds_ahead=4)
@@ -151,3 +152,33 @@ def test_pose_calls_validate_on_the_host(lib, orc):
         assert cylct.cyl_gamma_from_phase(*a) == pytest.approx(op.gamma_from_phase(*a), abs=1e-14)
     g = ctypes.c_double()
     assert lib.cyl_gamma_from_phase(float("nan"), 0, 0, 0, 0, ctypes.byref(g)) == cylct.CYL_EINVAL
+
+
+def test_struct_layout_matches_header(tmp_path):
+    """Every struct of the boundary has the same size and field offsets in the header (as
+    a C compiler lays it out) and in the binding."""
+    structs = {name: getattr(cylct, name) for name in (
+        "cyl_grid", "cyl_geom", "cyl_pose", "cyl_sart_params", "cyl_server_cfg", "cyl_request",
+        "cyl_result", "cyl_server_stats", "cyl_pose_params", "cyl_pose_info", "cyl_band")}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{os.path.join(ROOT, "include", "cylct.h")}"',
+             "int main(void) {"]
+    for name, st in structs.items():
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for f, _ in st._fields_:
+            c = "lambda" if f == "lambda_" else f
+            lines.append(f'printf("{name} {f} %zu\\n", offsetof({name}, {c}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-o", str(exe), str(src)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for ln in out:
+        if ln:
+            a, b, v = ln.split()
+            got[(a, b)] = int(v)
+    for name, st in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(st), name
+        for f, _ in st._fields_:
+            assert got[(name, f)] == getattr(st, f).offset, (name, f)

@@ -38,22 +38,22 @@ def inputs(s, seed):
             synth.roi_weights(s, 4.0, 7.0, 4.0, scale_to_radius=False))
 
 
-@pytest.mark.parametrize("subset", [1, 2])
-def test_batch_equals_single_and_oracle(lib, orc, subset):
+@pytest.mark.parametrize("subset,w_dt", [(1, cylct.CYL_F32), (2, cylct.CYL_F32), (1, cylct.CYL_U8)])
+def test_batch_equals_single_and_oracle(lib, orc, subset, w_dt):
     import torch
     ss = scans()
     plans = [cylct.Plan(s) for s in ss]
     data = [inputs(s, 10 + i) for i, s in enumerate(ss)]
     sinos = [gu.to_dev(d[0]) for d in data]
     x0s = [gu.to_dev(d[1]) for d in data]
-    ws = [gu.to_dev(d[2]) for d in data]
+    ws = [gu.to_dev(d[2], w_dt) for d in data]
     outs = [torch.empty(s.vol_shape, device="cuda") for s in ss]
-    prm = cylct.sart_params(n_iter=2, subset_size=subset, lam=0.5)
+    prm = cylct.sart_params(n_iter=2, subset_size=subset, lam=0.5, weight_dtype=w_dt)
     cylct.cyl_sart_solve_batch(plans, sinos, cylct.CYL_F32, x0s, ws, prm, outs, cylct.CYL_F32)
     got = [gu.to_np(o) for o in outs]
     for i, s in enumerate(ss):
         single = gu.sart(plans[i], data[i][0], x0=data[i][1], w=data[i][2], n_iter=2,
-                         subset_size=subset, lam=0.5)
+                         subset_size=subset, lam=0.5, w_dt=w_dt)
         assert gu.rel_l2(got[i], single) <= 1e-6, i
         ref = orc.sart(orc.Setup(**s.fields()), data[i][0], x0=data[i][1], w=data[i][2],
                        n_iter=2, subset_size=subset, lam=0.5)

@@ -328,6 +328,51 @@ def test_sart_weighted_warm_started_subsets(lib, orc):
         assert gu.rel_l2(eager, got) <= 1e-6
 
 
+@pytest.mark.parametrize("w_dt", [cylct.CYL_F32, cylct.CYL_F16, cylct.CYL_BF16, cylct.CYL_U8])
+def test_sart_weight_map_dtypes(lib, orc, w_dt):
+    """Weight maps of every element type (Sec. 2.2 weighted back-projection): the oracle
+    gets the values as stored.  A U8 class map holds the weights 1 and 4 exactly; the
+    16-bit maps hold non-integer weights rounded on the host.  Each through the vector
+    update (voxel count a multiple of 4, aligned arrays), the scalar update (the weight
+    map one element off its alignment) and the host-staged form."""
+    import torch
+    s = tilted_scan(n_proj=6)
+    assert s.n_vox % 4 == 0
+    rng = np.random.default_rng(23)
+    x0 = rng.uniform(0.0, 0.05, size=s.vol_shape)
+    p = rng.uniform(0.0, 1.0, size=s.sino_shape)
+    if w_dt == cylct.CYL_U8:
+        w = synth.roi_weights(s, 4.0, 7.0, 4.0, scale_to_radius=False)
+    else:
+        w = gu.stored(rng.uniform(0.5, 3.0, size=s.vol_shape), w_dt)
+    o = osetup(orc, s)
+    first = None
+    for mode in (1, 0):
+        lam = 0.5 if mode else 0.15
+        ref = orc.sart(o, p, x0=x0, w=w, n_iter=2, lam=lam, weight_mode=mode)
+        with cylct.Plan(s) as plan:
+            vec = gu.sart(plan, p, x0=x0, w=w, n_iter=2, lam=lam, weight_mode=mode, w_dt=w_dt)
+            wd = gu.to_dev(w, w_dt).ravel()
+            buf = torch.zeros(s.n_vox + 1, dtype=wd.dtype, device="cuda")
+            buf[1:] = wd
+            out = torch.empty(s.vol_shape, device="cuda")
+            prm = cylct.sart_params(n_iter=2, lam=lam, weight_mode=mode, weight_dtype=w_dt)
+            plan.cyl_sart_solve(gu.to_dev(p), cylct.CYL_F32, gu.to_dev(x0), buf[1:], prm, out, cylct.CYL_F32)
+            scalar = gu.to_np(out)
+            host = np.zeros(s.vol_shape, dtype=np.float32)
+            plan.cyl_sart_solve(np.ascontiguousarray(p, dtype=np.float32), cylct.CYL_F32,
+                                np.ascontiguousarray(x0, dtype=np.float32), wd.view(torch.uint8).cpu().numpy(),
+                                prm, host, cylct.CYL_F32)
+        for got in (vec, scalar, host):
+            assert gu.rel_l2(got, ref) <= TOL_FP32, (mode, w_dt)
+        first = vec if first is None else first
+    # an FP32 map of the same values gives the same iterate (up to the order of the
+    # back-projector's atomic sums)
+    with cylct.Plan(s) as plan:
+        f32 = gu.sart(plan, p, x0=x0, w=w, n_iter=2, lam=0.5)
+    assert gu.rel_l2(first, f32) <= 1e-6
+
+
 def test_sart_host_buffers_equal_device_buffers(lib):
     import torch
     s = tilted_scan(n_proj=4)

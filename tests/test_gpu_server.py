@@ -44,24 +44,25 @@ def stream(n, seed=3):
     return reqs
 
 
-def start(budget=8 << 30, storage=cylct.CYL_F32, **kw):
-    srv = cylct.Server(budget, n_iter=2, lam=0.5, storage=storage, **kw)
+def start(budget=8 << 30, storage=cylct.CYL_F32, weight_dtype=cylct.CYL_F32, **kw):
+    srv = cylct.Server(budget, n_iter=2, lam=0.5, storage=storage, weight_dtype=weight_dtype, **kw)
     parts = []
     for base in (PART_A, PART_B):
         x0 = np.random.default_rng(1).uniform(0.0, 0.05, size=base.vol_shape)
         w = synth.roi_weights(base, 3.0, 6.0, 4.0, scale_to_radius=False)
-        parts.append((srv.cyl_server_add_part(base, gu.to_dev(x0, storage), gu.to_dev(w)), x0, w))
+        parts.append((srv.cyl_server_add_part(base, gu.to_dev(x0, storage), gu.to_dev(w, weight_dtype)), x0, w))
     return srv, parts
 
 
-def alone(s, p, x0, w, storage=cylct.CYL_F32):
+def alone(s, p, x0, w, storage=cylct.CYL_F32, w_dt=cylct.CYL_F32):
     with cylct.Plan(s) as plan:
-        return gu.sart(plan, p, x0=x0, w=w, n_iter=2, lam=0.5, x_dt=storage, sino_dt=storage)
+        return gu.sart(plan, p, x0=x0, w=w, n_iter=2, lam=0.5, x_dt=storage, sino_dt=storage, w_dt=w_dt)
 
 
-def test_served_results_equal_solo(lib, orc):
+@pytest.mark.parametrize("w_dt", [cylct.CYL_F32, cylct.CYL_U8])
+def test_served_results_equal_solo(lib, orc, w_dt):
     import torch
-    srv, parts = start()
+    srv, parts = start(weight_dtype=w_dt)
     reqs = stream(8)
     outs, tickets = [], []
     for k, (part, s, p) in enumerate(reqs):
@@ -82,7 +83,7 @@ def test_served_results_equal_solo(lib, orc):
     assert st["completed"] == len(reqs) and st["failed"] == 0 and st["rounds"] > 0
     for k, (part, s, p) in enumerate(reqs):
         got = outs[k] if isinstance(outs[k], np.ndarray) else gu.to_np(outs[k])
-        solo = alone(s, p, parts[part][1], parts[part][2])
+        solo = alone(s, p, parts[part][1], parts[part][2], w_dt=w_dt)
         assert gu.rel_l2(got, solo) <= 1e-6, k
     # and one of them against the oracle
     part, s, p = reqs[0]
