@@ -319,8 +319,8 @@ int cyl_plan_kernel_time(cyl_plan *plan, int kind, double *ms_total, int64_t *la
 /* Work split of the projector and the back-projector: at set-up (plan creation and
  * cyl_plan_set_pose) each ray is walked once and cut into 16 pieces holding equal numbers
  * of steps; a launch runs P pieces per ray (P in 1, 2, 4, 8, 16; each piece one thread),
- * merging adjacent pieces for P < 16.  Defaults: 8 for the projector, 4 for the
- * back-projector.
+ * merging adjacent pieces for P < 16; the P pieces of a ray run in adjacent lanes of
+ * one warp.  Defaults: 8 for the projector, 2 for the back-projector.
  * cyl_plan_tune times one view (view 0) with each P and keeps the fastest for this plan;
  * synchronises `stream`.  cyl_plan_set_pieces fixes P (0 restores the default);
  * cyl_plan_get_pieces reports the P in use. */

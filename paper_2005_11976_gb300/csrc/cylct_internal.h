@@ -54,7 +54,7 @@ struct RayList {
 };
 
 constexpr int kSplit = 16;  // pieces per ray recorded at set-up (P divides it)
-constexpr int kPiecesFp = 8, kPiecesBp = 4;   // default pieces per ray of each kernel
+constexpr int kPiecesFp = 8, kPiecesBp = 2;   // default pieces per ray of each kernel
 constexpr int kSched = 8;   // ints of scheduler state per plan
 
 // SART update of one subset (Eq. 7): x += scale * w * num / den where den > 0.

@@ -430,7 +430,7 @@ def test_pieces_per_ray_do_not_change_results(lib, orc, pieces):
         got_q = gu.project(plan, x)
         got_b = gu.backproject(plan, y)
         plan.cyl_plan_set_pieces(0, 0)
-        assert plan.cyl_plan_get_pieces() == (8, 4)
+        assert plan.cyl_plan_get_pieces() == (8, 2)
     assert per_projection_rel(got_q, ref_q) <= TOL_FP32
     abs_ref = orc.backproject(o, np.abs(y))
     assert np.max(np.abs(got_b - ref_b)) <= TOL_FP32 * np.max(abs_ref)
