@@ -36,7 +36,7 @@ UNIT = "SART iters/s"
 N_ITER = 20
 # DRAM bytes (read + write) per launch of each kernel at the medium workload, from one ncu
 # capture of the current kernels (profiles/sart_medium_kernels.md).
-TRAFFIC: dict = {"k_fp": 73.27e6, "k_bp": 82.80e6, "k_update_nd4": 116.01e6}
+TRAFFIC: dict = {"k_fp": 73.27e6, "k_bp": 82.10e6, "k_update_nd4": 116.01e6}
 # DRAM bytes per scan of the corner pass on Table 1 scans (FP16), from one ncu capture of
 # 20 scans (profiles/pose_corners_table1.md); a launch's traffic scales with its scans.
 TRAFFIC_PER_SCAN: dict = {"k_corners": 2.5122e9 / 20}

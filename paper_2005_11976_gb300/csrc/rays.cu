@@ -658,9 +658,18 @@ static int log2_pieces(int P, int dflt)
     return (1 << l) == P && P <= kSplit ? l : -1;
 }
 
+// Resident 256-thread blocks per SM of the back-projectors' persistent grids.  Fewer
+// warps in flight than fit (4 by registers) measured faster, the fewer the faster: the
+// medium view's k_bp took 97.2 us at 2 blocks, 103 - 105.5 at 3, 111.7 - 113.8 at 4 and
+// 131 at 5 (forced to 48 registers); fewer reductions in flight contend less in L2.
+// k_fp is fastest with all 5 that fit (78.9 us; 83.2 at 4, 88.6 at 3).  The batched
+// back-projector (60 registers, 4 blocks fit) was measured at 3: 5.57 vs 5.41 scans/s.
+constexpr int kBpBlocksPerSm = 2, kBpBatchBlocksPerSm = 3;
+
 // Blocks of a persistent grid: every SM filled with as many 256-thread blocks of
-// `kernel` (with `smem` bytes of dynamic shared memory) as fit; looked up once.
-static unsigned persistent_blocks(const void *kernel, size_t smem)
+// `kernel` (with `smem` bytes of dynamic shared memory) as fit, at most `cap` per SM
+// (0: no cap); looked up once.
+static unsigned persistent_blocks(const void *kernel, size_t smem, int cap = 0)
 {
     static std::mutex mu;
     static std::map<std::pair<const void *, std::pair<int, size_t>>, unsigned> cache;
@@ -677,7 +686,7 @@ static unsigned persistent_blocks(const void *kernel, size_t smem)
         cudaGetLastError();
         return 152;
     }
-    const unsigned b = (unsigned)(n_sm * per_sm);
+    const unsigned b = (unsigned)(n_sm * (cap > 0 ? std::min(per_sm, cap) : per_sm));
     cache[key] = b;
     return b;
 }
@@ -793,7 +802,7 @@ cudaError_t launch_bp_rays(const ScanDev &sd, int P, int p0, int np, const void 
             using S = std::remove_pointer_t<decltype(ty)>;
             const S *yc = static_cast<const S *>(y) + (int64_t)c0 * npix;
             auto go = [&](auto kern) {
-                const unsigned blocks = persistent_blocks((const void *)kern, smem);
+                const unsigned blocks = persistent_blocks((const void *)kern, smem, kBpBlocksPerSm);
                 kern<<<blocks, 256, smem, st>>>(sd, lgP, p0 + c0, n_rays, yc, qc, nd, num, den, rl);
             };
             if (qc) {
@@ -870,7 +879,7 @@ cudaError_t launch_batch_round(const BatchScan *scans, const BatchItem *items, c
         e = dispatch_t(yt, [&](auto *ty) {
             using S = std::remove_pointer_t<decltype(ty)>;
             auto go = [&](auto kern) {
-                const unsigned blocks = persistent_blocks((const void *)kern, smem);
+                const unsigned blocks = persistent_blocks((const void *)kern, smem, kBpBatchBlocksPerSm);
                 kern<<<blocks, 256, smem, st>>>(scans, items, n_items, max_items, round, lgPb, sched);
             };
             if (lists) go(k_bp_batch<S, true>);
