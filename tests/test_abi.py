@@ -87,6 +87,12 @@ def test_host_validation_without_gpu(lib):
     assert lib.cyl_log_transform(None, 0, 1e4, None, 0, 0, None) == cylct.CYL_OK
     assert lib.cyl_log_transform(None, 7, 1e4, None, 0, 10, None) == cylct.CYL_EINVAL
     assert lib.cyl_log_transform(1, 0, -1.0, 2, 0, 10, None) == cylct.CYL_EINVAL
+    # U8 is a weight-map type only: never a sinogram or volume type
+    assert lib.cyl_log_transform(1, cylct.CYL_U8, 1e4, 2, 0, 10, None) == cylct.CYL_EINVAL
+    assert lib.cyl_log_transform(1, 0, 1e4, 2, cylct.CYL_U8, 10, None) == cylct.CYL_EINVAL
+    assert cylct.dtype_code("torch.uint8") == cylct.CYL_U8
+    prm = cylct.sart_params(weight_dtype=cylct.CYL_U8)
+    assert prm.weight_dtype == cylct.CYL_U8 and cylct.sart_params().weight_dtype == cylct.CYL_F32
     assert lib.cyl_sart_solve(None, None, 0, None, None, None, None, 0, None) == cylct.CYL_EINVAL
     assert lib.cyl_plan_destroy(None) == cylct.CYL_OK
 
