@@ -663,7 +663,8 @@ static int log2_pieces(int P, int dflt)
 // medium view's k_bp took 97.2 us at 2 blocks, 103 - 105.5 at 3, 111.7 - 113.8 at 4 and
 // 131 at 5 (forced to 48 registers); fewer reductions in flight contend less in L2.
 // k_fp is fastest with all 5 that fit (78.9 us; 83.2 at 4, 88.6 at 3).  The batched
-// back-projector (60 registers, 4 blocks fit) was measured at 3: 5.57 vs 5.41 scans/s.
+// back-projector (60 registers, 4 blocks fit) runs at 3: 5.57 vs 5.41 scans/s at 4 for
+// a 64-scan batch, and the same at 2.
 constexpr int kBpBlocksPerSm = 2, kBpBatchBlocksPerSm = 3;
 
 // Blocks of a persistent grid: every SM filled with as many 256-thread blocks of
