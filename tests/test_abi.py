@@ -118,6 +118,16 @@ def test_server_config_validation_without_gpu(lib):
         c = cylct.cyl_server_cfg(**cfg)
         h = ctypes.c_void_p()
         assert lib.cyl_server_create(ctypes.byref(c), ctypes.byref(h)) == cylct.CYL_EINVAL, b
+    # every weight-map type passes the configuration check (what follows needs a device)
+    for wt in (cylct.CYL_F32, cylct.CYL_F16, cylct.CYL_BF16, cylct.CYL_U8):
+        c = cylct.cyl_server_cfg(device=0, hbm_budget_bytes=1 << 30, max_active=8, n_iter=2, subset_size=1,
+                                 lambda_=0.5, weight_mode=1, clamp_nonneg=0, storage=0, rounds_ahead=4,
+                                 weight_dtype=wt)
+        h = ctypes.c_void_p()
+        rc = lib.cyl_server_create(ctypes.byref(c), ctypes.byref(h))
+        assert rc != cylct.CYL_EINVAL, wt
+        if rc == cylct.CYL_OK:
+            lib.cyl_server_destroy(h)
     assert lib.cyl_server_destroy(None) == cylct.CYL_OK
     assert lib.cyl_poll(None, 1, None) == cylct.CYL_EINVAL
     assert lib.cyl_sart_solve_batch(-1, None, None, 0, None, None, None, None, 0, None) == cylct.CYL_EINVAL
