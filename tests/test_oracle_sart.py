@@ -141,3 +141,93 @@ def test_voxels_no_ray_touches_stay(orc):
     x = orc.sart(o, rng.uniform(0, 1, size=s.sino_shape), x0=x0, n_iter=1, lam=0.5)
     np.testing.assert_array_equal(x[3], x0[3])
     assert np.abs(x[0] - x0[0]).max() > 0
+
+
+# ---------------------------------------------------------------- ordered subsets (Eq. 7)
+# "j in OS" of Eq. 7: one update per subset of consecutive projections, with the residual
+# sum and the column sum both taken over every ray of the subset.  The last subset holds
+# the remaining n_proj mod subset_size views.
+
+def one_voxel_scan(n_proj, det=1):
+    s = synth.Scan(1, 1, 1, 5.0, 4.0, 50.0, 100.0, det, det, 1.3, 1.1,
+                   synth.full_circle(n_proj) + 0.21, off_u=0.4, off_v=-0.3)
+    s.beta, s.tx, s.tz = 0.05, 0.6, -0.2
+    return s
+
+
+@pytest.mark.parametrize("n_proj,subset,det", [(5, 2, 1), (5, 5, 1), (7, 3, 3), (6, 4, 2)])
+def test_one_voxel_ordered_subsets_by_hand(orc, n_proj, subset, det):
+    # N = (1,1,1): every ray's only entry is its chord t_j = L_j, so the update of a subset
+    # OS is x <- x + lam * sum_{j in OS} (p_j - t_j x) / sum_{j in OS} t_j (rays with
+    # t_j = 0 add nothing to either sum).  Written out subset by subset, ragged tail
+    # included, from chords of the brute-force foot-of-perpendicular construction.
+    s = one_voxel_scan(n_proj, det)
+    S, D = bf.rays(s)
+    t = np.array([[bf.cylinder_chord(s, S[p, v, u], D[p, v, u]) for v in range(det) for u in range(det)]
+                  for p in range(n_proj)])
+    assert (t > 0).sum() >= n_proj
+    rng = np.random.default_rng(n_proj * 10 + subset)
+    p = rng.uniform(0.05, 0.4, size=(n_proj, det * det))
+    x0, lam = 0.013, 0.7
+    x = x0
+    for _ in range(2):
+        for a in range(0, n_proj, subset):
+            rows = slice(a, min(a + subset, n_proj))
+            tt, pp = t[rows].ravel(), p[rows].ravel()
+            hit = tt > 0
+            x = x + lam * (pp[hit] - tt[hit] * x).sum() / tt[hit].sum()
+    got = orc.sart(osetup(orc, s), p.reshape(s.sino_shape), x0=np.array([[[x0]]]), n_iter=2,
+                   subset_size=subset, lam=lam)
+    assert math.isclose(got.item(), x, rel_tol=1e-13)
+
+
+def test_ordered_subsets_on_bruteforce_matrix(orc):
+    # Eq. 7 over subsets of 3 consecutive views (7 views: subsets of 3, 3 and 1), weighted,
+    # on the dense matrix of the independent brute-force clip of every (ray, voxel) pair
+    s = synth.Scan(2, 5, 3, 6.0, 8.0, 40.0, 100.0, 5, 4, 2.0, 2.5, synth.full_circle(7) + 0.1)
+    s.alpha, s.beta, s.gamma, s.tx, s.ty, s.tz = 0.3, 0.12, 0.5, 0.4, -0.3, 0.2
+    A = bf.dense_matrix(s)
+    rng = np.random.default_rng(33)
+    x0 = rng.uniform(0.0, 0.05, size=s.n_vox)
+    w = rng.choice([1.0, 4.0], size=s.n_vox)
+    p = rng.uniform(0.0, 0.5, size=A.shape[0])
+    npix, lam, ss = s.det_w * s.det_h, 0.5, 3
+    L = A.sum(axis=1)
+    what = w / w.max()
+    x = x0.copy()
+    for _ in range(2):
+        for a in range(0, s.n_proj, ss):
+            rows = slice(a * npix, min(a + ss, s.n_proj) * npix)
+            As = A[rows]
+            r = np.where(L[rows] > 0, (p[rows] - As @ x) / np.where(L[rows] > 0, L[rows], 1.0), 0.0)
+            num, den = As.T @ r, As.T @ np.ones(As.shape[0])
+            upd = den > 0
+            x[upd] += lam * what[upd] * num[upd] / den[upd]
+    got = orc.sart(osetup(orc, s), p.reshape(s.sino_shape), x0=x0.reshape(s.vol_shape),
+                   w=w.reshape(s.vol_shape), n_iter=2, subset_size=ss, lam=lam)
+    np.testing.assert_allclose(got.reshape(-1), x, rtol=0, atol=1e-13)
+
+
+def test_fixed_point_with_subsets(orc):
+    s = synth.tiny_scan()
+    x_true = synth.tiny_phantom(s, synth.rng_for("tiny"))
+    o = osetup(orc, s)
+    p = orc.project(o, x_true)
+    x = orc.sart(o, p, x0=x_true, n_iter=2, subset_size=3, lam=0.5)
+    assert np.abs(x - x_true).max() <= 1e-14 * np.abs(x_true).max() * 10
+
+
+def test_resume_with_subsets(orc):
+    s = synth.tiny_scan()
+    p = synth.random_sinogram(s, synth.rng_for("tiny"))
+    o = osetup(orc, s)
+    x4 = orc.sart(o, p, n_iter=4, subset_size=3, lam=0.5)
+    x2 = orc.sart(o, p, n_iter=2, subset_size=3, lam=0.5)
+    x22 = orc.sart(o, p, x0=x2, n_iter=2, subset_size=3, lam=0.5)
+    np.testing.assert_allclose(x22, x4, rtol=0, atol=1e-15)
+    # a subset of every view is one simultaneous step, whatever the order of the views
+    perm = np.random.default_rng(2).permutation(s.n_proj)
+    sp = dataclasses.replace(s, angles=s.angles[perm])
+    a = orc.sart(o, p, n_iter=1, subset_size=s.n_proj, lam=0.5)
+    b = orc.sart(osetup(orc, sp), p[perm], n_iter=1, subset_size=s.n_proj, lam=0.5)
+    np.testing.assert_allclose(b, a, rtol=0, atol=1e-14 * np.abs(a).max())
