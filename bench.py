@@ -194,6 +194,8 @@ def main():
                     choices=["medium", "batched", "serving", "precision", "mtf", "pose", "table1", "table1_batch",
                              "phase"])
     ap.add_argument("--scans", type=int, default=0, help="batched/serving: number of scans")
+    ap.add_argument("--no-fused", action="store_true",
+                    help="two launches per subset (projector, back-projector) instead of one")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -248,6 +250,7 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
     prm = cylct.sart_params(n_iter=N_ITER, lam=LAMBDA, use_graph=bool(args.graph), weight_dtype=cylct.CYL_U8)
     plan.cyl_plan_set_timing(True)
+    plan.cyl_plan_set_fused(not args.no_fused)
 
     def step(st):
         plan.cyl_plan_set_pose(pose, st)
@@ -329,52 +332,61 @@ def main():
                "h2d_bytes_per_step": int(counts.numel() * 4),
                "d2h_bytes_per_step": int(n_vox * 4)}
 
-    # --- roofline of the dominant kernel (segment-touch algorithmic bytes)
+    # --- roofline of the dominant kernel, on the segment-touch byte model of the path's
+    # specification: forward S b_v + H W (b_s + 4); back-projection and update together
+    # S 4 + 2 V_hit b_v + V_hit b_w (V_hit = V: every voxel of the grid is crossed by some
+    # ray of a medium view).  One launch of every kernel covers one view (one subset).
     hbm, peak_kind = peaks()
-    kinds = ["forward projection (k_fp)",
-             "back-projection into (num, den) (k_bp)",
-             "SART voxel update (k_update_nd4)"]
     roof = None
-    if all(k_n):
+    if k_n[0] and k_n[2]:
         S = float(seg.sum()) / scan.n_proj           # segments per view (= per launch)
-        ray_rec = 48                                 # three float4 per ray
-        # segment-touch model per launch (one view):
-        #   forward: one volume value per segment, the ray records, the projections written,
-        #            and the spare (num, den) accumulator cleared for the next subset
-        #   back:    one 8-byte (num, den) update per segment, the ray records, y and q read
-        #   update:  (num, den), x read and written, the U8 weight class map read
-        per = [S * 4 + n_pix * (ray_rec + 4) + n_vox * 8,
-               S * 8 + n_pix * (ray_rec + 4 + 4),
-               n_vox * (8 + 4 + 4 + 1)]
-        avg_ms = [k_ms[k] / k_n[k] for k in range(3)]
+        b_v, b_s, b_w = 4, 4, 1                      # FP32 volume and data, U8 class map
+        fwd = S * b_v + n_pix * (b_s + 4)
+        back = S * 4                                 # the residual carried to every segment
+        upd = 2 * n_vox * b_v + n_vox * b_w          # x read and written, w read
+        avg_ms = [k_ms[k] / k_n[k] if k_n[k] else 0.0 for k in range(3)]
+        t_view = sum(avg_ms) / 1e3
+        if args.no_fused:
+            names = ["forward projection (k_fp)", "back-projection into (num, den) (k_bp)",
+                     "SART voxel update (k_update_nd4)"]
+            per = [fwd, back, upd]
+        else:
+            names = ["projection, residual and back-projection, one walk (k_sart)", None,
+                     "SART voxel update (k_update_nd4)"]
+            per = [fwd + back, 0.0, upd]
+        ach = [per[k] / (avg_ms[k] / 1e3) / 1e9 if k_n[k] else 0.0 for k in range(3)]
         dom = int(np.argmax(k_ms))
-        ach = [per[k] / (avg_ms[k] / 1e3) / 1e9 for k in range(3)]
+        kernel = names[dom].split("(")[-1][:-1]
+        # the builder's own per-kernel model: what the kernels move as built (48-byte ray
+        # records, the spare accumulator cleared, the packed 8-byte (num, den) reduction)
+        own = {"forward": S * 4 + n_pix * (48 + 4) + n_vox * 8,
+               "back": S * 8 + n_pix * (48 + 4 + 4),
+               "update": n_vox * (8 + 4 + 4 + 1)}
         # compulsory model: every array of a subset once (x read by the projector, read and
         # written by the update; w; p, q and the residual)
         comp = 3 * n_vox * 4 + n_vox * 1 + 3 * n_pix * 4
-        t_view = sum(avg_ms) / 1e3
-        compulsory = {"bytes_per_subset": comp, "achieved": comp / t_view / 1e9, "frac": comp / t_view / 1e9 / hbm,
-                      "unit": "GB/s", "subset_ms": t_view * 1e3}
-        # the segment-touch figures of the path's specification: forward S b_v + H W (b_s + 4);
-        # back-projection and update together S 4 + 2 V_hit b_v + V_hit b_w (V_hit = V here:
-        # every voxel of the grid is crossed by some ray of a medium view)
-        st_fp = S * 4 + n_pix * 8
-        st_bu = S * 4 + 2 * n_vox * 4 + n_vox * 1
-        t_fp, t_bu = avg_ms[0] / 1e3, (avg_ms[1] + avg_ms[2]) / 1e3
-        spec_model = {"forward": {"bytes": st_fp, "achieved": st_fp / t_fp / 1e9, "frac": st_fp / t_fp / 1e9 / hbm},
-                      "back_and_update": {"bytes": st_bu, "achieved": st_bu / t_bu / 1e9,
-                                          "frac": st_bu / t_bu / 1e9 / hbm},
-                      "unit": "GB/s"}
         roof = {"bound": "hbm", "achieved": ach[dom], "peak": hbm, "unit": "GB/s",
-                "frac": ach[dom] / hbm, "traffic": TRAFFIC.get(kinds[dom].split("(")[-1][:-1]),
-                "kernel": kinds[dom], "peak_source": peak_kind,
+                "frac": ach[dom] / hbm, "traffic": TRAFFIC.get(kernel),
+                "kernel": names[dom], "peak_source": peak_kind, "model": "segment-touch (path specification)",
                 "algorithmic_bytes_per_launch": per[dom],
                 "units_per_launch": "one view: %d rays, %.4g segments" % (n_pix, S),
-                "kernel_ms_avg": {kinds[k]: avg_ms[k] for k in range(3)},
-                "kernel_gbs": {kinds[k]: ach[k] for k in range(3)},
-                "kernel_frac": {kinds[k]: ach[k] / hbm for k in range(3)},
-                "kernel_share": {kinds[k]: k_ms[k] / sum(k_ms) for k in range(3)},
-                "segments_per_view": S, "compulsory_model": compulsory, "spec_segment_touch_model": spec_model}
+                "path_per_view": {"bytes": fwd + back + upd, "ms": t_view * 1e3,
+                                  "achieved": (fwd + back + upd) / t_view / 1e9,
+                                  "frac": (fwd + back + upd) / t_view / 1e9 / hbm},
+                "forward": {"bytes": fwd}, "back_and_update": {"bytes": back + upd},
+                "kernel_ms_avg": {names[k]: avg_ms[k] for k in range(3) if names[k]},
+                "kernel_gbs": {names[k]: ach[k] for k in range(3) if names[k]},
+                "kernel_frac": {names[k]: ach[k] / hbm for k in range(3) if names[k]},
+                "kernel_share": {names[k]: k_ms[k] / sum(k_ms) for k in range(3) if names[k]},
+                "segments_per_view": S,
+                "compulsory_model": {"bytes_per_subset": comp, "achieved": comp / t_view / 1e9,
+                                     "frac": comp / t_view / 1e9 / hbm, "unit": "GB/s"},
+                "own_model_bytes_per_view": own}
+        if args.no_fused:
+            t_fp, t_bu = avg_ms[0] / 1e3, (avg_ms[1] + avg_ms[2]) / 1e3
+            roof["forward"].update(achieved=fwd / t_fp / 1e9, frac=fwd / t_fp / 1e9 / hbm)
+            roof["back_and_update"].update(achieved=(back + upd) / t_bu / 1e9,
+                                           frac=(back + upd) / t_bu / 1e9 / hbm)
 
     # --- CPU oracle on a bounded sample, and a live parity check on that sample
     cpu = None
@@ -385,7 +397,9 @@ def main():
         oracle.build()
         view = 37
         counts_v = oracle_view_counts(scan, x_part, view)
-        dt, x1_or, o = oracle_sample(scan, x_warm, counts_v, w, view)
+        oracle_sample(scan, x_warm, counts_v, w, view)          # warm-up (pages, threads)
+        runs = [oracle_sample(scan, x_warm, counts_v, w, view) for _ in range(3)]
+        dt, x1_or = sum(r[0] for r in runs) / len(runs), runs[-1][1]
         cores = oracle.num_threads()
         oracle.set_num_threads(1)
         dt1, _, _ = oracle_sample(scan, x_warm, counts_v, w, view)
@@ -393,7 +407,8 @@ def main():
         cpu = {"value": 1.0 / (dt * scan.n_proj), "unit": UNIT, "cores": cores,
                "kind": "oracle",
                "sample": f"one SART subset (view {view} of {scan.n_proj}) of the medium workload, "
-                         f"{dt:.2f} s on {cores} threads, {dt1:.2f} s on one; scaled x{scan.n_proj}",
+                         f"{dt:.2f} s on {cores} threads (mean of 3 after a warm-up), {dt1:.2f} s on one; "
+                         f"scaled x{scan.n_proj}",
                "value_one_thread": 1.0 / (dt1 * scan.n_proj)}
         s1 = dataclasses.replace(scan, angles=scan.angles[view:view + 1])
         with cylct.Plan(s1, device=local) as p1:
@@ -409,7 +424,7 @@ def main():
 
     # per step: ray records + cuts (set_pose), log, weight max + scale, and per subset the
     # projector, the back-projector and the update
-    n_launch = args.steps * (2 + 1 + 2 + N_ITER * scan.n_proj * 3)
+    n_launch = args.steps * (2 + 1 + 2 + N_ITER * scan.n_proj * (3 if args.no_fused else 2))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -930,7 +945,7 @@ def run_pose(args):
         "metric": "pose estimates per second (axis detection by corner pixels + Levenberg-Marquardt)",
         "value": value, "unit": "scans/s", "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup),
         "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": value * 0.23, "dtype": "f16", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f16", "data": "synthetic",
         "config": {"workload": f"pose: Table 1 scans (21 projections over 200 deg, 1944x1536 at 0.0748 mm, "
                                f"SOD 679, SDD 791), {n_parts} parts x 5 stage positions, tube 64 mm x R8/R3, "
                                "Poisson I0 4e4, FP16 line integrals, threshold 0.1, dilation 2",

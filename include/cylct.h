@@ -113,6 +113,12 @@ const char *cyl_strerror(int code);
 /* Library version, e.g. "cylct 1.0". */
 const char *cyl_version(void);
 
+/* The compute capability the library's kernels were compiled for, as the runtime reports
+ * it for `device` (major * 10 + minor: 103 for a GB300 build), in *binary_version.  Errors:
+ * CYL_EINVAL (null output), CYL_EDEVICE (no such device, or the kernels have no image for
+ * it).  A diagnostic: the paper has no counterpart. */
+int cyl_binary_version(int device, int32_t *binary_version);
+
 /* Create a plan for one scan: validates the grid, geometry and pose, builds the
  * per-projection ray tables (FP64, from the pose of Eq. 1, "only the alignment matrix
  * needs to be precomputed", Sec. 2.2) on `device` and allocates the scratch of a SART
@@ -321,10 +327,21 @@ int cyl_plan_kernel_time(cyl_plan *plan, int kind, double *ms_total, int64_t *la
  * of steps; a launch runs P pieces per ray (P in 1, 2, 4, 8, 16; each piece one thread),
  * merging adjacent pieces for P < 16; the P pieces of a ray run in adjacent lanes of
  * one warp.  Defaults: 8 for the projector, 2 for the back-projector.
- * cyl_plan_tune times one view (view 0) with each P and keeps the fastest for this plan;
+ * cyl_plan_tune times one view (view 0) with each P and keeps the fastest for this plan,
+ * for the projector, the back-projector and the one-launch subset (cyl_plan_set_fused);
  * synchronises `stream`.  cyl_plan_set_pieces fixes P (0 restores the default);
  * cyl_plan_get_pieces reports the P in use. */
 int cyl_plan_tune(cyl_plan *plan, void *stream);
+/* How cyl_sart_solve runs a subset of Eq. 7.  enable = 1 (the default): one launch per
+ * subset; the lanes of each ray walk it forward for its projection (Eq. 6), form its
+ * residual, and walk it again to back-project the residual (kind 0 of
+ * cyl_plan_kernel_time; kind 1 then has no launches).  enable = 0: a projector launch and
+ * a back-projector launch (kinds 0 and 1), with the projections stored in between.  Both
+ * give the same iterates to rounding.  Errors: CYL_EINVAL (null plan). */
+int cyl_plan_set_fused(cyl_plan *plan, int32_t enable);
+/* Pieces per ray of the one-launch subset (P as for cyl_plan_set_pieces; 0 restores the
+ * default, 8).  Errors: CYL_EINVAL (null plan, P not 0 or a power of two up to 16). */
+int cyl_plan_set_sart_pieces(cyl_plan *plan, int32_t pieces);
 int cyl_plan_set_pieces(cyl_plan *plan, int32_t fp_pieces, int32_t bp_pieces);
 int cyl_plan_get_pieces(const cyl_plan *plan, int32_t *fp_pieces, int32_t *bp_pieces);
 

@@ -399,13 +399,21 @@ int orc_sart(const orc_setup *s, const double *p, const double *x0, const double
             what[m] = (weight_mode == 1) ? (wmax > 0.0 ? w[m] / wmax : 0.0) : w[m];
     }
     for (j = 0; j < npix * subset_size; ++j) ones[j] = 1.0;
+    /* The row and column sums of Eq. 7 are floored at eps (2^-16 of the grid radius, far
+     * below any voxel size): r_j = (p_j - q_j) / max(L_j, eps) and
+     * x_m += lambda w_m num_m / max(den_m, eps).  Rays and voxels met by chords of eps or
+     * more are updated exactly as in Eq. 7; a ray or voxel that is only grazed moves by a
+     * share (chord / eps)^2 of its plain update instead of by the whole residual of the ray
+     * that grazes it, however short the chord.  The paper's t_jl counts equidistant samples
+     * (Sec. 2.2), which a grazing chord does not receive. */
+    const double eps = ldexp(s->radius, -16);
     for (it = 0; it < n_iter; ++it) {
         for (p0 = 0; p0 < s->n_proj; p0 += subset_size) {
             int np = s->n_proj - p0 < subset_size ? s->n_proj - p0 : subset_size;
             long nr = npix * np;
             if (orc_project(s, x, p0, np, q) || orc_row_sums(s, p0, np, L)) { err = -1; goto done; }
             for (j = 0; j < nr; ++j)
-                res[j] = L[j] > 0.0 ? (p[(long)p0 * npix + j] - q[j]) / L[j] : 0.0;
+                res[j] = L[j] > 0.0 ? (p[(long)p0 * npix + j] - q[j]) / (L[j] > eps ? L[j] : eps) : 0.0;
             if (orc_backproject(s, res, p0, np, num) || orc_backproject(s, ones, p0, np, den)) {
                 err = -1;
                 goto done;
@@ -413,7 +421,7 @@ int orc_sart(const orc_setup *s, const double *p, const double *x0, const double
             for (m = 0; m < V; ++m) {
                 if (den[m] > 0.0) {
                     double wm = what ? what[m] : 1.0;
-                    x[m] += lambda * wm * num[m] / den[m];
+                    x[m] += lambda * wm * num[m] / (den[m] > eps ? den[m] : eps);
                     if (clamp_nonneg && x[m] < 0.0) x[m] = 0.0;
                 }
             }

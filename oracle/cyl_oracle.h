@@ -78,7 +78,9 @@ int orc_row_nnz(const orc_setup *s, int p0, int np, long *nnz);
 
 /* SART of Eq. 7.  x0 may be NULL (zeros), w may be NULL (all ones).
  * weight_mode 1: w_hat = w / max(w); 0: w_hat = w.  Subsets are runs of subset_size
- * consecutive projections in index order; one iteration is one sweep over all of them. */
+ * consecutive projections in index order; one iteration is one sweep over all of them.
+ * Row and column sums are floored at eps = 2^-16 radius in the normalisations (a grazed
+ * ray or voxel moves by (chord / eps)^2 of its plain update; see orc_sart). */
 int orc_sart(const orc_setup *s, const double *p, const double *x0, const double *w,
              int n_iter, int subset_size, double lambda, int clamp_nonneg,
              int weight_mode, double *x);

@@ -25,20 +25,6 @@ int fail(int code, const char *fmt, ...)
     return code;
 }
 
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev)
-    {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard()
-    {
-        int cur;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
-
 bool valid_dtype(int t) { return t == CYL_F32 || t == CYL_F16 || t == CYL_BF16; }
 
 int check_range(const cyl_plan *plan, int32_t p0, int32_t np)
@@ -92,6 +78,26 @@ extern "C" const char *cyl_strerror(int code)
 
 extern "C" const char *cyl_version(void) { return "cylct 1.0"; }
 
+extern "C" int cyl_binary_version(int device, int32_t *binary_version)
+{
+    if (!binary_version) return set_error(CYL_EINVAL, "binary_version is null");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return set_error(CYL_EDEVICE, "no such CUDA device");
+    }
+    DeviceGuard dg(device);
+    if (!dg.ok) return cuda_error(dg.err, "cudaSetDevice");
+    int v = 0;
+    const cudaError_t e = kernel_binary_version(&v);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_error(e, "cudaFuncGetAttributes");
+    }
+    *binary_version = v;
+    return CYL_OK;
+}
+
 extern "C" int cyl_plan_create(const cyl_grid *grid, const cyl_geom *geom, const cyl_pose *pose,
                                int device, cyl_plan **out)
 {
@@ -105,6 +111,7 @@ extern "C" int cyl_plan_create(const cyl_grid *grid, const cyl_geom *geom, const
         return set_error(CYL_EDEVICE, "no such CUDA device");
     }
     DeviceGuard dg(device);
+    if (!dg.ok) return cuda_error(dg.err, "cudaSetDevice");
     cyl_plan *pl = new (std::nothrow) cyl_plan();
     if (!pl) return set_error(CYL_ENOMEM, "host allocation failed");
     rc = pl->init(*grid, *geom, *pose, device);
@@ -122,6 +129,7 @@ extern "C" int cyl_plan_set_pose(cyl_plan *plan, const cyl_pose *pose, void *str
     int rc = validate_scan(&plan->grid, &plan->geom, pose);
     if (rc) return rc;
     DeviceGuard dg(plan->device);
+    if (!dg.ok) return cuda_error(dg.err, "cudaSetDevice");
     std::lock_guard<std::mutex> lock(plan->mu);
     cudaStream_t user = (cudaStream_t)stream;
     CYL_CUDA(cudaEventRecord(plan->ev_in, user));
@@ -136,6 +144,7 @@ extern "C" int cyl_plan_destroy(cyl_plan *plan)
 {
     if (!plan) return CYL_OK;
     DeviceGuard dg(plan->device);
+    if (!dg.ok) return cuda_error(dg.err, "cudaSetDevice");
     delete plan;
     return CYL_OK;
 }
@@ -171,28 +180,10 @@ extern "C" int cyl_row_sums(cyl_plan *plan, int32_t p0, int32_t np, float *L_out
     if (np == 0) return CYL_OK;
     if (!L_out) return set_error(CYL_EINVAL, "L_out is null");
     DeviceGuard dg(plan->device);
+    if (!dg.ok) return cuda_error(dg.err, "cudaSetDevice");
     cudaError_t e = launch_row_sums(plan->scan_dev(), p0, np, L_out, (cudaStream_t)stream, plan->ray_list());
     return e == cudaSuccess ? CYL_OK : cuda_error(e, "row sums");
 }
-
-// Plan kernels run on the plan's work stream, ordered after the caller's stream and
-// before its later work: the plan's scratch and work counters serve one launch at a time.
-namespace {
-struct OnPlanStream {
-    cyl_plan *pl;
-    cudaStream_t user;
-    cudaError_t begin()
-    {
-        cudaError_t e = cudaEventRecord(pl->ev_in, user);
-        return e == cudaSuccess ? cudaStreamWaitEvent(pl->ws, pl->ev_in, 0) : e;
-    }
-    cudaError_t end()
-    {
-        cudaError_t e = cudaEventRecord(pl->ev_out, pl->ws);
-        return e == cudaSuccess ? cudaStreamWaitEvent(user, pl->ev_out, 0) : e;
-    }
-};
-}  // namespace
 
 extern "C" int cyl_project(cyl_plan *plan, const void *vol, cyl_dtype vol_dtype, int32_t p0,
                            int32_t np, void *sino_out, cyl_dtype sino_dtype, void *stream)
@@ -203,6 +194,7 @@ extern "C" int cyl_project(cyl_plan *plan, const void *vol, cyl_dtype vol_dtype,
     if (np == 0) return CYL_OK;
     if (!vol || !sino_out) return set_error(CYL_EINVAL, "null array");
     DeviceGuard dg(plan->device);
+    if (!dg.ok) return cuda_error(dg.err, "cudaSetDevice");
     std::lock_guard<std::mutex> lock(plan->mu);
     const size_t n = (size_t)np * plan->n_pix;
     float *q = static_cast<float *>(sino_out);
@@ -230,6 +222,7 @@ extern "C" int cyl_backproject(cyl_plan *plan, const void *sino, cyl_dtype sino_
     if (!valid_dtype(sino_dtype)) return set_error(CYL_EINVAL, "bad dtype");
     if (!vol_out || (np > 0 && !sino)) return set_error(CYL_EINVAL, "null array");
     DeviceGuard dg(plan->device);
+    if (!dg.ok) return cuda_error(dg.err, "cudaSetDevice");
     std::lock_guard<std::mutex> lock(plan->mu);
     OnPlanStream ps{plan, (cudaStream_t)stream};
     CYL_CUDA(ps.begin());
@@ -249,6 +242,7 @@ extern "C" int cyl_count_segments(cyl_plan *plan, int32_t p0, int32_t np, int64_
     if (np == 0) return CYL_OK;
     if (!counts_out) return set_error(CYL_EINVAL, "counts_out is null");
     DeviceGuard dg(plan->device);
+    if (!dg.ok) return cuda_error(dg.err, "cudaSetDevice");
     std::lock_guard<std::mutex> lock(plan->mu);
     OnPlanStream ps{plan, (cudaStream_t)stream};
     CYL_CUDA(ps.begin());
@@ -259,10 +253,30 @@ extern "C" int cyl_count_segments(cyl_plan *plan, int32_t p0, int32_t np, int64_
     return CYL_OK;
 }
 
+extern "C" int cyl_plan_set_fused(cyl_plan *plan, int32_t enable)
+{
+    if (!plan) return set_error(CYL_EINVAL, "plan is null");
+    std::lock_guard<std::mutex> lock(plan->mu);
+    plan->fused = enable != 0;
+    plan->drop_graphs();
+    return CYL_OK;
+}
+
+extern "C" int cyl_plan_set_sart_pieces(cyl_plan *plan, int32_t pieces)
+{
+    if (!plan) return set_error(CYL_EINVAL, "plan is null");
+    if (pieces != 0 && !valid_pieces(pieces)) return set_error(CYL_EINVAL, "pieces must be 1, 2, 4, 8 or 16");
+    std::lock_guard<std::mutex> lock(plan->mu);
+    plan->p_sart = pieces;
+    plan->drop_graphs();
+    return CYL_OK;
+}
+
 extern "C" int cyl_plan_tune(cyl_plan *plan, void *stream)
 {
     if (!plan) return set_error(CYL_EINVAL, "plan is null");
     DeviceGuard dg(plan->device);
+    if (!dg.ok) return cuda_error(dg.err, "cudaSetDevice");
     std::lock_guard<std::mutex> lock(plan->mu);
     cudaStream_t user = (cudaStream_t)stream;
     CYL_CUDA(cudaEventRecord(plan->ev_in, user));
@@ -323,6 +337,7 @@ extern "C" int cyl_sart_solve(cyl_plan *plan, const void *sino, cyl_dtype sino_d
         return set_error(CYL_EINVAL, "weight_mode must be 0 or 1");
     if (!valid_weight_dtype(params->weight_dtype)) return set_error(CYL_EINVAL, "bad weight dtype");
     DeviceGuard dg(plan->device);
+    if (!dg.ok) return cuda_error(dg.err, "cudaSetDevice");
     std::lock_guard<std::mutex> lock(plan->mu);
     return plan->solve(sino, sino_dtype, x0, w, *params, x_out, x_dtype, (cudaStream_t)stream);
 }

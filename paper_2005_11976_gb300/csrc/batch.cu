@@ -183,6 +183,7 @@ int batch_run(int32_t n, cyl_plan *const *plans, const void *const *sinos, cyl_d
         u.wscale = w ? pl->d_wscale : nullptr;
         u.lambda = (float)prm->lambda;
         u.clamp = prm->clamp_nonneg ? 1 : 0;
+        u.den_eps = sc.sd.g.eps;
         if (w && !tune)
             BT_CUDA(launch_weight_scale(w, u.w_t, pl->n_vox, prm->weight_mode, (float)prm->lambda, pl->d_wscale,
                                         bs));

@@ -30,6 +30,7 @@ struct GridDev {
     float dr, inv_dr;       // shell spacing
     float dth, inv_dth;     // wedge angle and its inverse
     float dh, inv_dh, h0;   // slab spacing, first slab plane (-H/2)
+    float eps;              // floor of Eq. 7's row and column sums: 2^-16 radius
 };
 
 // Device tables of one scan.
@@ -55,7 +56,9 @@ struct RayList {
 
 constexpr int kSplit = 16;  // pieces per ray recorded at set-up (P divides it)
 constexpr int kPiecesFp = 8, kPiecesBp = 2;   // default pieces per ray of each kernel
-constexpr int kSched = 8;   // ints of scheduler state per plan
+constexpr int kSched = 8;   // ints of scheduler state per plan (two per ray kernel kind)
+// The one-launch SART subset (k_sart): threads per block and default pieces per ray.
+constexpr int kSartThreads = 128, kPiecesSart = 8;
 
 // SART update of one subset (Eq. 7): x += scale * w * num / den where den > 0.
 struct UpdateArgs {
@@ -68,6 +71,7 @@ struct UpdateArgs {
     const float *wscale;    // device scalar lambda / max(w) (or lambda), or null
     float lambda;
     int clamp;
+    float den_eps;          // floor of the column sums (x += s w num / max(den, den_eps))
 };
 
 // One scan of a batched solve (static for the whole solve).
@@ -122,6 +126,12 @@ cudaError_t launch_fp_rays(const ScanDev &sd, int P, int p0, int np, const void 
 cudaError_t launch_bp_rays(const ScanDev &sd, int P, int p0, int np, const void *y, cyl_dtype yt,
                            const float *q, float2 *nd, float *num, float *den, cudaStream_t st,
                            const RayList &rl = RayList{nullptr, nullptr});
+// One SART subset per launch (k_sart): the forward projection of views p0 .. p0+np-1,
+// the residuals against y, and their back-projection into nd (the spare accumulator
+// zero_buf cleared on the way).  P: pieces per ray (<= 0: kPiecesSart).
+cudaError_t launch_sart_rays(const ScanDev &sd, int P, int p0, int np, const void *x, cyl_dtype xt, const void *y,
+                             cyl_dtype yt, float2 *nd, float2 *zero_buf, int64_t zero_len, cudaStream_t st,
+                             const RayList &rl = RayList{nullptr, nullptr});
 cudaError_t launch_update_nd(int64_t n_vox, const float2 *nd, const UpdateArgs &u, cudaStream_t st);
 cudaError_t launch_count_rays(const ScanDev &sd, int p0, int np, unsigned long long *counts,
                               cudaStream_t st,
@@ -143,6 +153,8 @@ cudaError_t launch_weight_scale(const void *w, cyl_dtype w_t, int64_t n, int mod
                                 float *wscale, cudaStream_t st);
 
 size_t dtype_size(cyl_dtype t);
+// binaryVersion of the library's kernel image on the current device (e.g. 103)
+cudaError_t kernel_binary_version(int *v);
 // element types a weight map may have (sinograms and volumes: F32, F16, BF16 only)
 inline bool valid_weight_dtype(int t) { return t == CYL_F32 || t == CYL_F16 || t == CYL_BF16 || t == CYL_U8; }
 

@@ -120,6 +120,10 @@ void build_grid(const cyl_grid &grid, const cyl_geom &geom, GridDev &g, std::vec
     g.dh = (float)(grid.height_mm / grid.n_h);
     g.inv_dh = (float)(grid.n_h / grid.height_mm);
     g.h0 = (float)(-0.5 * grid.height_mm);
+    // Floor of Eq. 7's row and column sums: far below any voxel size, well above the
+    // FP32 walk's position error, so a grazed ray or voxel moves by (chord / eps)^2 of its
+    // plain update
+    g.eps = (float)ldexp(grid.radius_mm, -16);
 }
 
 void build_views(const cyl_geom &geom, const cyl_pose &pose, std::vector<ProjGeom> &geo)

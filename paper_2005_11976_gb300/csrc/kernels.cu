@@ -185,4 +185,12 @@ cudaError_t launch_weight_scale(const void *w, cyl_dtype w_t, int64_t n, int mod
     return cudaGetLastError();
 }
 
+cudaError_t kernel_binary_version(int *v)
+{
+    cudaFuncAttributes a;
+    const cudaError_t e = cudaFuncGetAttributes(&a, k_wscale);
+    if (e == cudaSuccess) *v = a.binaryVersion;
+    return e;
+}
+
 }  // namespace cylct

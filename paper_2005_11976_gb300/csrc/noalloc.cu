@@ -55,27 +55,21 @@ extern "C" int cyl_project_noalloc(cyl_plan *plan, const void *vol, cyl_dtype vo
     if (n > kNoAllocMaxElems)
         return set_error(CYL_EINVAL, "np * H * W exceeds the allocation-free buffer (4 Mi values)");
     if (plan->device < 0 || plan->device >= kMaxDevices) return set_error(CYL_EINVAL, "device index");
-    int prev = -1;
-    cudaGetDevice(&prev);
-    if (prev != plan->device) cudaSetDevice(plan->device);
-    struct Restore {
-        int d;
-        ~Restore() { if (d >= 0) cudaSetDevice(d); }
-    } restore{prev != plan->device ? prev : -1};
+    DeviceGuard dg(plan->device);
+    if (!dg.ok) return cuda_error(dg.err, "cudaSetDevice");
     float *acc = nullptr;
     int rc = acc_address(plan->device, &acc);
     if (rc) return rc;
     // the plan's kernels run on its work stream, ordered after the caller's stream
     std::lock_guard<std::mutex> lock(plan->mu);
-    cudaStream_t user = (cudaStream_t)stream, st = plan->ws;
-    cudaError_t e = cudaEventRecord(plan->ev_in, user);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, plan->ev_in, 0);
-    // the projector writes the rays of positive chord only
+    OnPlanStream ps{plan, (cudaStream_t)stream};
+    const cudaStream_t st = plan->ws;
+    cudaError_t e = ps.begin();
+    // the projector writes the rays of positive chord only: clear what the last call left
     if (e == cudaSuccess && plan->use_list) e = cudaMemsetAsync(acc, 0, sizeof(float) * n, st);
     if (e == cudaSuccess) e = launch_fp_rays(plan->scan_dev(), plan->p_fp, p0, np, vol, vol_dtype, acc, nullptr, 0, st,
                                               plan->ray_list());
     if (e == cudaSuccess) e = launch_convert(acc, CYL_F32, sino_out, sino_dtype, n, st);
-    if (e == cudaSuccess) e = cudaEventRecord(plan->ev_out, st);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(user, plan->ev_out, 0);
+    if (e == cudaSuccess) e = ps.end();
     return e == cudaSuccess ? CYL_OK : cuda_error(e, "cyl_project_noalloc");
 }

@@ -191,6 +191,7 @@ int cyl_plan::queue_sweep(const SolveState &s, cudaStream_t st, bool timed, int 
     upd.wscale = s.w ? d_wscale : nullptr;
     upd.lambda = (float)s.lambda;
     upd.clamp = s.clamp;
+    upd.den_eps = g.eps;
     // timing events captured into a graph must be external records to be timed
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     if (timed) PL_CUDA(cudaStreamIsCapturing(st, &cap));
@@ -203,9 +204,18 @@ int cyl_plan::queue_sweep(const SolveState &s, cudaStream_t st, bool timed, int 
         cudaEvent_t *ev = timed ? next_events(4) : nullptr;
         if (timed && !ev) return set_error(CYL_EDEVICE, "event creation failed");
         if (ev) PL_CUDA(cudaEventRecordWithFlags(ev[0], st, rec_flags));
-        PL_CUDA(launch_fp_rays(sd, p_fp, p0, np, s.x_proj, s.x_proj_t, d_q, d_nd[b ^ 1], n_vox, st, ray_list()));
-        if (ev) PL_CUDA(cudaEventRecordWithFlags(ev[1], st, rec_flags));
-        PL_CUDA(launch_bp_rays(sd, p_bp, p0, np, sino_p, s.sino_t, d_q, d_nd[b], nullptr, nullptr, st, ray_list()));
+        if (fused) {
+            // projection, residual and back-projection in one launch; no back-projector time
+            PL_CUDA(launch_sart_rays(sd, p_sart, p0, np, s.x_proj, s.x_proj_t, sino_p, s.sino_t, d_nd[b], d_nd[b ^ 1],
+                                     n_vox, st, ray_list()));
+            if (ev) PL_CUDA(cudaEventRecordWithFlags(ev[1], st, rec_flags));
+        } else {
+            PL_CUDA(launch_fp_rays(sd, p_fp, p0, np, s.x_proj, s.x_proj_t, d_q, d_nd[b ^ 1], n_vox, st,
+                                   ray_list()));
+            if (ev) PL_CUDA(cudaEventRecordWithFlags(ev[1], st, rec_flags));
+            PL_CUDA(launch_bp_rays(sd, p_bp, p0, np, sino_p, s.sino_t, d_q, d_nd[b], nullptr, nullptr, st,
+                                   ray_list()));
+        }
         if (ev) PL_CUDA(cudaEventRecordWithFlags(ev[2], st, rec_flags));
         PL_CUDA(launch_update_nd(n_vox, d_nd[b], upd, st));
         if (ev) PL_CUDA(cudaEventRecordWithFlags(ev[3], st, rec_flags));
@@ -360,6 +370,7 @@ int cyl_plan::solve(const void *sino, cyl_dtype sino_t, const void *x0, const vo
         }
         for (size_t base = 0; base + 4 <= ev_used; base += 4)
             for (int k = 0; k < 3; ++k) {
+                if (fused && k == 1) continue;   // no separate back-projector launch
                 float ms = 0.f;
                 PL_CUDA(cudaEventElapsedTime(&ms, events[base + k], events[base + k + 1]));
                 kernel_ms[k] += ms;
@@ -369,8 +380,8 @@ int cyl_plan::solve(const void *sino, cyl_dtype sino_t, const void *x0, const vo
     return CYL_OK;
 }
 
-// Autotuner: time the projector and the back-projector of view 0 for 1, 2, 4, 8 and 16
-// pieces per ray and keep the fastest of each (the walk's cost does not depend on the
+// Autotuner: time the projector, the back-projector and the one-launch subset of view 0
+// for 1, 2, 4, 8 and 16 pieces per ray and keep the fastest of each (the walk's cost does not depend on the
 // volume's values, so a zero volume and zero data serve).
 int cyl_plan::tune(cudaStream_t st)
 {
@@ -383,16 +394,19 @@ int cyl_plan::tune(cudaStream_t st)
     cudaEvent_t e[2];
     PL_CUDA(cudaEventCreate(&e[0]));
     PL_CUDA(cudaEventCreate(&e[1]));
-    float best_fp = 1e30f, best_bp = 1e30f;
+    float best_fp = 1e30f, best_bp = 1e30f, best_sart = 1e30f;
     for (int P = 1; P <= kSplit; P *= 2) {
-        for (int kind = 0; kind < 2; ++kind) {
+        for (int kind = 0; kind < 3; ++kind) {
             float ms_min = 1e30f;
             for (int rep = 0; rep < 3; ++rep) {
                 PL_CUDA(cudaEventRecord(e[0], st));
                 if (kind == 0)
                     PL_CUDA(launch_fp_rays(sd, P, 0, 1, d_x32, CYL_F32, d_q, nullptr, 0, st, ray_list()));
-                else
+                else if (kind == 1)
                     PL_CUDA(launch_bp_rays(sd, P, 0, 1, d_q, CYL_F32, d_q, d_nd[0], nullptr, nullptr, st, ray_list()));
+                else
+                    PL_CUDA(launch_sart_rays(sd, P, 0, 1, d_x32, CYL_F32, d_q, CYL_F32, d_nd[0], nullptr, 0, st,
+                                             ray_list()));
                 PL_CUDA(cudaEventRecord(e[1], st));
                 PL_CUDA(cudaEventSynchronize(e[1]));
                 float ms = 0.f;
@@ -401,6 +415,7 @@ int cyl_plan::tune(cudaStream_t st)
             }
             if (kind == 0 && ms_min < best_fp) { best_fp = ms_min; p_fp = P; }
             if (kind == 1 && ms_min < best_bp) { best_bp = ms_min; p_bp = P; }
+            if (kind == 2 && ms_min < best_sart) { best_sart = ms_min; p_sart = P; }
         }
     }
     cudaEventDestroy(e[0]);

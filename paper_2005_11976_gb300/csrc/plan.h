@@ -52,6 +52,45 @@ struct SolveState {
 
 }  // namespace cylct
 
+struct cyl_plan;
+
+namespace cylct {
+
+// Makes `dev` the current device for the guard's scope and restores the previous one.
+// ok is false (err the CUDA error) when the switch failed; nothing may then be queued.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    cudaError_t err = cudaSuccess;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            cudaGetLastError();
+            prev = -1;
+        }
+        if (prev != dev && (err = cudaSetDevice(dev)) != cudaSuccess) {
+            cudaGetLastError();
+            ok = false;
+        }
+    }
+    ~DeviceGuard()
+    {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// Plan kernels run on the plan's work stream, ordered after the caller's stream and
+// before its later work: the plan's scratch and work counters serve one launch at a time.
+struct OnPlanStream {
+    cyl_plan *pl;
+    cudaStream_t user;
+    cudaError_t begin();
+    cudaError_t end();
+};
+
+}  // namespace cylct
+
 struct cyl_plan {
     int device = 0;
     cyl_grid grid{};
@@ -82,6 +121,8 @@ struct cyl_plan {
     size_t q_cap = 0;
     float2 *d_nd[2] = {nullptr, nullptr};   // (numerator, column sum) accumulators, per voxel
     int p_fp = 0, p_bp = 0;        // pieces per ray of the projector / back-projector (0: default)
+    int p_sart = 0;                // pieces per ray of the fused SART kernel (0: default)
+    bool fused = true;             // SART subsets in one launch (k_sart) instead of two
     float *d_x32 = nullptr;
     size_t x32_cap = 0;
     void *d_stage[4] = {nullptr, nullptr, nullptr, nullptr};  // sino, x0, w, x_out
@@ -150,3 +191,15 @@ struct cyl_plan {
               const cyl_sart_params &prm, void *x_out, cyl_dtype x_t, cudaStream_t user);
     ~cyl_plan();
 };
+
+inline cudaError_t cylct::OnPlanStream::begin()
+{
+    cudaError_t e = cudaEventRecord(pl->ev_in, user);
+    return e == cudaSuccess ? cudaStreamWaitEvent(pl->ws, pl->ev_in, 0) : e;
+}
+
+inline cudaError_t cylct::OnPlanStream::end()
+{
+    cudaError_t e = cudaEventRecord(pl->ev_out, pl->ws);
+    return e == cudaSuccess ? cudaStreamWaitEvent(user, pl->ev_out, 0) : e;
+}

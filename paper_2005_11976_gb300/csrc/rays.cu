@@ -33,17 +33,26 @@ namespace cylct {
 
 // ------------------------------------------------------------------ piece walks
 
+// Sum of t_jl x_l over a piece, compensated (Kahan): the rounding error of each addition
+// is carried into the next, so the sum keeps FP32 accuracy over any number of segments.
+// The residual p_j - q_j of a nearly fitted ray cancels most of q_j, which would magnify
+// a plainly accumulated sum's rounding.
 template <class T>
 __device__ __forceinline__ float fp_walk(const GridDev &g, const float2 *__restrict__ trig,
                                          const RayRec &rr, float ua, float ub, const T *__restrict__ x)
 {
     Walker w;
     w.init(g, trig, rr, ua, ub);
-    float acc = 0.f;
-    auto op = [&](int idx, float len) { acc = fmaf(len, as_f32<T>(__ldg(x + idx)), acc); };
+    float acc = 0.f, comp = 0.f;
+    auto op = [&](int idx, float len) {
+        const float y = fmaf(len, as_f32<T>(__ldg(x + idx)), -comp);
+        const float t = acc + y;
+        comp = (t - acc) - y;
+        acc = t;
+    };
     while (w.step(g, trig, op)) {
     }
-    return acc;
+    return acc - comp;
 }
 
 // yv: the ray's value (residual or data); into nd, or into num / den when nd is null
@@ -84,11 +93,12 @@ __device__ __forceinline__ void bp_walk(const GridDev &g, const float2 *__restri
     }
 }
 
-// sum over the P adjacent lanes of a ray (P divides 32)
-__device__ __forceinline__ float ray_sum(float v, int P)
+// sum over the P adjacent lanes of a ray (P divides 32), in FP64
+__device__ __forceinline__ double ray_sum(float v, int P)
 {
-    for (int o = P >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+    double d = v;
+    for (int o = P >> 1; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    return d;
 }
 
 // weight of voxel m (1 without a map); the element type is uniform over a launch
@@ -136,7 +146,7 @@ __device__ __forceinline__ void update_voxel(const UpdateArgs &u, int64_t m, flo
     X *x16 = static_cast<X *>(u.x16);
     float xv = u.strict16 ? as_f32<X>(x16[m]) : u.x32[m];
     const float wm = weight_at(u, m);
-    xv = fmaf(sc * wm, v.x / v.y, xv);
+    xv = fmaf(sc * wm, v.x / fmaxf(v.y, u.den_eps), xv);
     if (u.clamp) xv = fmaxf(xv, 0.f);
     if (!u.strict16) u.x32[m] = xv;
     if (x16) x16[m] = from_f32r<X>(xv);
@@ -379,7 +389,7 @@ k_bp(ScanDev sd, int lgP, int p0, int64_t n_rays, const S *__restrict__ y, const
         float yv;
         if (SART) {
             const float L = rr.c.z;
-            yv = L > 0.f ? (as_f32<S>(y[r]) - q[r]) / L : 0.f;
+            yv = L > 0.f ? (as_f32<S>(y[r]) - q[r]) / fmaxf(L, sd.g.eps) : 0.f;
         } else {
             yv = as_f32<S>(y[r]);
             if (yv == 0.f && !den) continue;
@@ -389,12 +399,61 @@ k_bp(ScanDev sd, int lgP, int p0, int64_t n_rays, const S *__restrict__ y, const
     retire(sched);
 }
 
+// One SART subset in one launch (Eq. 7).  A warp task holds 32 / P rays, the P pieces
+// of a ray in P adjacent lanes.  Each lane walks its piece forward, adding t_jl x_l; the
+// P lanes sum q_j and form the residual r_j = (p_j - q_j) / L_j; each lane then walks its
+// piece again, back-projecting r_j into the packed (numerator, column sum) accumulator.
+// One launch instead of a projector and a back-projector: the projections never go to
+// memory, and the gathers of some warps overlap the reductions of others.  The spare
+// accumulator is cleared on the way, as in k_fp.
+template <class T, class S, bool LIST>
+__global__ void __launch_bounds__(kSartThreads)
+k_sart(ScanDev sd, int lgP, int p0, int64_t n_rays, const T *__restrict__ x, const S *__restrict__ y, float2 *nd,
+       float2 *zero_buf, int64_t zero_len, RayList rl)
+{
+    extern __shared__ float2 s_trig[];
+    stage_trig_smem(sd.trig, sd.g.n_t, s_trig);
+    zero_slice(zero_buf, zero_len, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+               (int64_t)gridDim.x * blockDim.x);
+    const int P = 1 << lgP, lane = threadIdx.x & 31;
+    const int64_t npix = (int64_t)sd.g.det_w * sd.g.det_h, base = (int64_t)p0 * npix;
+    int64_t a0, n_task;
+    launch_tasks<LIST>(rl, p0, npix, n_rays, a0, n_task);
+    const int64_t n_wt = ((n_task << lgP) + 31) >> 5, span = task_span(n_wt);
+    int *sched = sd.sched + 6;
+    for (;;) {
+        const int f = fetch_task(sched);
+        if (f >= span) break;
+        const int64_t wt = task_of(f, n_wt);
+        if (wt < 0) continue;
+        const int64_t t = wt * 32 + lane, i = t >> lgP;
+        const int piece = (int)(t & (P - 1));
+        float acc = 0.f, ua = 0.f, ub = 0.f;
+        int64_t r = -1, rec = 0;
+        bool have = false;
+        if (i < n_task) {
+            r = LIST ? (int64_t)__ldg(rl.act + a0 + i) - base : i;
+            rec = LIST ? a0 + i : base + r;
+            const RayRec rr = ray_at(sd, rec);
+            have = piece_bounds(rr, sd.split + rec * kSplit, piece, P, ua, ub);
+            if (have) acc = fp_walk<T>(sd.g, s_trig, rr, ua, ub, x);
+        }
+        const double q = ray_sum(acc, P);
+        if (!have) continue;
+        const RayRec rr = ray_at(sd, rec);
+        const float L = rr.c.z;
+        const float yv = L > 0.f ? (float)(((double)as_f32<S>(y[r]) - q) / fmaxf(L, sd.g.eps)) : 0.f;
+        bp_walk(sd.g, s_trig, rr, ua, ub, yv, nd, nullptr, nullptr);
+    }
+    retire(sched);
+}
+
 // The FP32 iterate without a 16-bit copy: four voxels per thread, 16-byte loads and
 // stores (the same arithmetic as update_voxel; voxels with den = 0 keep their value).
-__device__ __forceinline__ float upd1(float x, float num, float den, float w, float sc, int clamp)
+__device__ __forceinline__ float upd1(float x, float num, float den, float w, float sc, int clamp, float eps)
 {
     if (!(den > 0.f)) return x;
-    x = fmaf(sc * w, num / den, x);
+    x = fmaf(sc * w, num / fmaxf(den, eps), x);
     return clamp ? fmaxf(x, 0.f) : x;
 }
 
@@ -405,10 +464,10 @@ __device__ __forceinline__ void update4(const UpdateArgs &u, const float4 *__res
     const float4 a = __ldg(nd + 2 * i), b = __ldg(nd + 2 * i + 1);
     const float4 wv = weight4_at(u, i);
     float4 xv = x[i];
-    xv.x = upd1(xv.x, a.x, a.y, wv.x, sc, u.clamp);
-    xv.y = upd1(xv.y, a.z, a.w, wv.y, sc, u.clamp);
-    xv.z = upd1(xv.z, b.x, b.y, wv.z, sc, u.clamp);
-    xv.w = upd1(xv.w, b.z, b.w, wv.w, sc, u.clamp);
+    xv.x = upd1(xv.x, a.x, a.y, wv.x, sc, u.clamp, u.den_eps);
+    xv.y = upd1(xv.y, a.z, a.w, wv.y, sc, u.clamp, u.den_eps);
+    xv.z = upd1(xv.z, b.x, b.y, wv.z, sc, u.clamp, u.den_eps);
+    xv.w = upd1(xv.w, b.z, b.w, wv.w, sc, u.clamp, u.den_eps);
     x[i] = xv;
 }
 
@@ -600,7 +659,7 @@ k_bp_batch(const BatchScan *__restrict__ scans, const BatchItem *__restrict__ it
         if (!piece_bounds(rr, sc.sd.split + rec * kSplit, piece, P, ua, ub)) continue;
         const float L = rr.c.z;
         const S *y = static_cast<const S *>(sc.sino) + base;
-        const float yv = L > 0.f ? (as_f32<S>(y[r]) - sc.q[it.buf][r]) / L : 0.f;
+        const float yv = L > 0.f ? (as_f32<S>(y[r]) - sc.q[it.buf][r]) / fmaxf(L, sc.sd.g.eps) : 0.f;
         bp_walk(sc.sd.g, sc.sd.trig, rr, ua, ub, yv, sc.nd[it.buf], nullptr, nullptr);
     }
     retire(sched + 2);
@@ -670,19 +729,19 @@ constexpr int kBpBlocksPerSm = 2, kBpBatchBlocksPerSm = 3;
 // Blocks of a persistent grid: every SM filled with as many 256-thread blocks of
 // `kernel` (with `smem` bytes of dynamic shared memory) as fit, at most `cap` per SM
 // (0: no cap); looked up once.
-static unsigned persistent_blocks(const void *kernel, size_t smem, int cap = 0)
+static unsigned persistent_blocks(const void *kernel, size_t smem, int cap = 0, int threads = 256)
 {
     static std::mutex mu;
     static std::map<std::pair<const void *, std::pair<int, size_t>>, unsigned> cache;
     int dev = 0;
     cudaGetDevice(&dev);
-    const auto key = std::make_pair(kernel, std::make_pair(dev, smem));
+    const auto key = std::make_pair(kernel, std::make_pair(dev * 4096 + threads, smem));
     std::lock_guard<std::mutex> lk(mu);
     auto it = cache.find(key);
     if (it != cache.end()) return it->second;
     int n_sm = 0, per_sm = 0;
     if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess ||
         n_sm < 1 || per_sm < 1) {
         cudaGetLastError();
         return 152;
@@ -814,6 +873,40 @@ cudaError_t launch_bp_rays(const ScanDev &sd, int P, int p0, int np, const void 
                 else go(k_bp<S, false, false>);
             }
             return cudaGetLastError();
+        });
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_sart_rays(const ScanDev &sd, int P, int p0, int np, const void *x, cyl_dtype xt, const void *y,
+                             cyl_dtype yt, float2 *nd, float2 *zero_buf, int64_t zero_len, cudaStream_t st,
+                             const RayList &rl)
+{
+    if (np <= 0) return cudaSuccess;
+    const int lgP = log2_pieces(P, kPiecesSart);
+    if (lgP < 0) return cudaErrorInvalidValue;
+    const int64_t npix = (int64_t)sd.g.det_w * sd.g.det_h;
+    const size_t smem = trig_smem(sd.g.n_t);
+    const int vmax = views_per_launch(sd);
+    for (int c0 = 0; c0 < np; c0 += vmax) {
+        const int cn = std::min(vmax, np - c0);
+        const int64_t n_rays = (int64_t)cn * npix;
+        float2 *zb = c0 == 0 ? zero_buf : nullptr;
+        const int64_t zl = c0 == 0 ? zero_len : 0;
+        const cudaError_t e = dispatch_t(xt, [&](auto *tx) {
+            using T = std::remove_pointer_t<decltype(tx)>;
+            return dispatch_t(yt, [&](auto *ty) {
+                using S = std::remove_pointer_t<decltype(ty)>;
+                const S *yc = static_cast<const S *>(y) + (int64_t)c0 * npix;
+                auto go = [&](auto kern) {
+                    const unsigned blocks = persistent_blocks((const void *)kern, smem, 0, kSartThreads);
+                    kern<<<blocks, kSartThreads, smem, st>>>(sd, lgP, p0 + c0, n_rays, (const T *)x, yc, nd, zb, zl,
+                                                             rl);
+                    return cudaGetLastError();
+                };
+                return rl.act ? go(k_sart<T, S, true>) : go(k_sart<T, S, false>);
+            });
         });
         if (e != cudaSuccess) return e;
     }

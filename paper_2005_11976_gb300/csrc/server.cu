@@ -320,6 +320,7 @@ int cyl_server::run_round()
         sc.upd.w_t = (cyl_dtype)cfg.weight_dtype;
         sc.upd.wscale = pt.d_w ? pt.d_wscale : nullptr;
         sc.upd.lambda = (float)cfg.lambda;
+        sc.upd.den_eps = sc.sd.g.eps;
         sc.upd.clamp = cfg.clamp_nonneg;
         items.push_back(BatchItem{(int)scans.size(), p0, std::min(subset, s->req.n_proj - p0), r & 1});
         scans.push_back(sc);

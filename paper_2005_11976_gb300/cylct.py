@@ -127,6 +127,9 @@ SIGNATURES = {
                                          _I64, _VP]),
     "cyl_row_sums": (ctypes.c_int, [_VP, _I32, _I32, _VP, _VP]),
     "cyl_project": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _I32, _I32, _VP, ctypes.c_int, _VP]),
+    "cyl_plan_set_fused": (ctypes.c_int, [_VP, _I32]),
+    "cyl_plan_set_sart_pieces": (ctypes.c_int, [_VP, _I32]),
+    "cyl_binary_version": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_I32)]),
     "cyl_project_noalloc": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _I32, _I32, _VP, ctypes.c_int, _VP]),
     "cyl_backproject": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _I32, _I32, _VP, _VP, _VP]),
     "cyl_sart_solve": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP,
@@ -336,6 +339,12 @@ class Plan:
 
     def cyl_plan_set_pieces(self, fp: int = 0, bp: int = 0):
         _check(load().cyl_plan_set_pieces(self.h, int(fp), int(bp)), "cyl_plan_set_pieces")
+
+    def cyl_plan_set_fused(self, enable: bool):
+        _check(load().cyl_plan_set_fused(self.h, int(bool(enable))), "cyl_plan_set_fused")
+
+    def cyl_plan_set_sart_pieces(self, pieces: int = 0):
+        _check(load().cyl_plan_set_sart_pieces(self.h, int(pieces)), "cyl_plan_set_sart_pieces")
 
     def cyl_plan_set_timing(self, enable: bool):
         _check(load().cyl_plan_set_timing(self.h, int(enable)), "cyl_plan_set_timing")

@@ -43,10 +43,21 @@ def test_every_declared_symbol_is_exported(lib):
     assert not [n for n in declared_functions() if n not in cylct.SIGNATURES]
 
 
-def test_built_for_sm_103a(lib):
-    out = subprocess.run(["cuobjdump", "--list-elf", cylct.LIB_PATH], capture_output=True,
-                         text=True).stdout
-    assert "sm_103a" in out
+def test_build_targets_sm_103a_only():
+    from paper_2005_11976_gb300 import build
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+@pytest.mark.gpu
+def test_kernels_run_as_sm_103_binaries(lib):
+    # the runtime's view of the loaded kernel image: compiled for compute capability 10.3
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    v = cylct._I32()
+    assert lib.cyl_binary_version(0, ctypes.byref(v)) == cylct.CYL_OK, lib.cyl_last_error_detail()
+    assert v.value == 103
+    assert lib.cyl_binary_version(0, None) == cylct.CYL_EINVAL
 
 
 def test_host_validation_without_gpu(lib):

@@ -472,6 +472,55 @@ def test_medium_single_view_projection_and_subset(lib, orc):
     assert gu.rel_l2(got, ref) <= TOL_FP32
 
 
+@pytest.mark.parametrize("fused", [True, False])
+def test_medium_two_sweeps_per_iterate(lib, orc, fused):
+    # the medium workload at full size (grid (128, 512, 128), 256^2 detector, its pose,
+    # warm start, ROI weights and Poisson data) on 8 of its 180 views, so that the oracle
+    # finishes in seconds: both sweeps and both increments against the FP64 oracle
+    full = synth.medium_scan(synth.rng_for("medium"))
+    s = dataclasses.replace(full, angles=full.angles[::23][:8])
+    az = synth.insert_azimuths(synth.rng_for("medium"))
+    x0 = gu.stored(synth.part_phantom(s, az), cylct.CYL_F32)      # the values the GPU holds
+    o = osetup(orc, s)
+    p_clean = orc.project(o, synth.part_phantom(s, az, removed=5))
+    p = gu.stored(orc.log_transform(synth.poisson_counts(p_clean, 1.0e4, np.random.default_rng(8)), 1.0e4),
+                  cylct.CYL_F32)
+    w = synth.roi_weights(s)
+    ref1 = orc.sart(o, p, x0=x0, w=w, n_iter=1, lam=0.5)
+    ref2 = orc.sart(o, p, x0=ref1, w=w, n_iter=1, lam=0.5)
+    with cylct.Plan(s) as plan:
+        plan.cyl_plan_set_fused(fused)
+        got1 = gu.sart(plan, p, x0=x0, w=w, n_iter=1, lam=0.5)
+        got2 = gu.sart(plan, p, x0=x0, w=w, n_iter=2, lam=0.5)
+    assert gu.rel_l2(got1, ref1) <= TOL_FP32
+    assert gu.rel_l2(got2, ref2) <= TOL_FP32
+    # Each sweep changes x by a few per cent of it; the FP32 iterate and the FP32 crossing
+    # positions round at 1e-7 of x, so the increments themselves hold to a few 1e-5
+    # (2.1e-5 measured for the first sweep, 7.5e-7 for the iterate).
+    assert gu.rel_l2(got1 - x0, ref1 - x0) <= TOL_FP32 * 5
+    assert gu.rel_l2(got2 - ref1, ref2 - ref1) <= TOL_FP32 * 10
+
+
+def test_fused_and_two_launch_subsets_agree(lib, orc):
+    # one launch per subset (walk once, replay the recorded segments) and two launches
+    # (walk twice) give the same iterates to rounding, with subsets of 3 views, a compact
+    # plan included
+    rng = np.random.default_rng(12)
+    for s in (tilted_scan(),
+              dataclasses.replace(synth.Scan(5, 16, 6, 6.0, 10.0, 60.0, 240.0, 28, 24, 1.6, 1.6,
+                                             synth.full_circle(7) + 0.2), alpha=0.2, beta=0.1,
+                                  gamma=0.3, tx=14.0, ty=7.0)):
+        x0 = rng.uniform(0.0, 0.05, size=s.vol_shape)
+        p = rng.uniform(0.0, 1.0, size=s.sino_shape)
+        with cylct.Plan(s) as plan:
+            a = gu.sart(plan, p, x0=x0, n_iter=2, lam=0.5, subset_size=3)
+            plan.cyl_plan_set_fused(False)
+            b = gu.sart(plan, p, x0=x0, n_iter=2, lam=0.5, subset_size=3)
+        assert gu.rel_l2(a, b) <= 1e-6
+        ref = orc.sart(osetup(orc, s), p, x0=x0, n_iter=2, lam=0.5, subset_size=3)
+        assert gu.rel_l2(a, ref) <= TOL_FP32
+
+
 @pytest.mark.parametrize("vol_dt", [cylct.CYL_F16, cylct.CYL_BF16])
 def test_precision_size_single_view_projection(lib, orc, vol_dt):
     # full precision-variant grid (256, 1024, 256) and 512^2 detector, volume stored in
@@ -512,3 +561,18 @@ def test_general_trajectory_frames(lib, orc):
         got = gu.sart(plan, ref_q, n_iter=2, lam=0.5)
     assert gu.rel_l2(got, orc.sart(o, ref_q, n_iter=2, lam=0.5)) <= TOL_FP32
 
+
+
+@pytest.mark.parametrize("ratio", [0.5, 4.0])
+def test_grazing_ray_and_voxel_floor_on_gpu(lib, orc, ratio):
+    # a ray that grazes the one-voxel grid over eps / 2 or 4 eps (eps = 2^-16 R, the floor
+    # of Eq. 7's row and column sums): the update equals the oracle's
+    from test_oracle_sart import GRAZE_EPS, graze_scan
+    s, t = graze_scan(ratio * GRAZE_EPS)
+    x0, p = np.array([[[0.02]]]), np.array([[[3e-5]]])
+    ref = orc.sart(osetup(orc, s), p, x0=x0, n_iter=1, lam=0.6)
+    with cylct.Plan(s) as plan:
+        for fused in (True, False):
+            plan.cyl_plan_set_fused(fused)
+            got = gu.sart(plan, p, x0=x0, n_iter=1, lam=0.6)
+            assert abs(got.item() - ref.item()) <= 2e-3 * abs(ref.item() - 0.02)

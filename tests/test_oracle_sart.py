@@ -231,3 +231,45 @@ def test_resume_with_subsets(orc):
     a = orc.sart(o, p, n_iter=1, subset_size=s.n_proj, lam=0.5)
     b = orc.sart(osetup(orc, sp), p[perm], n_iter=1, subset_size=s.n_proj, lam=0.5)
     np.testing.assert_allclose(b, a, rtol=0, atol=1e-14 * np.abs(a).max())
+
+
+# ------------------------------------------------------- grazing rays and voxels (Eq. 7)
+
+GRAZE_R = 5.0
+GRAZE_EPS = math.ldexp(GRAZE_R, -16)
+
+
+def graze_scan(chord):
+    """One pixel, one view, a one-voxel grid of radius 5 mm: the ray's offset on the
+    detector bisected (on the brute-force chord) until its chord in the grid is ``chord``."""
+    def scan_at(off):
+        return synth.Scan(1, 1, 1, GRAZE_R, 4.0, 50.0, 100.0, 1, 1, 1.0, 1.0, np.array([0.0]), off_u=off)
+
+    def chord_at(off):
+        s = scan_at(off)
+        S, D = bf.rays(s)
+        return bf.cylinder_chord(s, S[0, 0, 0], D[0, 0, 0])
+
+    lo, hi = 0.0, 20.0            # chord(lo) = 2R, chord(hi) = 0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if chord_at(mid) > chord:
+            lo = mid
+        else:
+            hi = mid
+    s = scan_at(lo)
+    return s, chord_at(lo)
+
+
+@pytest.mark.parametrize("ratio", [0.5, 4.0])
+def test_grazing_ray_and_voxel_floor(orc, ratio):
+    # Eq. 7 with its row and column sums floored at eps = 2^-16 R: a chord t >= eps moves
+    # the voxel by lam (p - t x0) / t as usual; a grazing chord t < eps by
+    # lam (t / eps)^2 (p - t x0) / t
+    s, t = graze_scan(ratio * GRAZE_EPS)
+    assert abs(t - ratio * GRAZE_EPS) <= 1e-3 * ratio * GRAZE_EPS
+    x0, p, lam = 0.02, 3e-5, 0.6
+    x = orc.sart(osetup(orc, s), np.array([p]), x0=np.array([x0]), n_iter=1, lam=lam).item()
+    share = min(t / GRAZE_EPS, 1.0) ** 2
+    # a grazing chord is ill-conditioned in FP64 too (R^2 - d^2 cancels): 1e-3
+    assert math.isclose(x - x0, lam * share * (p - t * x0) / t, rel_tol=1e-3)
