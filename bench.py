@@ -35,8 +35,9 @@ METRIC = "SART iters/sec and GRays/s at stated rel err; batched-serve vs plain s
 UNIT = "SART iters/s"
 N_ITER = 20
 # DRAM bytes (read + write) per launch of each kernel at the medium workload, from one ncu
-# capture of the current kernels (profiles/sart_medium_kernels.md).
-TRAFFIC: dict = {"k_fp": 73.27e6, "k_bp": 82.10e6, "k_update_nd4": 116.01e6}
+# capture of the current kernels (profiles/sart_medium_kernels.md; k_fp and k_bp, the
+# two-launch form, from an earlier capture of the same walks).
+TRAFFIC: dict = {"k_sart": 183.69e6, "k_update_nd4": 115.70e6, "k_fp": 73.27e6, "k_bp": 82.10e6}
 # DRAM bytes per scan of the corner pass on Table 1 scans (FP16), from one ncu capture of
 # 20 scans (profiles/pose_corners_table1.md); a launch's traffic scales with its scans.
 TRAFFIC_PER_SCAN: dict = {"k_corners": 2.5122e9 / 20}
@@ -194,6 +195,8 @@ def main():
                     choices=["medium", "batched", "serving", "precision", "mtf", "pose", "table1", "table1_batch",
                              "phase"])
     ap.add_argument("--scans", type=int, default=0, help="batched/serving: number of scans")
+    ap.add_argument("--no-batch-serve", action="store_true",
+                    help="skip the bounded batched-vs-plain and served-vs-plain comparisons")
     ap.add_argument("--no-fused", action="store_true",
                     help="two launches per subset (projector, back-projector) instead of one")
     args = ap.parse_args()
@@ -310,12 +313,12 @@ def main():
     if not args.no_e2e:
         h_counts = counts.cpu().pin_memory()
         h_out = torch.empty(scan.vol_shape, dtype=torch.float32).pin_memory()
-        d_counts = torch.empty_like(counts)
 
         def e2e_step(st):
-            d_counts.copy_(h_counts, non_blocking=True)
+            # every transfer through the C ABI: the log transform reads the pinned host counts
+            # (device-addressable), the solve writes its result to the pinned host volume
             plan.cyl_plan_set_pose(pose, st)
-            cylct.cyl_log_transform(d_counts, cylct.CYL_F32, I0, p, cylct.CYL_F32,
+            cylct.cyl_log_transform(h_counts, cylct.CYL_F32, I0, p, cylct.CYL_F32,
                                     counts.numel(), st)
             plan.cyl_sart_solve(p, cylct.CYL_F32, x0, wd, prm, h_out, cylct.CYL_F32, st)
 
@@ -422,6 +425,17 @@ def main():
             xg = xg.cpu().numpy().astype(np.float64)
         parity = float(np.linalg.norm(xg - x1_or) / np.linalg.norm(x1_or))
 
+    # --- the metric's second half on the same GPU, bounded: batched vs plain scans/s, and
+    # served vs plain scans/s with p50 / p99 latency on a stream the GPU sustains
+    batched = serving = None
+    if rank == 0 and world == 1 and not args.no_batch_serve:
+        plan.cyl_plan_set_timing(False)
+        batched = batched_compare(torch, cylct, 16)
+        # at the configured 20 scans/s the GPU saturates (throughput); at 3 scans/s it keeps up
+        # and the queue stays short (latency); the large part type is left to --workload serving
+        serving = {"saturated": serving_compare(torch, cylct, 24, 20.0, 60.0, ("small", "medium")),
+                   "sustained": serving_compare(torch, cylct, 24, 3.0, 60.0, ("small", "medium"))}
+
     # per step: ray records + cuts (set_pose), log, weight max + scale, and per subset the
     # projector, the back-projector and the update
     n_launch = args.steps * (2 + 1 + 2 + N_ITER * scan.n_proj * (3 if args.no_fused else 2))
@@ -438,6 +452,7 @@ def main():
         "rel_err_bound": "<=1e-5 rel L2 per projection and per iterate (tests)",
         "wall_s_timed": t_wall, "clocks": clk, "gpu_launches": n_launch,
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+        "batched_vs_plain": batched, "serving_vs_plain": serving,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -490,12 +505,10 @@ def _sinogram(torch, cylct, plan, scan, x_part, i0, seed, dtype):
     return out
 
 
-def run_batched(args):
-    """64 scans of one part type (own pose, N_p in {60, 90, 120, 180}) reconstructed by one
-    batched graph launch vs one cyl_sart_solve per scan, 10 sweeps each, FP32."""
-    torch, cylct = _gpu_setup()
+def batched_compare(torch, cylct, n):
+    """n scans of one part type (own pose, N_p in {60, 90, 120, 180}): one batched graph
+    launch vs one cyl_sart_solve per scan, 10 sweeps each, FP32.  Returns the figures."""
     from paper_2005_11976_gb300 import synth
-    n = args.scans or 64
     scans = synth.batched_scans(n)
     rng = synth.rng_for("batched", 1000)
     x_warm, x_part = _part_data(scans[0], rng)
@@ -518,8 +531,6 @@ def run_batched(args):
     plans[0].cyl_sart_solve(sinos[0], cylct.CYL_F32, x0, wd, cylct.sart_params(n_iter=1, lam=LAMBDA, weight_dtype=cylct.CYL_U8),
                             outs_p[0], cylct.CYL_F32)
     torch.cuda.synchronize()
-    clocks = ClockSampler(0)
-    clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     cylct.cyl_sart_solve_batch(plans, sinos, cylct.CYL_F32, [x0] * n, [wd] * n, prm, outs_b,
@@ -533,27 +544,39 @@ def run_batched(args):
     e1.record()
     e1.synchronize()
     t_plain = e0.elapsed_time(e1) / 1e3
-    clk = clocks.stop()
     err = max(float((outs_b[i] - outs_p[i]).norm() / outs_p[i].norm()) for i in range(n))
     views = sum(s.n_proj for s in scans)
-    line = {
-        "metric": METRIC, "value": n / t_batch, "unit": "scans/s", "n_gpus": 1, "steps": 1,
-        "warmup": 1, "ms_per_step": t_batch * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"batched: {n} scans of one part, grid (128,512,128), 256x256 det, "
-                               f"N_p in {{60,90,120,180}} ({views} views), |T|<=5 mm, tilt<=3 deg, "
-                               "10 sweeps, shared warm start, ROI weights",
-                   "launch": "one CUDA graph (batched) vs one cyl_sart_solve graph per scan (plain)"},
-        "pieces_per_ray_tuned": {"projector": pieces[0], "back_projector": pieces[1]},
-        "plain_scans_per_s": n / t_plain, "batched_over_plain": t_plain / t_batch,
-        "max_rel_err_batched_vs_plain": err,
-        "sart_iters_per_s_batched": n * 10 / t_batch,
-        "grays_per_s_batched": 2 * 10 * views * scans[0].det_w * scans[0].det_h / t_batch / 1e9,
-        "clocks": clk,
-    }
-    print(json.dumps(line), flush=True)
     for p in plans:
         p.close()
+    return {"scans": n, "views": views, "batched_scans_per_s": n / t_batch, "plain_scans_per_s": n / t_plain,
+            "batched_over_plain": t_plain / t_batch, "max_rel_err_batched_vs_plain": err,
+            "batched_s": t_batch, "plain_s": t_plain,
+            "pieces_per_ray_tuned": {"projector": pieces[0], "back_projector": pieces[1]},
+            "sart_iters_per_s_batched": n * 10 / t_batch,
+            "grays_per_s_batched": 2 * 10 * views * scans[0].det_w * scans[0].det_h / t_batch / 1e9,
+            "workload": f"{n} scans of one part, grid (128,512,128), 256x256 det, N_p in {{60,90,120,180}} "
+                        f"({views} views), |T|<=5 mm, tilt<=3 deg, 10 sweeps, shared warm start, ROI weights "
+                        "(U8 class map), FP32; one CUDA graph (batched) vs one cyl_sart_solve graph per scan (plain)"}
+
+
+def run_batched(args):
+    """64 scans of one part type (own pose, N_p in {60, 90, 120, 180}) reconstructed by one
+    batched graph launch vs one cyl_sart_solve per scan, 10 sweeps each, FP32."""
+    torch, cylct = _gpu_setup()
+    n = args.scans or 64
+    clocks = ClockSampler(0)
+    clocks.start()
+    r = batched_compare(torch, cylct, n)
+    clk = clocks.stop()
+    line = {
+        "metric": METRIC, "value": r["batched_scans_per_s"], "unit": "scans/s", "n_gpus": 1, "steps": 1,
+        "warmup": 1, "ms_per_step": r["batched_s"] * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "batched: " + r["workload"]},
+        "clocks": clk,
+    }
+    line.update({k: v for k, v in r.items() if k not in ("workload", "batched_s")})
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -955,26 +978,25 @@ def run_pose(args):
         "precision_std_over_stage_positions": prec, "accuracy_vs_truth": acc,
         "clocks": clk, "gpu_launches": 2 * args.steps,
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+        "batched_vs_plain": batched, "serving_vs_plain": serving,
     }
     print(json.dumps(line), flush=True)
     return 0
 
 
-def run_serving(args):
-    """Poisson arrivals (20 scans/s) of the three part types through the server
-    (continuous batching, BF16 storage, 150 GB budget) vs the same scans solved one at a
-    time in arrival order."""
-    torch, cylct = _gpu_setup()
+def serving_compare(torch, cylct, n, rate, duration_s, part_types):
+    """The first n arrivals of a Poisson stream (``rate`` scans/s) of the given part types
+    through the server (continuous batching, BF16 storage, 150 GB budget) vs the same scans
+    solved one at a time in arrival order.  Returns the figures."""
     from paper_2005_11976_gb300 import synth
-    n = args.scans or 48
-    stream = [r for r in synth.serving_stream(20.0, 600.0)][:n]
+    stream = [r for r in synth.serving_stream(rate, duration_s, part_types=part_types)][:n]
     dev = torch.device("cuda")
     bf16 = cylct.CYL_BF16
     parts = {}
-    for pt in ("small", "medium", "large"):
+    for pt in part_types:
         cfgp = synth.SERVING_PART_TYPES[pt]
         base = synth.medium_scan(n_proj=1, grid=cfgp["grid"], det=cfgp["det"], pitch=204.8 / cfgp["det"])
-        rng = synth.rng_for("serving", 500 + len(parts))
+        rng = synth.rng_for("serving", 500 + ("small", "medium", "large").index(pt))
         az = synth.insert_azimuths(rng)
         parts[pt] = (base, synth.part_phantom(base, az), az, synth.roi_weights(base))
     # inputs of every request (projected on the GPU before the timed run)
@@ -999,8 +1021,6 @@ def run_serving(args):
         keep += [x0, wd]
         pid[pt] = srv.cyl_server_add_part(base, x0, wd)
     outs = [torch.empty(s.vol_shape, dtype=torch.bfloat16, device=dev) for _, _, s, _ in reqs]
-    clocks = ClockSampler(0)
-    clocks.start()
     t0 = time.perf_counter()
     tickets = []
     for k, (t_arr, pt, s, sino) in enumerate(reqs):
@@ -1032,7 +1052,6 @@ def run_serving(args):
             torch.cuda.synchronize()
             svc.append(time.perf_counter() - a)
         outs_p.append(out)
-    clk = clocks.stop()
     arr = [r[0] - reqs[0][0] for r in reqs]
     free = 0.0
     lat_p = []
@@ -1043,19 +1062,37 @@ def run_serving(args):
     err = max(float((outs[i].float() - outs_p[i].float()).norm() / outs_p[i].float().norm())
               for i in range(len(reqs)))
     pct = lambda v, q: float(np.percentile(np.array(v), q))
+    return {"scans": len(reqs), "arrival_rate_per_s": rate, "served_scans_per_s": len(reqs) / t_served,
+            "served_s": t_served, "p50_latency_s": pct(lat, 50), "p99_latency_s": pct(lat, 99),
+            "plain_scans_per_s": len(reqs) / free, "plain_p50_latency_s": pct(lat_p, 50),
+            "plain_p99_latency_s": pct(lat_p, 99), "served_over_plain": free / t_served,
+            "max_rel_err_served_vs_plain": err, "rounds": rounds,
+            "part_mix": {pt: sum(1 for r in reqs if r[1] == pt) for pt in part_types},
+            "workload": f"first {len(reqs)} arrivals of a Poisson stream at {rate:g} scans/s, part types "
+                        + ", ".join(f"{synth.SERVING_PART_TYPES[pt]['grid']}/{synth.SERVING_PART_TYPES[pt]['det']}^2"
+                                    for pt in part_types)
+                        + ", N_p in {60..360}, 10% with a removed insert, 10 sweeps, BF16 storage, 150 GB budget; "
+                          "plain: the same scans one cyl_sart_solve at a time in arrival order (FIFO)"}
+
+
+def run_serving(args):
+    """Poisson arrivals (20 scans/s) of the three part types through the server
+    (continuous batching, BF16 storage, 150 GB budget) vs the same scans solved one at a
+    time in arrival order."""
+    torch, cylct = _gpu_setup()
+    n = args.scans or 48
+    clocks = ClockSampler(0)
+    clocks.start()
+    r = serving_compare(torch, cylct, n, 20.0, 600.0, ("small", "medium", "large"))
+    clk = clocks.stop()
     line = {
-        "metric": METRIC, "value": len(reqs) / t_served, "unit": "scans/s", "n_gpus": 1, "steps": 1,
-        "warmup": 0, "ms_per_step": t_served * 1e3, "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC, "value": r["served_scans_per_s"], "unit": "scans/s", "n_gpus": 1, "steps": 1,
+        "warmup": 0, "ms_per_step": r["served_s"] * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-        "config": {"workload": f"serving: first {len(reqs)} arrivals of a Poisson stream at 20 scans/s, part "
-                               "types (64,256,64)/128^2, (128,512,128)/256^2 and (256,1024,256)/512^2, N_p in "
-                               "{60..360}, 10% with a removed insert, 10 sweeps, BF16 storage, 150 GB budget"},
-        "part_mix": {pt: sum(1 for r in reqs if r[1] == pt) for pt in ("small", "medium", "large")},
-        "p50_latency_s": pct(lat, 50), "p99_latency_s": pct(lat, 99),
-        "plain_scans_per_s": len(reqs) / free, "plain_p50_latency_s": pct(lat_p, 50),
-        "plain_p99_latency_s": pct(lat_p, 99), "served_over_plain": free / t_served,
-        "max_rel_err_served_vs_plain": err, "rounds": rounds, "clocks": clk,
+        "config": {"workload": "serving: " + r["workload"]},
+        "clocks": clk,
     }
+    line.update({k: v for k, v in r.items() if k not in ("workload", "served_s")})
     print(json.dumps(line), flush=True)
     return 0
 

@@ -136,9 +136,10 @@ int cyl_plan_destroy(cyl_plan *plan);
  * CYL_EDEVICE. */
 int cyl_plan_set_pose(cyl_plan *plan, const cyl_pose *pose, void *stream);
 
-/* Eq. 6, left side: p = -ln(max(I, 1) / I0) for n detector values.  counts: device
- * array of `in` type; p_out: device array of `out` type; n >= 0.  In-place (counts ==
- * p_out, same dtype) is allowed. */
+/* Eq. 6, left side: p = -ln(max(I, 1) / I0) for n detector values.  counts: array of
+ * `in` type; p_out: array of `out` type; n >= 0.  Both are device memory or pinned
+ * (page-locked) host memory, which the kernel reads or writes directly.  In-place
+ * (counts == p_out, same dtype) is allowed. */
 int cyl_log_transform(const void *counts, cyl_dtype in, double i0, void *p_out,
                       cyl_dtype out, int64_t n, void *stream);
 

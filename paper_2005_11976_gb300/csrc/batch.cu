@@ -212,22 +212,26 @@ int batch_run(int32_t n, cyl_plan *const *plans, const void *const *sinos, cyl_d
         // projector and update types: the 16-bit iterate in strict mode, else FP32
         const bool strict = x_dtype != CYL_F32 && prm->strict_16bit;
         const cyl_dtype xt = strict ? x_dtype : CYL_F32, x16t = xt;
-        const int Pf = plans[0]->p_fp, Pb = plans[0]->p_bp;
+        // one launch per round for projection and back-projection when the first plan runs
+        // its subsets so (cyl_plan_set_fused), with its pieces per ray
+        const bool fused = plans[0]->fused;
+        const int Pf = fused ? plans[0]->p_sart : plans[0]->p_fp, Pb = plans[0]->p_bp;
+        const int round_parts = fused ? (kRoundFused | kRoundUpdate) : kRoundAll;
         if (tune) {
             cudaEvent_t e[2];
             BT_CUDA(cudaEventCreate(&e[0]));
             BT_CUDA(cudaEventCreate(&e[1]));
-            float best[2] = {1e30f, 1e30f};
-            int pick[2] = {0, 0};
+            float best[3] = {1e30f, 1e30f, 1e30f};
+            int pick[3] = {0, 0, 0};
+            const int tparts[3] = {kRoundFp, kRoundBp, kRoundFused};
             cudaError_t ce = cudaSuccess;
-            for (int part = 0; part < 2 && ce == cudaSuccess; ++part)
+            for (int part = 0; part < 3 && ce == cudaSuccess; ++part)
                 for (int P = 1; P <= kSplit && ce == cudaSuccess; P *= 2)
                     for (int rep = 0; rep < 3 && ce == cudaSuccess; ++rep) {
                         ce = cudaEventRecord(e[0], bs);
                         if (ce == cudaSuccess)
-                            ce = launch_batch_round(d_scans, d_items, d_n, n, 0, max_vox, P, P,
-                                                    part ? kRoundBp : kRoundFp, d_sched, xt, sino_dtype, x16t, bs,
-                                                    lists);
+                            ce = launch_batch_round(d_scans, d_items, d_n, n, 0, max_vox, P, P, tparts[part], d_sched,
+                                                    xt, sino_dtype, x16t, bs, lists);
                         if (ce == cudaSuccess) ce = cudaEventRecord(e[1], bs);
                         if (ce == cudaSuccess) ce = cudaEventSynchronize(e[1]);
                         float ms = 0.f;
@@ -242,6 +246,7 @@ int batch_run(int32_t n, cyl_plan *const *plans, const void *const *sinos, cyl_d
             if (ce != cudaSuccess) return cuda_error(ce, "batch autotuner");
             plans[0]->p_fp = pick[0];
             plans[0]->p_bp = pick[1];
+            plans[0]->p_sart = pick[2];
             plans[0]->drop_graphs();
         } else if (prm->use_graph) {
             cudaGraph_t graph = nullptr;
@@ -249,7 +254,7 @@ int batch_run(int32_t n, cyl_plan *const *plans, const void *const *sinos, cyl_d
             BT_CUDA(cudaStreamBeginCapture(bs, cudaStreamCaptureModeThreadLocal));
             cudaError_t ce = cudaSuccess;
             for (int r = 0; r < rounds && ce == cudaSuccess; ++r)
-                ce = launch_batch_round(d_scans, d_items, d_n, n, r, max_vox, Pf, Pb, kRoundAll, d_sched,
+                ce = launch_batch_round(d_scans, d_items, d_n, n, r, max_vox, Pf, Pb, round_parts, d_sched,
                                         xt, sino_dtype, x16t, bs, lists);
             cudaError_t ee = cudaStreamEndCapture(bs, &graph);
             if (ce != cudaSuccess) {
@@ -265,7 +270,7 @@ int batch_run(int32_t n, cyl_plan *const *plans, const void *const *sinos, cyl_d
             if (ce != cudaSuccess) return cuda_error(ce, "cudaGraphLaunch");
         } else {
             for (int r = 0; r < rounds; ++r)
-                BT_CUDA(launch_batch_round(d_scans, d_items, d_n, n, r, max_vox, Pf, Pb, kRoundAll, d_sched,
+                BT_CUDA(launch_batch_round(d_scans, d_items, d_n, n, r, max_vox, Pf, Pb, round_parts, d_sched,
                                            xt, sino_dtype, x16t, bs, lists));
         }
         BT_CUDA(cudaFreeAsync(d_blob, bs));

@@ -137,10 +137,11 @@ cudaError_t launch_count_rays(const ScanDev &sd, int p0, int np, unsigned long l
                               cudaStream_t st,
                               const RayList &rl = RayList{nullptr, nullptr});
 // One round of a batched solve: forward projection, back-projection and update of every
-// item of the round (the kernels selected by `parts`).  Pf, Pb: pieces per ray of the
-// two kernels (<= 0: their defaults).  sched: the batch's scheduler state (kSched ints,
-// zero at rest).
-constexpr int kRoundFp = 1, kRoundBp = 2, kRoundUpdate = 4, kRoundAll = 7;
+// item of the round (the kernels selected by `parts`; kRoundFused: projection, residual
+// and back-projection in one launch with Pf pieces per ray).  Pf, Pb: pieces per ray of
+// the two kernels (<= 0: their defaults).  sched: the batch's scheduler state (kSched
+// ints, zero at rest).
+constexpr int kRoundFp = 1, kRoundBp = 2, kRoundUpdate = 4, kRoundAll = 7, kRoundFused = 8;
 cudaError_t launch_batch_round(const BatchScan *scans, const BatchItem *items, const int *n_items,
                                int max_items, int round, int64_t max_vox, int Pf, int Pb, int parts,
                                int *sched, cyl_dtype xt, cyl_dtype yt, cyl_dtype x16t, cudaStream_t st,

@@ -665,6 +665,58 @@ k_bp_batch(const BatchScan *__restrict__ scans, const BatchItem *__restrict__ it
     retire(sched + 2);
 }
 
+// One round of a batched solve in one launch per the single-scan k_sart: the round's
+// items' rays as ray-major warp tasks, each ray walked forward, its residual formed from
+// the lanes' FP64 sum, and walked again to back-project it.
+template <class T, class S, bool LIST>
+__global__ void __launch_bounds__(256)
+k_sart_batch(const BatchScan *__restrict__ scans, const BatchItem *__restrict__ items,
+             const int *__restrict__ n_items, int max_items, int round, int lgP, int *sched)
+{
+    extern __shared__ int s_pre[];
+    const int n = n_items[round];
+    const BatchItem *its = items + (int64_t)round * max_items;
+    const int total = round_prefix<false, LIST>(scans, its, n, lgP, s_pre);
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
+    for (int k = 0; k < n; ++k) {   // spare accumulators of every item's scan
+        const BatchScan &sc = scans[its[k].scan];
+        zero_slice(sc.nd[its[k].buf ^ 1], sc.nd_len, tid, nth);
+    }
+    const int P = 1 << lgP, lane = threadIdx.x & 31;
+    for (;;) {
+        const int wt = fetch_task(sched + 6);
+        if (wt >= total) break;
+        const int k = item_of(s_pre, n, wt);
+        const BatchItem it = its[k];
+        const BatchScan &sc = scans[it.scan];
+        const int64_t npix = (int64_t)sc.sd.g.det_w * sc.sd.g.det_h;
+        const int64_t base = it.p0 * npix;
+        int64_t a0;
+        const int64_t n_task = item_rays<LIST>(sc, it, a0);
+        const int64_t t = (int64_t)(wt - s_pre[k]) * 32 + lane, i = t >> lgP;
+        const int piece = (int)(t & (P - 1));
+        float acc = 0.f, ua = 0.f, ub = 0.f;
+        int64_t r = -1, rec = 0;
+        bool have = false;
+        if (i < n_task) {
+            const bool listed = LIST && sc.rl.act;
+            r = listed ? (int64_t)__ldg(sc.rl.act + a0 + i) - base : i;
+            rec = listed ? a0 + i : base + r;
+            const RayRec rr = ray_at(sc.sd, rec);
+            have = piece_bounds(rr, sc.sd.split + rec * kSplit, piece, P, ua, ub);
+            if (have) acc = fp_walk<T>(sc.sd.g, sc.sd.trig, rr, ua, ub, static_cast<const T *>(sc.x_proj));
+        }
+        const double q = ray_sum(acc, P);
+        if (!have) continue;
+        const RayRec rr = ray_at(sc.sd, rec);
+        const float L = rr.c.z;
+        const S *y = static_cast<const S *>(sc.sino) + base;
+        const float yv = L > 0.f ? (float)(((double)as_f32<S>(y[r]) - q) / fmaxf(L, sc.sd.g.eps)) : 0.f;
+        bp_walk(sc.sd.g, sc.sd.trig, rr, ua, ub, yv, sc.nd[it.buf], nullptr, nullptr);
+    }
+    retire(sched + 6);
+}
+
 template <class X>
 __global__ void k_update_batch(const BatchScan *__restrict__ scans, const BatchItem *__restrict__ items,
                                const int *__restrict__ n_items, int max_items, int round)
@@ -967,6 +1019,21 @@ cudaError_t launch_batch_round(const BatchScan *scans, const BatchItem *items, c
             if (lists) go(k_fp_batch<T, true>);
             else go(k_fp_batch<T, false>);
             return cudaGetLastError();
+        });
+    if (e != cudaSuccess) return e;
+    if (parts & kRoundFused)
+        e = dispatch_t(xt, [&](auto *tx) {
+            using T = std::remove_pointer_t<decltype(tx)>;
+            return dispatch_t(yt, [&](auto *ty) {
+                using S = std::remove_pointer_t<decltype(ty)>;
+                auto go = [&](auto kern) {
+                    const unsigned blocks = persistent_blocks((const void *)kern, smem);
+                    kern<<<blocks, 256, smem, st>>>(scans, items, n_items, max_items, round, lgPf, sched);
+                };
+                if (lists) go(k_sart_batch<T, S, true>);
+                else go(k_sart_batch<T, S, false>);
+                return cudaGetLastError();
+            });
         });
     if (e != cudaSuccess) return e;
     if (parts & kRoundBp)

@@ -291,6 +291,7 @@ int cyl_server::run_round()
     std::vector<BatchItem> items;
     std::vector<std::shared_ptr<Scan>> members;
     int Pf = 0, Pb = 0, have_p = 0;
+    bool fused = true;    // the round in one launch (as the first member's plan runs its subsets)
     bool lists = false;   // some member takes its tasks from its list of rays
     int64_t max_vox = 0;
     for (auto &s : active) {
@@ -327,7 +328,8 @@ int cyl_server::run_round()
         members.push_back(s);
         max_vox = std::max(max_vox, pl->n_vox);
         if (!have_p) {
-            Pf = pl->p_fp;
+            fused = pl->fused;
+            Pf = fused ? pl->p_sart : pl->p_fp;
             Pb = pl->p_bp;
             have_p = 1;
         }
@@ -349,7 +351,8 @@ int cyl_server::run_round()
     if (cudaEventRecord(slot_ev[slot], st) != cudaSuccess) return set_error(CYL_EDEVICE, "event");
     cudaError_t e = launch_batch_round(reinterpret_cast<BatchScan *>(d), reinterpret_cast<BatchItem *>(d + b_scans),
                                        reinterpret_cast<int *>(d + b_scans + b_items), n, 0, max_vox, Pf, Pb,
-                                       kRoundAll, d_sched, CYL_F32, cfg.storage, CYL_F32, st, lists);
+                                       fused ? (kRoundFused | kRoundUpdate) : kRoundAll, d_sched, CYL_F32,
+                                       cfg.storage, CYL_F32, st, lists);
     if (e != cudaSuccess) return cuda_error(e, "round launch");
     ++stats.rounds;
     for (auto &s : members) {

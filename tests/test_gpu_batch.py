@@ -62,7 +62,9 @@ def test_batch_equals_single_and_oracle(lib, orc, subset, w_dt):
         p.close()
 
 
-def test_batch_16bit_and_eager(lib):
+def test_batch_16bit_and_eager(lib, orc):
+    # batched with BF16 storage: against each scan's own solve, and against the FP64 oracle
+    # fed the same BF16 sinogram (the reduced-precision bound, 2e-3)
     import torch
     ss = scans()
     plans = [cylct.Plan(s) for s in ss]
@@ -72,9 +74,12 @@ def test_batch_16bit_and_eager(lib):
     prm = cylct.sart_params(n_iter=2, lam=0.5, use_graph=False)
     cylct.cyl_sart_solve_batch(plans, sinos, cylct.CYL_BF16, None, None, prm, outs, cylct.CYL_BF16)
     for i, s in enumerate(ss):
-        single = gu.sart(plans[i], gu.to_np(sinos[i]), n_iter=2, lam=0.5, x_dt=cylct.CYL_BF16,
-                         sino_dt=cylct.CYL_BF16)
-        assert gu.rel_l2(gu.to_np(outs[i]), single) <= 1e-2 / 4, i   # a few BF16 ulps
+        p16 = gu.stored(data[i][0], cylct.CYL_BF16)
+        got = gu.to_np(outs[i])
+        single = gu.sart(plans[i], p16, n_iter=2, lam=0.5, x_dt=cylct.CYL_BF16, sino_dt=cylct.CYL_BF16)
+        assert gu.rel_l2(got, single) <= 1e-2 / 4, i   # a few BF16 ulps
+        ref = orc.sart(orc.Setup(**s.fields()), p16, n_iter=2, lam=0.5)
+        assert gu.rel_l2(got, ref) <= 2e-3, i
     for p in plans:
         p.close()
 

@@ -121,7 +121,9 @@ def test_errors(lib):
     srv.close()
 
 
-def test_bf16_storage(lib):
+def test_bf16_storage(lib, orc):
+    # served with BF16 storage: against the scan solved alone, and against the FP64 oracle
+    # fed the same BF16 sinogram and warm start (the reduced-precision bound, 2e-3)
     import torch
     srv, parts = start(storage=cylct.CYL_BF16)
     reqs = stream(4, seed=5)
@@ -132,9 +134,13 @@ def test_bf16_storage(lib):
     for t in tickets:
         assert srv.cyl_wait(t, 120000)[0] == cylct.CYL_OK
     for k, (part, s, p) in enumerate(reqs):
-        x0 = gu.to_np(gu.to_dev(parts[part][1], cylct.CYL_BF16))
-        solo = alone(s, gu.to_np(sinos[k]), x0, parts[part][2], cylct.CYL_BF16)
-        assert gu.rel_l2(gu.to_np(outs[k]), solo) <= 2.5e-3, k
+        x0 = gu.stored(parts[part][1], cylct.CYL_BF16)
+        p16 = gu.stored(p, cylct.CYL_BF16)
+        got = gu.to_np(outs[k])
+        solo = alone(s, p16, x0, parts[part][2], cylct.CYL_BF16)
+        assert gu.rel_l2(got, solo) <= 2.5e-3, k
+        ref = orc.sart(orc.Setup(**s.fields()), p16, x0=x0, w=parts[part][2], n_iter=2, lam=0.5)
+        assert gu.rel_l2(got, ref) <= 2e-3, k
     srv.close()
 
 
