@@ -3,10 +3,10 @@
 A single scan does not shard: the subsets of Eq. 7 are applied one after the other and
 each touches the whole volume, so splitting a scan over GPUs would need an exchange of
 partial ray sums after every subset.  Scans are independent, so N GPUs run N replicas of
-the path, each on its own scans (round-robin shards of a batch), with no collective on
-the data path: the ranks meet only at the barriers around a timed region and in one
-max-reduction of their elapsed times, and the whole-job rate is the units of all ranks
-over the slowest rank's time.
+the path, each on its own scans (round-robin shards of a batch or of a serving stream),
+with no collective on the data path: the ranks meet at the barriers around a timed region,
+in one max-reduction of their elapsed times (the whole-job rate is the units of all ranks
+over the slowest rank's time), and in one gather of per-scan results to rank 0 after it.
 """
 from __future__ import annotations
 
@@ -60,3 +60,24 @@ def whole_job_rate(units_per_rank: float, world: int, max_seconds: float) -> flo
     if max_seconds <= 0.0:
         raise ValueError("max_seconds must be > 0")
     return units_per_rank * world / max_seconds
+
+
+def gather_ordered(values, n_items: int, rank: int, world: int):
+    """All ranks' per-scan results on rank 0, in global scan order: ``values`` are this
+    rank's results for its shard(n_items, rank, world), in that order.  Rank 0 receives the
+    list of n_items results, other ranks None; one process gets its own list back."""
+    import torch.distributed as dist
+    values = list(values)
+    if len(values) != len(shard(n_items, rank, world)):
+        raise ValueError("one result per scan of the rank's shard")
+    if world == 1 or not (dist.is_available() and dist.is_initialized()):
+        return values
+    parts = [None] * world if rank == 0 else None
+    dist.gather_object(values, parts, dst=0)
+    if rank != 0:
+        return None
+    out = [None] * n_items
+    for r, part in enumerate(parts):
+        for i, v in zip(shard(n_items, r, world), part):
+            out[i] = v
+    return out

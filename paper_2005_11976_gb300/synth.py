@@ -331,6 +331,99 @@ def part_phantom(scan: Scan, azimuths: np.ndarray, removed: int = -1,
     return x
 
 
+# --------------------------------------------------------- analytic line integrals
+
+PART_SHELL_MU = (0.05, 0.04, 0.03, 0.02, 0.01)
+
+
+def _object_rays(scan: Scan, p: int):
+    """Source (3,) and pixel centres (H*W, 3) of projection p in the part's frame:
+    X' = R (X - T), R = (Rz(alpha) Rx(beta) Rz(gamma))^T, from the scan's stage frames."""
+    f = (scan.frames if scan.frames is not None else frames_from_circular(scan))[p]
+    ca, sa = math.cos(scan.alpha), math.sin(scan.alpha)
+    cb, sb = math.cos(scan.beta), math.sin(scan.beta)
+    cg, sg = math.cos(scan.gamma), math.sin(scan.gamma)
+    rz = lambda c, s_: np.array([[c, -s_, 0.0], [s_, c, 0.0], [0.0, 0.0, 1.0]])
+    rx = np.array([[1.0, 0.0, 0.0], [0.0, cb, -sb], [0.0, sb, cb]])
+    R = (rz(ca, sa) @ rx @ rz(cg, sg)).T
+    T = np.array([scan.tx, scan.ty, scan.tz])
+    iu, iv = np.meshgrid(np.arange(scan.det_w), np.arange(scan.det_h))
+    pts = f[3:6] + iu.reshape(-1, 1) * f[6:9] + iv.reshape(-1, 1) * f[9:12]
+    return R @ (f[0:3] - T), (pts - T) @ R.T
+
+
+def _cap(lo1, hi1, lo2, hi2):
+    return np.maximum(lo1, lo2), np.minimum(hi1, hi2)
+
+
+def _disk_span(S, d, cx, cy, rad):
+    """Parameter interval [lo, hi] of the lines S + t d (t along each row of d) inside the
+    infinite cylinder of radius rad about the z' axis through (cx, cy); empty: lo >= hi."""
+    ox, oy = S[0] - cx, S[1] - cy
+    a = d[:, 0] ** 2 + d[:, 1] ** 2
+    b = ox * d[:, 0] + oy * d[:, 1]
+    c = ox * ox + oy * oy - rad * rad
+    disc = b * b - a * c
+    ok = (disc > 0.0) & (a > 0.0)
+    sq = np.sqrt(np.where(ok, disc, 0.0))
+    aa = np.where(ok, a, 1.0)
+    lo = np.where(ok, (-b - sq) / aa, np.inf)
+    hi = np.where(ok, (-b + sq) / aa, -np.inf)
+    inside = (a == 0.0) & (c <= 0.0)          # parallel to the axis, inside the disk
+    return np.where(inside, -np.inf, lo), np.where(inside, np.inf, hi)
+
+
+def _slab_span(S, d, h_a, h_b):
+    dz = d[:, 2]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        t1, t2 = (h_a - S[2]) / dz, (h_b - S[2]) / dz
+    par = dz == 0.0
+    inside = (S[2] >= h_a) & (S[2] <= h_b)
+    lo = np.where(par, -np.inf if inside else np.inf, np.minimum(t1, t2))
+    hi = np.where(par, np.inf if inside else -np.inf, np.maximum(t1, t2))
+    return lo, hi
+
+
+def part_line_integrals(scan: Scan, azimuths: np.ndarray, removed: int = -1, insert_mu: float = 0.10):
+    """Line integrals through the continuous part of part_phantom() (five equal shells over
+    the full height, r = 0.08 R inserts centred at 0.6 R over h in [-H/4, H/4] replacing the
+    shell material they occupy; insert ``removed`` left out) for every ray of the scan, in
+    the sinogram's layout [N_p][H][W]: the measured data of the part, not a projection of
+    its voxelisation.  Each shape is a clipped cylinder, so each line integral is a sum of
+    chord lengths times attenuations."""
+    R, H = scan.radius, scan.height
+    out = np.zeros(scan.sino_shape)
+    rs = [k * R / 5.0 for k in range(6)]
+    for p in range(scan.n_proj):
+        S, D = _object_rays(scan, p)
+        d = D - S
+        norm = np.linalg.norm(d, axis=1)
+        s_lo, s_hi = _cap(*_slab_span(S, d, -0.5 * H, 0.5 * H), 0.0, 1.0)
+        i_lo, i_hi = _cap(*_slab_span(S, d, -0.25 * H, 0.25 * H), 0.0, 1.0)
+        # chord of each shell disk within the grid's height
+        disk = []
+        for r_ in rs:
+            lo, hi = _cap(*_disk_span(S, d, 0.0, 0.0, r_), s_lo, s_hi) if r_ > 0 else (np.zeros(len(d)), np.zeros(len(d)))
+            disk.append((lo, hi))
+        val = np.zeros(len(d))
+        for k, mu in enumerate(PART_SHELL_MU):
+            val += mu * (np.clip(disk[k + 1][1] - disk[k + 1][0], 0.0, None)
+                         - np.clip(disk[k][1] - disk[k][0], 0.0, None))
+        for i, phi in enumerate(azimuths):
+            if i == removed:
+                continue
+            lo, hi = _cap(*_disk_span(S, d, 0.6 * R * math.cos(phi), 0.6 * R * math.sin(phi), 0.08 * R), i_lo, i_hi)
+            # split the insert's chord by the shells it crosses: each part replaces its shell
+            inner = np.zeros(len(d))              # its chord inside the previous shell disk
+            for k, mu in enumerate(PART_SHELL_MU):
+                a_lo, a_hi = _cap(lo, hi, *disk[k + 1])
+                upto = np.clip(a_hi - a_lo, 0.0, None)
+                val += (insert_mu - mu) * (upto - inner)
+                inner = upto
+        out[p] = (val * norm).reshape(scan.det_h, scan.det_w)
+    return out
+
+
 def pinned_tube(scan: Scan, r_in: float = 3.0, pin_r: float = 0.8, pin_c: float = 5.5,
                 pin_az: float = 0.0, pin_h=(-16.0, 16.0), mu_wall: float = 0.05,
                 mu_pin: float = 0.3) -> np.ndarray:

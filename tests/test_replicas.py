@@ -61,3 +61,44 @@ def test_two_ranks_meet_only_in_the_timing_reduction():
     assert [r[1] for r in res] == [[0, 2, 4, 6, 8], [1, 3, 5, 7, 9]]
     assert all(r[2] == pytest.approx(2.5) for r in res)   # the slowest rank's time
     assert all(r[3] == pytest.approx(5 * 2 / 2.5) for r in res)
+
+
+def _batch_rank(rank, world, port, out):
+    # a batch of 7 scan descriptions sharded over the ranks; each rank "reconstructs" its
+    # scans (a deterministic function of the scan's seeded inputs stands in for the GPU
+    # solve) and rank 0 gathers the per-scan results in the batch's order
+    import numpy as np
+    from paper_2005_11976_gb300 import synth
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    replicas.init("gloo")
+    scans = synth.batched_scans(7)
+    mine = replicas.shard(len(scans), rank, world)
+    vals = [(i, scans[i].n_proj, float(np.round(scans[i].tx, 12))) for i in mine]
+    got = replicas.gather_ordered(vals, len(scans), rank, world)
+    out.put((rank, got))
+    import torch.distributed as dist
+    dist.destroy_process_group()
+
+
+def test_two_ranks_shard_a_batch_and_gather_results_in_order():
+    import torch.multiprocessing as mp
+    from paper_2005_11976_gb300 import synth
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_batch_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = dict(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    scans = synth.batched_scans(7)
+    assert res[1] is None
+    assert res[0] == [(i, s.n_proj, float(round(s.tx, 12))) for i, s in enumerate(scans)]
+    # one process: the list comes back as it is
+    assert replicas.gather_ordered([1, 2], 2, 0, 1) == [1, 2]
+    with pytest.raises(ValueError):
+        replicas.gather_ordered([1], 4, 0, 2)
+
