@@ -198,6 +198,11 @@ def main():
                     help="skip the bounded batched-vs-plain and served-vs-plain comparisons")
     ap.add_argument("--no-fused", action="store_true",
                     help="two launches per subset (projector, back-projector) instead of one")
+    ap.add_argument("--record-runs", type=int, default=0,
+                    help="medium: runs per ray of the stored segment records (0: the library's default)")
+    ap.add_argument("--no-records", action="store_true",
+                    help="medium: walk every ray in every subset instead of replaying the pose's "
+                         "stored segment records")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -254,6 +259,10 @@ def main():
     prm = cylct.sart_params(n_iter=N_ITER, lam=LAMBDA, use_graph=bool(args.graph), weight_dtype=cylct.CYL_U8)
     plan.cyl_plan_set_timing(True)
     plan.cyl_plan_set_fused(not args.no_fused)
+    use_rec = not args.no_records and not args.no_fused
+    if use_rec:
+        plan.cyl_plan_set_records(1, args.record_runs, stream)
+    rec_ready, rec_bytes = plan.cyl_plan_records()
 
     def step(st):
         plan.cyl_plan_set_pose(pose, st)
@@ -353,6 +362,10 @@ def main():
             names = ["forward projection (k_fp)", "back-projection into (num, den) (k_bp)",
                      "SART voxel update (k_update_nd4)"]
             per = [fwd, back, upd]
+        elif rec_ready:
+            names = ["projection, residual and back-projection from the stored segment records (k_rec_sart)",
+                     None, "SART voxel update (k_update_nd4)"]
+            per = [fwd + back, 0.0, upd]
         else:
             names = ["projection, residual and back-projection, one walk (k_sart)", None,
                      "SART voxel update (k_update_nd4)"]
@@ -438,9 +451,10 @@ def main():
             r = serving_compare(torch, cylct, 24, rate, 60.0, ("small", "medium"))
             serving[key] = {k: v for k, v in r.items() if k not in ("latencies_s", "plain_latencies_s")}
 
-    # per step: ray records + cuts (set_pose), log, weight max + scale, and per subset the
-    # projector, the back-projector and the update
-    n_launch = args.steps * (2 + 1 + 2 + N_ITER * scan.n_proj * (3 if args.no_fused else 2))
+    # per step: ray records + cuts (set_pose; with segment records also their count walk,
+    # rows, scan and record walk), log, weight max + scale, and per subset the projector,
+    # the back-projector and the update
+    n_launch = args.steps * (2 + (4 if rec_ready else 0) + 1 + 2 + N_ITER * scan.n_proj * (3 if args.no_fused else 2))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -451,6 +465,9 @@ def main():
                        else "eager, a CUDA event between launches",
                        parallelism="replicas" if world > 1 else "single GPU"),
         "grays_per_s": grays, "rel_err_vs_oracle_one_subset": parity, "set_pose_ms": set_pose_ms,
+        "segment_records": {"used": rec_ready, "bytes": rec_bytes,
+                            "note": "each pose's pieces written once at set-up (inside every timed step) "
+                                    "and replayed by the subsets"} if use_rec else {"used": False},
         "rel_err_bound": "<=1e-5 rel L2 per projection and per iterate (tests)",
         "wall_s_timed": t_wall, "clocks": clk, "gpu_launches": n_launch,
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,

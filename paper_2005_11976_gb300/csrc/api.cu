@@ -272,6 +272,38 @@ extern "C" int cyl_plan_set_sart_pieces(cyl_plan *plan, int32_t pieces)
     return CYL_OK;
 }
 
+extern "C" int cyl_plan_set_records(cyl_plan *plan, int32_t enable, int32_t runs, void *stream)
+{
+    if (!plan) return set_error(CYL_EINVAL, "plan is null");
+    if (enable != 0 && enable != 1) return set_error(CYL_EINVAL, "enable must be 0 or 1");
+    int lg = 0;
+    while (lg < 5 && (1 << lg) < runs) ++lg;
+    if (runs != 0 && (runs < 0 || (1 << lg) != runs)) return set_error(CYL_EINVAL, "runs must be 0, 1, 2, 4, 8, 16 or 32");
+    DeviceGuard dg(plan->device);
+    if (!dg.ok) return cuda_error(dg.err, "cudaSetDevice");
+    std::lock_guard<std::mutex> lock(plan->mu);
+    cudaStream_t user = (cudaStream_t)stream;
+    CYL_CUDA(cudaEventRecord(plan->ev_in, user));
+    CYL_CUDA(cudaStreamWaitEvent(plan->ws, plan->ev_in, 0));
+    plan->rec_mode = enable;
+    plan->rec_lgP = runs ? lg : kRecLgP;
+    int rc = CYL_OK;
+    if (enable == 0) plan->free_records();
+    else rc = plan->build_records(plan->ws);
+    if (rc) return rc;
+    CYL_CUDA(cudaEventRecord(plan->ev_out, plan->ws));
+    CYL_CUDA(cudaStreamWaitEvent(user, plan->ev_out, 0));
+    return CYL_OK;
+}
+
+extern "C" int cyl_plan_records(const cyl_plan *plan, int32_t *ready, int64_t *rec_bytes)
+{
+    if (!plan) return set_error(CYL_EINVAL, "plan is null");
+    if (ready) *ready = plan->rec_ready ? 1 : 0;
+    if (rec_bytes) *rec_bytes = plan->rec_ready ? plan->rec_rows * 32 * (int64_t)sizeof(uint32_t) : 0;
+    return CYL_OK;
+}
+
 extern "C" int cyl_plan_tune(cyl_plan *plan, void *stream)
 {
     if (!plan) return set_error(CYL_EINVAL, "plan is null");

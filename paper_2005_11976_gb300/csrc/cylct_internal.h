@@ -56,9 +56,28 @@ struct RayList {
 
 constexpr int kSplit = 16;  // pieces per ray recorded at set-up (P divides it)
 constexpr int kPiecesFp = 8, kPiecesBp = 2;   // default pieces per ray of each kernel
-constexpr int kSched = 8;   // ints of scheduler state per plan (two per ray kernel kind)
+constexpr int kSched = 10;  // ints of scheduler state per plan (two per ray kernel kind)
 // The one-launch SART subset (k_sart): threads per block and default pieces per ray.
 constexpr int kSartThreads = 128, kPiecesSart = 8;
+
+// Stored segment records of a pose (records.cu): each ray's pieces as 4-byte records
+// (FP32 length, low 3 bits the move to the next piece's voxel), cut into P runs of
+// consecutive pieces; a task is 32 / P consecutive pixels of a view, one run per lane,
+// whose records are rows of 32 words.
+constexpr int kRecMoves = 8;
+constexpr int kRecLgP = 3;    // default runs per ray: 8
+struct RecDev {
+    const uint32_t *rec;      // [rows][32]
+    const int64_t *row_off;   // [n_tasks + 1]: first row of each task (task = view * tpv + pixel / R)
+    const uint32_t *cnt;      // [view][pixel]: pieces of each ray
+    const int32_t *idx0;      // [view][pixel][P]: voxel of the first piece of each run
+    const float4 *ray_c;      // ray records' third part (chord = row sum L_j in .z)
+    int64_t npix;
+    int64_t tpv;              // tasks per view
+    int lgP;                  // log2 of the runs per ray
+    int delta[kRecMoves];     // voxel index change of each move code
+    float eps;                // floor of Eq. 7's sums
+};
 
 // SART update of one subset (Eq. 7): x += scale * w * num / den where den > 0.
 struct UpdateArgs {
@@ -133,6 +152,31 @@ cudaError_t launch_sart_rays(const ScanDev &sd, int P, int p0, int np, const voi
                              cyl_dtype yt, float2 *nd, float2 *zero_buf, int64_t zero_len, cudaStream_t st,
                              const RayList &rl = RayList{nullptr, nullptr});
 cudaError_t launch_update_nd(int64_t n_vox, const float2 *nd, const UpdateArgs &u, cudaStream_t st);
+// Blocks of a persistent grid of `kernel`: every SM filled with as many blocks of
+// `threads` threads (and `smem` bytes of dynamic shared memory) as fit, at most `cap`
+// per SM (0: no cap); looked up once per kernel and device.
+unsigned persistent_blocks(const void *kernel, size_t smem, int cap = 0, int threads = 256);
+// Records (records.cu), 2^lgP runs per ray.  Count the pieces of every ray of views
+// 0 .. n_proj-1 into cnt and the first row of each task into row_off (n_tasks + 1
+// entries, row_off[n_tasks] = rows); then, with rec sized for those rows, write the
+// records and the runs' first voxels (*bad set if a ray's pieces differ from its count).
+cudaError_t launch_rec_count(const ScanDev &sd, int n_proj, int lgP, uint32_t *cnt, int64_t *row_off,
+                             cudaStream_t st);
+cudaError_t launch_rec_fill(const ScanDev &sd, int n_proj, int lgP, uint32_t *cnt, const int64_t *row_off,
+                            uint32_t *rec, int32_t *idx0, int *bad, cudaStream_t st);
+RecDev rec_dev(const ScanDev &sd, int lgP, const uint32_t *rec, const int64_t *row_off, const uint32_t *cnt,
+               const int32_t *idx0);
+// One SART subset of views p0 .. p0+np-1 from the records: the projections, the residuals
+// against y and their back-projection into num (the numerator of Eq. 7, 4 ceil(V / 4)
+// floats, 16-byte aligned).  sched: two ints of scheduler state, zero at rest.
+cudaError_t launch_rec_sart(const RecDev &rd, int p0, int np, const void *x, cyl_dtype xt, const void *y,
+                            cyl_dtype yt, float *num, int *sched, cudaStream_t st);
+// The reciprocal column sums r (Eq. 7's normalisation, summed in FP64 into den, which
+// must be zero on entry and is zero again on return) of the subset of views p0 .. p0+np-1.
+cudaError_t launch_rec_inv_den(const RecDev &rd, int p0, int np, int64_t n_vox, double *den, float *r,
+                               cudaStream_t st);
+// x += s w num r, num cleared.
+cudaError_t launch_update_rec(int64_t n_vox, float *num, const float *r, const UpdateArgs &u, cudaStream_t st);
 cudaError_t launch_count_rays(const ScanDev &sd, int p0, int np, unsigned long long *counts,
                               cudaStream_t st,
                               const RayList &rl = RayList{nullptr, nullptr});

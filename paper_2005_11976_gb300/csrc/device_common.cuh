@@ -53,6 +53,46 @@ __device__ __forceinline__ void zero_slice(float2 *buf, int64_t len, int64_t tid
     for (int64_t i = tid; i < len; i += nthreads) buf[i] = make_float2(0.f, 0.f);
 }
 
+// --------------------------------------------------------------- SART update weights
+
+// weight of voxel m (1 without a map); the element type is uniform over a launch
+__device__ __forceinline__ float weight_at(const UpdateArgs &u, int64_t m)
+{
+    if (!u.w) return 1.f;
+    switch (u.w_t) {
+    case CYL_F16: return weight_f32(__ldg(static_cast<const __half *>(u.w) + m));
+    case CYL_BF16: return weight_f32(__ldg(static_cast<const __nv_bfloat16 *>(u.w) + m));
+    case CYL_U8: return weight_f32(__ldg(static_cast<const uint8_t *>(u.w) + m));
+    default: return __ldg(static_cast<const float *>(u.w) + m);
+    }
+}
+
+// weights of voxels 4i .. 4i + 3 in one aligned load (4, 8 or 16 bytes)
+__device__ __forceinline__ float4 weight4_at(const UpdateArgs &u, int64_t i)
+{
+    if (!u.w) return make_float4(1.f, 1.f, 1.f, 1.f);
+    switch (u.w_t) {
+    case CYL_F16: {
+        const uint2 r = __ldg(static_cast<const uint2 *>(u.w) + i);
+        const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&r.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&r.y));
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+    case CYL_BF16: {
+        const uint2 r = __ldg(static_cast<const uint2 *>(u.w) + i);
+        const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&r.x));
+        const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&r.y));
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+    case CYL_U8: {
+        const unsigned r = __ldg(static_cast<const unsigned *>(u.w) + i);
+        return make_float4((float)(r & 0xffu), (float)((r >> 8) & 0xffu), (float)((r >> 16) & 0xffu),
+                           (float)(r >> 24));
+    }
+    default: return __ldg(static_cast<const float4 *>(u.w) + i);
+    }
+}
+
 // --------------------------------------------------------------- work scheduling
 
 // sched[0] hands out warp tasks; sched[1] counts the warps that found no work left, and

@@ -92,6 +92,8 @@ int cyl_plan::upload_pose(const cyl_pose &po, cudaStream_t st)
     if (!use_list) {
         PL_CUDA(launch_rays(g, d_geo, geom.n_proj, d_ray[0], d_ray[1], d_ray[2], st));
         PL_CUDA(launch_split(scan_dev(), (int64_t)geom.n_proj * n_pix, d_split, st));
+        int rc;
+        if ((rc = build_records(st))) return rc;
     } else if (d_act && po.alpha == pose.alpha && po.beta == pose.beta && po.tx == pose.tx &&
                po.ty == pose.ty && po.tz == pose.tz) {
         // a spin about the part's axis: the grid cylinder, and so the list, stay as they are
@@ -145,6 +147,117 @@ int cyl_plan::ensure(void **p, size_t &cap, size_t nbytes)
     int rc = alloc(p, nbytes);
     if (!rc) cap = nbytes;
     return rc;
+}
+
+void cyl_plan::release(void **p, size_t &cap)
+{
+    if (!*p) return;
+    cudaStreamSynchronize(ws);
+    auto it = std::find(allocs.begin(), allocs.end(), *p);
+    if (it != allocs.end()) allocs.erase(it);
+    cudaFree(*p);
+    bytes -= cap;
+    *p = nullptr;
+    cap = 0;
+    drop_graphs();
+}
+
+void cyl_plan::free_records()
+{
+    release((void **)&d_rinv, rinv_cap);
+    release((void **)&d_den64, den64_cap);
+    release((void **)&d_num, num_cap);
+    rinv_sub = 0;
+    release((void **)&d_rec, rec_cap);
+    release((void **)&d_rcnt, rcnt_cap);
+    release((void **)&d_ridx0, ridx0_cap);
+    release((void **)&d_rrow, rrow_cap);
+    release((void **)&d_rbad, rbad_cap);
+    rec_ready = false;
+    rec_rows = 0;
+}
+
+int cyl_plan::build_records(cudaStream_t st)
+{
+    const bool was = rec_ready;
+    rec_ready = false;
+    rinv_sub = 0;             // the column sums belong to the pose
+    if (was) drop_graphs();   // captured sweeps launch the record kernel
+    if (!rec_mode || use_list) return CYL_OK;
+    const int64_t n_rays = (int64_t)geom.n_proj * n_pix;
+    const int64_t n_tasks = (int64_t)geom.n_proj * ((n_pix + 31) / 32);   // 32 rays per task
+    int rc;
+    if ((rc = ensure((void **)&d_rcnt, rcnt_cap, sizeof(uint32_t) * n_rays))) return rc;
+    if ((rc = ensure((void **)&d_ridx0, ridx0_cap, sizeof(int32_t) * (n_rays << rec_lgP)))) return rc;
+    if ((rc = ensure((void **)&d_rrow, rrow_cap, sizeof(int64_t) * (n_tasks + 1)))) return rc;
+    if ((rc = ensure((void **)&d_rbad, rbad_cap, sizeof(int)))) return rc;
+    PL_CUDA(launch_rec_count(scan_dev(), geom.n_proj, rec_lgP, d_rcnt, d_rrow, st));
+    int64_t rows = 0;
+    PL_CUDA(cudaMemcpyAsync(&rows, d_rrow + n_tasks, sizeof rows, cudaMemcpyDeviceToHost, st));
+    PL_CUDA(cudaStreamSynchronize(st));
+    if (rows < 0 || rows > n_tasks * (int64_t)g.max_steps) return set_error(CYL_EDEVICE, "record rows out of range");
+    const size_t need = (size_t)std::max<int64_t>(rows, 1) * 32 * sizeof(uint32_t);
+    if (need > rec_cap) {
+        // the records leave room for everything else: at most 40 % of the device, and
+        // 1 GiB of it free afterwards; otherwise the subsets walk the rays
+        size_t fr = 0, tot = 0;
+        PL_CUDA(cudaMemGetInfo(&fr, &tot));
+        if (need > tot / 10 * 4 || need + ((size_t)1 << 30) > fr + rec_cap) {
+            release((void **)&d_rec, rec_cap);
+            return CYL_OK;
+        }
+        if (ensure((void **)&d_rec, rec_cap, need + need / 16)) return CYL_OK;
+    }
+    PL_CUDA(cudaMemsetAsync(d_rbad, 0, sizeof(int), st));
+    PL_CUDA(launch_rec_fill(scan_dev(), geom.n_proj, rec_lgP, d_rcnt, d_rrow, d_rec, d_ridx0, d_rbad, st));
+    int bad = 1;
+    PL_CUDA(cudaMemcpyAsync(&bad, d_rbad, sizeof bad, cudaMemcpyDeviceToHost, st));
+    PL_CUDA(cudaStreamSynchronize(st));
+    rec_rows = rows;
+    rec_ready = bad == 0;
+    if (rec_ready != was) drop_graphs();
+    return CYL_OK;
+}
+
+bool cyl_plan::prepare_records(int subset, cudaStream_t st, int &rc)
+{
+    rc = CYL_OK;
+    if (!rec_ready) return false;
+    const int n_sub = (geom.n_proj + subset - 1) / subset;
+    const size_t nv4 = (size_t)((n_vox + 3) / 4) * 4;
+    if (rinv_sub != subset) {
+        const size_t want = sizeof(float) * (size_t)n_vox * n_sub;
+        if (want > rinv_cap) {
+            size_t fr = 0, tot = 0;
+            if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+                cudaGetLastError();
+                return false;
+            }
+            if (want + ((size_t)1 << 30) > fr + rinv_cap) return false;   // walk instead
+        }
+        if (ensure((void **)&d_rinv, rinv_cap, want)) return false;
+        if ((rc = ensure((void **)&d_den64, den64_cap, sizeof(double) * (size_t)n_vox))) return false;
+        if (cudaMemsetAsync(d_den64, 0, sizeof(double) * (size_t)n_vox, st) != cudaSuccess) {
+            rc = cuda_error(cudaGetLastError(), "cudaMemsetAsync");
+            return false;
+        }
+        const RecDev rd = rec_dev();
+        for (int k = 0; k < n_sub; ++k) {
+            const int p0 = k * subset, np = std::min(subset, geom.n_proj - p0);
+            const cudaError_t e = launch_rec_inv_den(rd, p0, np, n_vox, d_den64, d_rinv + (size_t)k * n_vox, st);
+            if (e != cudaSuccess) {
+                rc = cuda_error(e, "launch_rec_inv_den");
+                return false;
+            }
+        }
+        rinv_sub = subset;
+    }
+    if ((rc = ensure((void **)&d_num, num_cap, sizeof(float) * nv4))) return false;
+    if (cudaMemsetAsync(d_num, 0, sizeof(float) * nv4, st) != cudaSuccess) {
+        rc = cuda_error(cudaGetLastError(), "cudaMemsetAsync");
+        return false;
+    }
+    return true;
 }
 
 cudaEvent_t *cyl_plan::next_events(int n)
@@ -204,7 +317,17 @@ int cyl_plan::queue_sweep(const SolveState &s, cudaStream_t st, bool timed, int 
         cudaEvent_t *ev = timed ? next_events(4) : nullptr;
         if (timed && !ev) return set_error(CYL_EDEVICE, "event creation failed");
         if (ev) PL_CUDA(cudaEventRecordWithFlags(ev[0], st, rec_flags));
-        if (fused) {
+        if (s.rec) {
+            // the same subset replaying the pose's stored records into the numerator; the
+            // update divides by the pose's column sums
+            PL_CUDA(launch_rec_sart(rec_dev(), p0, np, s.x_proj, s.x_proj_t, sino_p, s.sino_t, d_num, d_sched + 8,
+                                    st));
+            if (ev) PL_CUDA(cudaEventRecordWithFlags(ev[1], st, rec_flags));
+            if (ev) PL_CUDA(cudaEventRecordWithFlags(ev[2], st, rec_flags));
+            PL_CUDA(launch_update_rec(n_vox, d_num, d_rinv + (size_t)k * n_vox, upd, st));
+            if (ev) PL_CUDA(cudaEventRecordWithFlags(ev[3], st, rec_flags));
+            continue;
+        } else if (fused) {
             // projection, residual and back-projection in one launch; no back-projector time
             PL_CUDA(launch_sart_rays(sd, p_sart, p0, np, s.x_proj, s.x_proj_t, sino_p, s.sino_t, d_nd[b], d_nd[b ^ 1],
                                      n_vox, st, ray_list()));
@@ -296,7 +419,10 @@ int cyl_plan::solve(const void *sino, cyl_dtype sino_t, const void *x0, const vo
         PL_CUDA(launch_convert(d_xo, x_t, d_x32, CYL_F32, n_vox, ws));
     }
     if (d_w) PL_CUDA(launch_weight_scale(d_w, w_t, n_vox, prm.weight_mode, (float)prm.lambda, d_wscale, ws));
-    for (int k = 0; k < 2; ++k) PL_CUDA(cudaMemsetAsync(d_nd[k], 0, sizeof(float2) * n_vox, ws));
+    s.rec = fused && prepare_records(subset, ws, rc) ? 1 : 0;
+    if (rc) return rc;
+    if (!s.rec)
+        for (int k = 0; k < 2; ++k) PL_CUDA(cudaMemsetAsync(d_nd[k], 0, sizeof(float2) * n_vox, ws));
 
     const bool one_graph = !(n_sub & 1) || prm.n_iter == 1;
     if (timing && prm.use_graph && prm.n_iter > 0 && one_graph) {

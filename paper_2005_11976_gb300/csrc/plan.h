@@ -40,13 +40,14 @@ struct SolveState {
     double lambda = 0.5;
     int clamp = 0;
     int subset = 1;
+    int rec = 0;                   // subsets replay the pose's stored records
 
     bool operator==(const SolveState &o) const
     {
         return sino == o.sino && sino_t == o.sino_t && x_proj == o.x_proj &&
                x_proj_t == o.x_proj_t && x32 == o.x32 && x16 == o.x16 && x16_t == o.x16_t &&
                strict16 == o.strict16 && w == o.w && w_t == o.w_t && lambda == o.lambda && clamp == o.clamp &&
-               subset == o.subset;
+               subset == o.subset && rec == o.rec;
     }
 };
 
@@ -123,6 +124,28 @@ struct cyl_plan {
     int p_fp = 0, p_bp = 0;        // pieces per ray of the projector / back-projector (0: default)
     int p_sart = 0;                // pieces per ray of the fused SART kernel (0: default)
     bool fused = true;             // SART subsets in one launch (k_sart) instead of two
+    // Stored segment records of the pose (records.cu; dense plans): rec_mode 0 (the
+    // default) walks every ray in every subset; 1 writes each pose's pieces as records at
+    // set-up, when they fit the device, and replays them in the one-launch subsets.
+    int rec_mode = 0;
+    int rec_lgP = cylct::kRecLgP;  // log2 of the runs per ray (replay lanes per ray)
+    bool rec_ready = false;        // the records hold the current pose
+    uint32_t *d_rcnt = nullptr;    // [view][pixel] pieces of each ray
+    int32_t *d_ridx0 = nullptr;    // [view][pixel][runs] first voxel of each run
+    int64_t *d_rrow = nullptr;     // first row of each task, and the total
+    uint32_t *d_rec = nullptr;     // the records, rows of 32
+    int *d_rbad = nullptr;         // set by the record walk if a count differs
+    size_t rcnt_cap = 0, ridx0_cap = 0, rrow_cap = 0, rec_cap = 0, rbad_cap = 0;
+    int64_t rec_rows = 0;
+    // Eq. 7 with records: the numerator alone is reduced per subset (d_num, 4 ceil(V / 4)
+    // floats); the column sums depend only on the pose and the subsets, so their
+    // reciprocals are summed once (FP64, d_den64) per pose and subset size (rinv_sub,
+    // 0: none) into d_rinv [subset][voxel].
+    float *d_num = nullptr;
+    float *d_rinv = nullptr;
+    double *d_den64 = nullptr;
+    size_t num_cap = 0, rinv_cap = 0, den64_cap = 0;
+    int rinv_sub = 0;
     float *d_x32 = nullptr;
     size_t x32_cap = 0;
     void *d_stage[4] = {nullptr, nullptr, nullptr, nullptr};  // sino, x0, w, x_out
@@ -164,6 +187,7 @@ struct cyl_plan {
         return sd;
     }
     cylct::RayList ray_list() const { return cylct::RayList{use_list ? d_act : nullptr, d_act_off}; }
+    cylct::RecDev rec_dev() const { return cylct::rec_dev(scan_dev(), rec_lgP, d_rec, d_rrow, d_rcnt, d_ridx0); }
 
     template <class T> int alloc(T **p, size_t nbytes)
     {
@@ -182,6 +206,13 @@ struct cyl_plan {
     int upload_pose(const cyl_pose &po, cudaStream_t st);
     // Grow-only scratch buffer.
     int ensure(void **p, size_t &cap, size_t nbytes);
+    void release(void **p, size_t &cap);
+    // Records of the current pose (rec_mode 1): count, size, write; rec_ready tells whether
+    // they fit.  Synchronises st.
+    int build_records(cudaStream_t st);
+    void free_records();
+    // Record buffers of a solve with subsets of `subset` views; false: walk instead.
+    bool prepare_records(int subset, cudaStream_t st, int &rc);
     cudaEvent_t *next_events(int n);
     // Queue one sweep; `parity` is the subset counter's parity at its first subset.
     int queue_sweep(const cylct::SolveState &s, cudaStream_t st, bool timed, int parity);

@@ -101,44 +101,6 @@ __device__ __forceinline__ double ray_sum(float v, int P)
     return d;
 }
 
-// weight of voxel m (1 without a map); the element type is uniform over a launch
-__device__ __forceinline__ float weight_at(const UpdateArgs &u, int64_t m)
-{
-    if (!u.w) return 1.f;
-    switch (u.w_t) {
-    case CYL_F16: return weight_f32(__ldg(static_cast<const __half *>(u.w) + m));
-    case CYL_BF16: return weight_f32(__ldg(static_cast<const __nv_bfloat16 *>(u.w) + m));
-    case CYL_U8: return weight_f32(__ldg(static_cast<const uint8_t *>(u.w) + m));
-    default: return __ldg(static_cast<const float *>(u.w) + m);
-    }
-}
-
-// weights of voxels 4i .. 4i + 3 in one aligned load (4, 8 or 16 bytes)
-__device__ __forceinline__ float4 weight4_at(const UpdateArgs &u, int64_t i)
-{
-    if (!u.w) return make_float4(1.f, 1.f, 1.f, 1.f);
-    switch (u.w_t) {
-    case CYL_F16: {
-        const uint2 r = __ldg(static_cast<const uint2 *>(u.w) + i);
-        const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&r.x));
-        const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&r.y));
-        return make_float4(a.x, a.y, b.x, b.y);
-    }
-    case CYL_BF16: {
-        const uint2 r = __ldg(static_cast<const uint2 *>(u.w) + i);
-        const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&r.x));
-        const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&r.y));
-        return make_float4(a.x, a.y, b.x, b.y);
-    }
-    case CYL_U8: {
-        const unsigned r = __ldg(static_cast<const unsigned *>(u.w) + i);
-        return make_float4((float)(r & 0xffu), (float)((r >> 8) & 0xffu), (float)((r >> 16) & 0xffu),
-                           (float)(r >> 24));
-    }
-    default: return __ldg(static_cast<const float4 *>(u.w) + i);
-    }
-}
-
 template <class X>
 __device__ __forceinline__ void update_voxel(const UpdateArgs &u, int64_t m, float2 v, float sc)
 {
@@ -778,10 +740,7 @@ static int log2_pieces(int P, int dflt)
 // a 64-scan batch, and the same at 2.
 constexpr int kBpBlocksPerSm = 2, kBpBatchBlocksPerSm = 3;
 
-// Blocks of a persistent grid: every SM filled with as many 256-thread blocks of
-// `kernel` (with `smem` bytes of dynamic shared memory) as fit, at most `cap` per SM
-// (0: no cap); looked up once.
-static unsigned persistent_blocks(const void *kernel, size_t smem, int cap = 0, int threads = 256)
+unsigned persistent_blocks(const void *kernel, size_t smem, int cap, int threads)
 {
     static std::mutex mu;
     static std::map<std::pair<const void *, std::pair<int, size_t>>, unsigned> cache;

@@ -129,6 +129,8 @@ SIGNATURES = {
     "cyl_project": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _I32, _I32, _VP, ctypes.c_int, _VP]),
     "cyl_plan_set_fused": (ctypes.c_int, [_VP, _I32]),
     "cyl_plan_set_sart_pieces": (ctypes.c_int, [_VP, _I32]),
+    "cyl_plan_set_records": (ctypes.c_int, [_VP, _I32, _I32, _VP]),
+    "cyl_plan_records": (ctypes.c_int, [_VP, ctypes.POINTER(_I32), ctypes.POINTER(_I64)]),
     "cyl_binary_version": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_I32)]),
     "cyl_project_noalloc": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _I32, _I32, _VP, ctypes.c_int, _VP]),
     "cyl_backproject": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _I32, _I32, _VP, _VP, _VP]),
@@ -345,6 +347,16 @@ class Plan:
 
     def cyl_plan_set_sart_pieces(self, pieces: int = 0):
         _check(load().cyl_plan_set_sart_pieces(self.h, int(pieces)), "cyl_plan_set_sart_pieces")
+
+    def cyl_plan_set_records(self, enable: int, runs: int = 0, stream=None):
+        _check(load().cyl_plan_set_records(self.h, int(enable), int(runs), stream_ptr(stream)),
+               "cyl_plan_set_records")
+
+    def cyl_plan_records(self):
+        """(ready, bytes) of the plan's stored segment records."""
+        r, b = _I32(), _I64()
+        _check(load().cyl_plan_records(self.h, ctypes.byref(r), ctypes.byref(b)), "cyl_plan_records")
+        return bool(r.value), b.value
 
     def cyl_plan_set_timing(self, enable: bool):
         _check(load().cyl_plan_set_timing(self.h, int(enable)), "cyl_plan_set_timing")

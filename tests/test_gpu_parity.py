@@ -576,3 +576,33 @@ def test_grazing_ray_and_voxel_floor_on_gpu(lib, orc, ratio):
             plan.cyl_plan_set_fused(fused)
             got = gu.sart(plan, p, x0=x0, n_iter=1, lam=0.6)
             assert abs(got.item() - ref.item()) <= 2e-3 * abs(ref.item() - 0.02)
+
+
+@pytest.mark.parametrize("size", ["medium", "precision"])
+def test_column_sums_at_full_size(lib, orc, size):
+    # The normalisation sums of Eq. 7 at full size: den_m = sum_j t_jm over one view,
+    # accumulated in FP32 by the walking back-projector, against the FP64 oracle's A^T 1.
+    # A voxel receives about two pieces per view, so the FP32 additions round at ~1e-7;
+    # the error is that of the pieces' FP32 end positions.  Written out for the record (-s)
+    # for whole rays (1 piece per ray) and rays cut into 16 pieces.
+    full = (synth.medium_scan(synth.rng_for("medium")) if size == "medium"
+            else synth.precision_scan(synth.rng_for("precision")))
+    s = dataclasses.replace(full, angles=full.angles[37:38])
+    o = osetup(orc, s)
+    ref = orc.backproject(o, np.ones(s.sino_shape))
+    eps = s.radius * 2.0 ** -16                       # the floor of the sums
+    hit = ref >= eps
+    dr = s.radius / s.n_r
+    with cylct.Plan(s) as plan:
+        for pieces in (1, 16):
+            plan.cyl_plan_set_pieces(8, pieces)
+            _, cs = gu.backproject(plan, np.ones(s.sino_shape), colsum=True)
+            err = np.abs(cs - ref)
+            worst = np.unravel_index(int(np.argmax(err)), s.vol_shape)
+            rel = err[hit] / ref[hit]
+            print(f"\ncolumn sums {size}, {pieces} pieces per ray: rel L2 {gu.rel_l2(cs, ref):.2e}, "
+                  f"max abs {err.max():.2e} mm at (ih, itheta, ir) {tuple(int(v) for v in worst)} "
+                  f"(den {ref[worst]:.3e}), max rel over sums >= eps {rel.max():.2e}, "
+                  f"sums on opposite sides of eps {int(np.sum((cs >= eps) != hit))}")
+            assert gu.rel_l2(cs, ref) <= 2 * TOL_FP32
+            assert err.max() <= 0.01 * dr
