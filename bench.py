@@ -34,10 +34,12 @@ sys.path.insert(0, ROOT)
 METRIC = "SART iters/sec and GRays/s at stated rel err; batched-serve vs plain scans/s, p99"
 UNIT = "SART iters/s"
 N_ITER = 20
-# DRAM bytes (read + write) per launch of each kernel at the medium workload, from one ncu
-# capture of the current kernels (profiles/sart_medium_kernels.md; k_fp and k_bp, the
-# two-launch form, from an earlier capture of the same walks).
-TRAFFIC: dict = {"k_sart": 183.69e6, "k_update_nd4": 115.70e6, "k_fp": 73.27e6, "k_bp": 82.10e6}
+# DRAM bytes (read + write) per launch of each kernel at the medium workload (one launch =
+# one view), from one ncu capture of the same kernels on the medium grid and detector
+# (k_rec_sart and k_update_rec4 on 8 of the 180 views; k_fp and k_bp, the two-launch
+# form, from an earlier capture of the same walks).
+TRAFFIC: dict = {"k_sart": 183.69e6, "k_update_nd4": 115.70e6, "k_fp": 73.27e6, "k_bp": 82.10e6,
+                 "k_rec_sart": 194.59e6, "k_update_rec4": 112.07e6}
 # DRAM bytes per scan of the corner pass on Table 1 scans (FP16), from one ncu capture of
 # 20 scans (profiles/pose_corners_table1.md); a launch's traffic scales with its scans.
 TRAFFIC_PER_SCAN: dict = {"k_corners": 2.5122e9 / 20}
@@ -187,9 +189,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--graph", action="store_true",
-                    help="one captured CUDA graph per sweep, timing events captured in it "
-                         "(default: eager launches with an event between kernels)")
+    ap.add_argument("--eager", action="store_true",
+                    help="eager launches with a CUDA event between kernels (default: one captured CUDA "
+                         "graph per sweep, as cyl_sart_solve runs by default, timing events captured in it)")
     ap.add_argument("--workload", default="medium",
                     choices=["medium", "batched", "serving", "precision", "mtf", "pose", "table1", "table1_batch",
                              "phase", "l2ops"])
@@ -256,7 +258,7 @@ def main():
     p = torch.empty_like(counts)
     x_out = torch.empty(scan.vol_shape, dtype=torch.float32, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
-    prm = cylct.sart_params(n_iter=N_ITER, lam=LAMBDA, use_graph=bool(args.graph), weight_dtype=cylct.CYL_U8)
+    prm = cylct.sart_params(n_iter=N_ITER, lam=LAMBDA, use_graph=not args.eager, weight_dtype=cylct.CYL_U8)
     plan.cyl_plan_set_timing(True)
     plan.cyl_plan_set_fused(not args.no_fused)
     use_rec = not args.no_records and not args.no_fused
@@ -364,7 +366,7 @@ def main():
             per = [fwd, back, upd]
         elif rec_ready:
             names = ["projection, residual and back-projection from the stored segment records (k_rec_sart)",
-                     None, "SART voxel update (k_update_nd4)"]
+                     None, "SART voxel update with the pose's column sums (k_update_rec4)"]
             per = [fwd + back, 0.0, upd]
         else:
             names = ["projection, residual and back-projection, one walk (k_sart)", None,
@@ -451,17 +453,18 @@ def main():
             r = serving_compare(torch, cylct, 24, rate, 60.0, ("small", "medium"))
             serving[key] = {k: v for k, v in r.items() if k not in ("latencies_s", "plain_latencies_s")}
 
-    # per step: ray records + cuts (set_pose; with segment records also their count walk,
-    # rows, scan and record walk), log, weight max + scale, and per subset the projector,
-    # the back-projector and the update
-    n_launch = args.steps * (2 + (4 if rec_ready else 0) + 1 + 2 + N_ITER * scan.n_proj * (3 if args.no_fused else 2))
+    # per step: ray records + cuts (set_pose; with segment records also their rows, scan
+    # and record walk, and the pose's column sums, two launches per view), log, weight
+    # max + scale, and per subset the projector, the back-projector and the update
+    n_launch = args.steps * (2 + (3 + 2 * scan.n_proj if rec_ready else 0) + 1 + 2
+                             + N_ITER * scan.n_proj * (3 if args.no_fused else 2))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": dict(CONFIG_MEDIUM,
                        launch="one captured CUDA graph per sweep, CUDA events captured between its "
-                              "kernels (kernel times: the last sweep of every timed step)" if args.graph
+                              "kernels (kernel times: the last sweep of every timed step)" if not args.eager
                        else "eager, a CUDA event between launches",
                        parallelism="replicas" if world > 1 else "single GPU"),
         "grays_per_s": grays, "rel_err_vs_oracle_one_subset": parity, "set_pose_ms": set_pose_ms,

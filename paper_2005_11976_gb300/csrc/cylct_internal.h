@@ -124,7 +124,9 @@ cudaError_t launch_row_sums(const ScanDev &sd, int p0, int np, float *L, cudaStr
 int valid_pieces(int P);
 int default_pieces(int kind /* 0 forward, 1 back */);
 // Cut every ray of all views into kSplit pieces of equal step counts (once per pose).
-cudaError_t launch_split(const ScanDev &sd, int64_t n_rays, uint16_t *split, cudaStream_t st);   // n_rays records
+// cnt (if not null): each ray's number of pieces.
+cudaError_t launch_split(const ScanDev &sd, int64_t n_rays, uint16_t *split, cudaStream_t st,
+                         uint32_t *cnt = nullptr);   // n_rays records
 // Compact plans: the rays of positive chord of every view, in ray order, with their
 // records at their list positions.  Count (and scan into act_off), then fill.
 constexpr int kActChunk = 1024;   // rays per block of the list's count and fill passes
@@ -162,6 +164,8 @@ unsigned persistent_blocks(const void *kernel, size_t smem, int cap = 0, int thr
 // records and the runs' first voxels (*bad set if a ray's pieces differ from its count).
 cudaError_t launch_rec_count(const ScanDev &sd, int n_proj, int lgP, uint32_t *cnt, int64_t *row_off,
                              cudaStream_t st);
+// The rows and row offsets from counts already in cnt (launch_rec_count without its walk).
+cudaError_t launch_rec_rows(const ScanDev &sd, int n_proj, const uint32_t *cnt, int64_t *row_off, cudaStream_t st);
 cudaError_t launch_rec_fill(const ScanDev &sd, int n_proj, int lgP, uint32_t *cnt, const int64_t *row_off,
                             uint32_t *rec, int32_t *idx0, int *bad, cudaStream_t st);
 RecDev rec_dev(const ScanDev &sd, int lgP, const uint32_t *rec, const int64_t *row_off, const uint32_t *cnt,
@@ -171,10 +175,12 @@ RecDev rec_dev(const ScanDev &sd, int lgP, const uint32_t *rec, const int64_t *r
 // floats, 16-byte aligned).  sched: two ints of scheduler state, zero at rest.
 cudaError_t launch_rec_sart(const RecDev &rd, int p0, int np, const void *x, cyl_dtype xt, const void *y,
                             cyl_dtype yt, float *num, int *sched, cudaStream_t st);
-// The reciprocal column sums r (Eq. 7's normalisation, summed in FP64 into den, which
-// must be zero on entry and is zero again on return) of the subset of views p0 .. p0+np-1.
-cudaError_t launch_rec_inv_den(const RecDev &rd, int p0, int np, int64_t n_vox, double *den, float *r,
-                               cudaStream_t st);
+// The reciprocal column sums r (4 ceil(V / 4) floats, 16-byte aligned) of the subset of
+// views p0 .. p0+np-1 (Eq. 7's normalisation): each view's sums in FP32 into den32
+// (4 ceil(V / 4) floats), added across the subset's views in FP64 into den64 (as many
+// doubles; only used when np > 1).  Both must be zero on entry and are zero on return.
+cudaError_t launch_rec_inv_den(const RecDev &rd, int p0, int np, int64_t n_vox, float *den32, double *den64,
+                               float *r, cudaStream_t st);
 // x += s w num r, num cleared.
 cudaError_t launch_update_rec(int64_t n_vox, float *num, const float *r, const UpdateArgs &u, cudaStream_t st);
 cudaError_t launch_count_rays(const ScanDev &sd, int p0, int np, unsigned long long *counts,

@@ -91,9 +91,12 @@ int cyl_plan::upload_pose(const cyl_pose &po, cudaStream_t st)
     PL_CUDA(cudaEventRecord(ev_geo, st));
     if (!use_list) {
         PL_CUDA(launch_rays(g, d_geo, geom.n_proj, d_ray[0], d_ray[1], d_ray[2], st));
-        PL_CUDA(launch_split(scan_dev(), (int64_t)geom.n_proj * n_pix, d_split, st));
+        // the cut walk also counts each ray's pieces when the pose keeps records
+        const int64_t n_rays = (int64_t)geom.n_proj * n_pix;
         int rc;
-        if ((rc = build_records(st))) return rc;
+        if (rec_mode && (rc = ensure((void **)&d_rcnt, rcnt_cap, sizeof(uint32_t) * n_rays))) return rc;
+        PL_CUDA(launch_split(scan_dev(), n_rays, d_split, st, rec_mode ? d_rcnt : nullptr));
+        if ((rc = build_records(st, rec_mode != 0))) return rc;
     } else if (d_act && po.alpha == pose.alpha && po.beta == pose.beta && po.tx == pose.tx &&
                po.ty == pose.ty && po.tz == pose.tz) {
         // a spin about the part's axis: the grid cylinder, and so the list, stay as they are
@@ -166,6 +169,7 @@ void cyl_plan::free_records()
 {
     release((void **)&d_rinv, rinv_cap);
     release((void **)&d_den64, den64_cap);
+    release((void **)&d_den32, den32_cap);
     release((void **)&d_num, num_cap);
     rinv_sub = 0;
     release((void **)&d_rec, rec_cap);
@@ -177,12 +181,20 @@ void cyl_plan::free_records()
     rec_rows = 0;
 }
 
-int cyl_plan::build_records(cudaStream_t st)
+int cyl_plan::build_records(cudaStream_t st, bool counted)
 {
+    // captured sweeps launch the record kernels with the buffers' addresses: they stay
+    // valid while the records do (a reallocation drops them in ensure)
     const bool was = rec_ready;
     rec_ready = false;
     rinv_sub = 0;             // the column sums belong to the pose
-    if (was) drop_graphs();   // captured sweeps launch the record kernel
+    const int rc = write_records(st, counted);
+    if (rec_ready != was) drop_graphs();
+    return rc;
+}
+
+int cyl_plan::write_records(cudaStream_t st, bool counted)
+{
     if (!rec_mode || use_list) return CYL_OK;
     const int64_t n_rays = (int64_t)geom.n_proj * n_pix;
     const int64_t n_tasks = (int64_t)geom.n_proj * ((n_pix + 31) / 32);   // 32 rays per task
@@ -191,7 +203,8 @@ int cyl_plan::build_records(cudaStream_t st)
     if ((rc = ensure((void **)&d_ridx0, ridx0_cap, sizeof(int32_t) * (n_rays << rec_lgP)))) return rc;
     if ((rc = ensure((void **)&d_rrow, rrow_cap, sizeof(int64_t) * (n_tasks + 1)))) return rc;
     if ((rc = ensure((void **)&d_rbad, rbad_cap, sizeof(int)))) return rc;
-    PL_CUDA(launch_rec_count(scan_dev(), geom.n_proj, rec_lgP, d_rcnt, d_rrow, st));
+    if (counted) PL_CUDA(launch_rec_rows(scan_dev(), geom.n_proj, d_rcnt, d_rrow, st));
+    else PL_CUDA(launch_rec_count(scan_dev(), geom.n_proj, rec_lgP, d_rcnt, d_rrow, st));
     int64_t rows = 0;
     PL_CUDA(cudaMemcpyAsync(&rows, d_rrow + n_tasks, sizeof rows, cudaMemcpyDeviceToHost, st));
     PL_CUDA(cudaStreamSynchronize(st));
@@ -215,7 +228,6 @@ int cyl_plan::build_records(cudaStream_t st)
     PL_CUDA(cudaStreamSynchronize(st));
     rec_rows = rows;
     rec_ready = bad == 0;
-    if (rec_ready != was) drop_graphs();
     return CYL_OK;
 }
 
@@ -226,7 +238,7 @@ bool cyl_plan::prepare_records(int subset, cudaStream_t st, int &rc)
     const int n_sub = (geom.n_proj + subset - 1) / subset;
     const size_t nv4 = (size_t)((n_vox + 3) / 4) * 4;
     if (rinv_sub != subset) {
-        const size_t want = sizeof(float) * (size_t)n_vox * n_sub;
+        const size_t want = sizeof(float) * nv4 * n_sub;   // each subset's r padded to a multiple of 4
         if (want > rinv_cap) {
             size_t fr = 0, tot = 0;
             if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
@@ -236,15 +248,23 @@ bool cyl_plan::prepare_records(int subset, cudaStream_t st, int &rc)
             if (want + ((size_t)1 << 30) > fr + rinv_cap) return false;   // walk instead
         }
         if (ensure((void **)&d_rinv, rinv_cap, want)) return false;
-        if ((rc = ensure((void **)&d_den64, den64_cap, sizeof(double) * (size_t)n_vox))) return false;
-        if (cudaMemsetAsync(d_den64, 0, sizeof(double) * (size_t)n_vox, st) != cudaSuccess) {
+        if ((rc = ensure((void **)&d_den32, den32_cap, sizeof(float) * nv4))) return false;
+        if (cudaMemsetAsync(d_den32, 0, sizeof(float) * nv4, st) != cudaSuccess) {
             rc = cuda_error(cudaGetLastError(), "cudaMemsetAsync");
             return false;
+        }
+        if (subset > 1) {
+            if ((rc = ensure((void **)&d_den64, den64_cap, sizeof(double) * nv4))) return false;
+            if (cudaMemsetAsync(d_den64, 0, sizeof(double) * nv4, st) != cudaSuccess) {
+                rc = cuda_error(cudaGetLastError(), "cudaMemsetAsync");
+                return false;
+            }
         }
         const RecDev rd = rec_dev();
         for (int k = 0; k < n_sub; ++k) {
             const int p0 = k * subset, np = std::min(subset, geom.n_proj - p0);
-            const cudaError_t e = launch_rec_inv_den(rd, p0, np, n_vox, d_den64, d_rinv + (size_t)k * n_vox, st);
+            const cudaError_t e =
+                launch_rec_inv_den(rd, p0, np, n_vox, d_den32, d_den64, d_rinv + (size_t)k * nv4, st);
             if (e != cudaSuccess) {
                 rc = cuda_error(e, "launch_rec_inv_den");
                 return false;
@@ -324,7 +344,7 @@ int cyl_plan::queue_sweep(const SolveState &s, cudaStream_t st, bool timed, int 
                                     st));
             if (ev) PL_CUDA(cudaEventRecordWithFlags(ev[1], st, rec_flags));
             if (ev) PL_CUDA(cudaEventRecordWithFlags(ev[2], st, rec_flags));
-            PL_CUDA(launch_update_rec(n_vox, d_num, d_rinv + (size_t)k * n_vox, upd, st));
+            PL_CUDA(launch_update_rec(n_vox, d_num, d_rinv + (size_t)k * (((size_t)n_vox + 3) / 4 * 4), upd, st));
             if (ev) PL_CUDA(cudaEventRecordWithFlags(ev[3], st, rec_flags));
             continue;
         } else if (fused) {

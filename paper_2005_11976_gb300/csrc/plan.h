@@ -138,13 +138,14 @@ struct cyl_plan {
     size_t rcnt_cap = 0, ridx0_cap = 0, rrow_cap = 0, rec_cap = 0, rbad_cap = 0;
     int64_t rec_rows = 0;
     // Eq. 7 with records: the numerator alone is reduced per subset (d_num, 4 ceil(V / 4)
-    // floats); the column sums depend only on the pose and the subsets, so their
-    // reciprocals are summed once (FP64, d_den64) per pose and subset size (rinv_sub,
-    // 0: none) into d_rinv [subset][voxel].
+    // floats); the column sums depend only on the pose and the subsets, so they are summed
+    // once per pose and subset size (rinv_sub, 0: none; per view in FP32, d_den32, across
+    // a subset's views in FP64, d_den64) and kept as reciprocals in d_rinv [subset][voxel].
     float *d_num = nullptr;
     float *d_rinv = nullptr;
+    float *d_den32 = nullptr;
     double *d_den64 = nullptr;
-    size_t num_cap = 0, rinv_cap = 0, den64_cap = 0;
+    size_t num_cap = 0, rinv_cap = 0, den32_cap = 0, den64_cap = 0;
     int rinv_sub = 0;
     float *d_x32 = nullptr;
     size_t x32_cap = 0;
@@ -207,9 +208,10 @@ struct cyl_plan {
     // Grow-only scratch buffer.
     int ensure(void **p, size_t &cap, size_t nbytes);
     void release(void **p, size_t &cap);
-    // Records of the current pose (rec_mode 1): count, size, write; rec_ready tells whether
-    // they fit.  Synchronises st.
-    int build_records(cudaStream_t st);
+    // Records of the current pose (rec_mode 1): count (unless counted), size, write;
+    // rec_ready tells whether they fit.  Synchronises st.
+    int build_records(cudaStream_t st, bool counted = false);   // counted: d_rcnt holds the pose's counts
+    int write_records(cudaStream_t st, bool counted);
     void free_records();
     // Record buffers of a solve with subsets of `subset` views; false: walk instead.
     bool prepare_records(int subset, cudaStream_t st, int &rc);

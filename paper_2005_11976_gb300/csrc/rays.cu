@@ -138,8 +138,9 @@ __device__ __forceinline__ float estimate_steps(const GridDev &g, const RayRec &
 
 // One thread per ray of every view: walk the ray once and record kSplit - 1 cuts, cut i
 // in the middle of the segment that holds step ceil(i N / kSplit) of an estimated N.  The
-// last entry keeps the estimate (saturated), for diagnostics.
-__global__ void __launch_bounds__(256) k_split(ScanDev sd, int64_t n_rays, uint16_t *split)
+// last entry keeps the estimate (saturated), for diagnostics.  cnt (if not null) receives
+// the ray's number of pieces (the stored segment records are sized from it).
+__global__ void __launch_bounds__(256) k_split(ScanDev sd, int64_t n_rays, uint16_t *split, uint32_t *cnt)
 {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n_rays) return;
@@ -147,6 +148,7 @@ __global__ void __launch_bounds__(256) k_split(ScanDev sd, int64_t n_rays, uint1
     uint16_t *out = split + j * kSplit;
     if (!(rr.c.y > rr.c.x)) {
         for (int i = 0; i < kSplit; ++i) out[i] = 0;
+        if (cnt) cnt[j] = 0;
         return;
     }
     const GridDev &g = sd.g;
@@ -168,6 +170,7 @@ __global__ void __launch_bounds__(256) k_split(ScanDev sd, int64_t n_rays, uint1
     }
     for (; next < kSplit; ++next) out[next - 1] = 65535;
     out[kSplit - 1] = (uint16_t)fminf(n_est, 65535.f);
+    if (cnt) cnt[j] = (uint32_t)s;
 }
 
 // ------------------------------------------------------------------ listed rays
@@ -765,10 +768,10 @@ unsigned persistent_blocks(const void *kernel, size_t smem, int cap, int threads
 int valid_pieces(int P) { return log2_pieces(P, kSplit) >= 0; }
 int default_pieces(int kind) { return kind == 0 ? kPiecesFp : kPiecesBp; }
 
-cudaError_t launch_split(const ScanDev &sd, int64_t n_rays, uint16_t *split, cudaStream_t st)
+cudaError_t launch_split(const ScanDev &sd, int64_t n_rays, uint16_t *split, cudaStream_t st, uint32_t *cnt)
 {
     if (n_rays <= 0) return cudaSuccess;
-    k_split<<<(unsigned)((n_rays + 255) / 256), 256, 0, st>>>(sd, n_rays, split);
+    k_split<<<(unsigned)((n_rays + 255) / 256), 256, 0, st>>>(sd, n_rays, split, cnt);
     return cudaGetLastError();
 }
 

@@ -18,8 +18,9 @@
 // the voxel it is in at the first row of every run.
 //
 // The column sums of Eq. 7 depend on the pose and the subsets only: they are summed once
-// per pose in FP64 (k_rec_den) and kept as reciprocals, so the subsets reduce the
-// numerator alone, into one 4-byte accumulator that the update clears.
+// per pose (k_rec_den: each view's few pieces per voxel in FP32, the views of a subset in
+// FP64) and kept as reciprocals, so the subsets reduce the numerator alone, into one
+// 4-byte accumulator that the update clears.
 //
 // The count walk and the record walk are one kernel (k_rec_walk) in two modes, so both
 // produce the same pieces; the record walk checks the count and reports a mismatch.
@@ -163,10 +164,13 @@ __device__ __forceinline__ void red_add4f_if(bool c, float *p, float a, float b,
                  ::"l"(p), "f"(a), "f"(b), "f"(d), "f"(e), "r"((unsigned)c) : "memory");
 }
 
-// Column sums of Eq. 7 over the views of tasks [t0, t0 + n_task): den_m = sum_j t_jm,
-// accumulated in FP64.  One warp per run of a task (as the subsets replay them), the 32
-// rays side by side, each lane issuing one FP64 reduction per piece.
-__global__ void __launch_bounds__(256) k_rec_den(RecDev rd, int64_t t0, int64_t n_task, double *den)
+// Column sums of Eq. 7 over one view (tasks [t0, t0 + n_task)): den_m = sum_j t_jm.  One
+// warp per run of a task, as the subsets replay them: the 32 rays side by side, the
+// pieces of a lane that fall in one aligned quad of voxels going out as one 4 x FP32
+// reduction.  A voxel meets about two pieces of a view, each length rounded to 20
+// mantissa bits, so these FP32 sums are exact unless the lengths differ by more than a
+// factor of 16 (then within 2^-24 relative); the views of a subset add in FP64.
+__global__ void __launch_bounds__(256) k_rec_den(RecDev rd, int64_t t0, int64_t n_task, float *den)
 {
     __shared__ int s_d[kRecMoves];
     if (threadIdx.x < kRecMoves) s_d[threadIdx.x] = rd.delta[threadIdx.x];
@@ -182,24 +186,56 @@ __global__ void __launch_bounds__(256) k_rec_den(RecDev rd, int64_t t0, int64_t 
         const int64_t ray = p * rd.npix + pix;
         const int64_t c = pix < rd.npix ? (int64_t)__ldg(rd.cnt + ray) : 0;
         const int64_t b = min(a + ch, c);
-        int idx = b > a ? __ldg(rd.idx0 + (ray << lgP) + k) : 0;
-        const uint32_t *rp = rd.rec + r0 * 32 + lane;
-        for (int64_t s = a; s < b; ++s) {
-            const uint32_t v = __ldcs(rp + s * 32);
-            atomicAdd(den + idx, (double)rec_len(v));
-            idx += s_d[v & 7u];
+        if (b > a) {   // per lane; the warp takes its next item together
+            int idx = __ldg(rd.idx0 + (ray << lgP) + k);
+            const uint32_t *rp = rd.rec + r0 * 32 + lane;
+            int qc = -1;
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll 4
+            for (int64_t s = a; s < b; ++s) {
+                const uint32_t v = __ldcs(rp + s * 32);
+                const float len = rec_len(v);
+                const int qn = idx >> 2, sl = idx & 3;
+                const bool flush = qn != qc;
+                red_add4f_if(flush && qc >= 0, den + 4 * (qc < 0 ? 0 : qc), a0, a1, a2, a3);
+                a0 = (flush ? 0.f : a0) + (sl == 0 ? len : 0.f);
+                a1 = (flush ? 0.f : a1) + (sl == 1 ? len : 0.f);
+                a2 = (flush ? 0.f : a2) + (sl == 2 ? len : 0.f);
+                a3 = (flush ? 0.f : a3) + (sl == 3 ? len : 0.f);
+                qc = qn;
+                idx += s_d[v & 7u];
+            }
+            red_add4f_if(qc >= 0, den + 4 * (qc < 0 ? 0 : qc), a0, a1, a2, a3);
         }
+        __syncwarp();
     }
 }
 
-// r_m = 1 / max(den_m, eps) where den_m > 0, else 0 (the voxel keeps its value in Eq. 7);
-// den is cleared for the next subset.
-__global__ void k_rec_inv(int64_t n, double *den, float eps, float *r)
+// den64 += den32 (a view of a subset of several views)
+__global__ void k_rec_acc(int64_t n, const float *__restrict__ den32, double *__restrict__ den64)
 {
-    for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < n; m += (int64_t)gridDim.x * blockDim.x) {
-        const double d = den[m];
-        r[m] = d > 0.0 ? (float)(1.0 / fmax(d, (double)eps)) : 0.f;
-        den[m] = 0.0;
+    for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < n; m += (int64_t)gridDim.x * blockDim.x)
+        den64[m] += (double)__ldg(den32 + m);
+}
+
+__device__ __forceinline__ float rec_inv1(float d, float eps) { return d > 0.f ? 1.f / fmaxf(d, eps) : 0.f; }
+
+// r_m = 1 / max(den_m, eps) where den_m > 0, else 0 (the voxel keeps its value in Eq. 7),
+// four voxels per thread, from den32 (one view) or den64 (the subset's views added in
+// FP64, rounded to FP32 first: FP64 division is slow on this GPU, and r is FP32).  The
+// caller clears the sums afterwards.
+__global__ void k_rec_inv4(int64_t n4, const float4 *__restrict__ den32, const double2 *__restrict__ den64,
+                           float eps, float4 *__restrict__ r)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+        float4 d;
+        if (den64) {
+            const double2 a = __ldg(den64 + 2 * i), b = __ldg(den64 + 2 * i + 1);
+            d = make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
+        } else {
+            d = __ldg(den32 + i);
+        }
+        r[i] = make_float4(rec_inv1(d.x, eps), rec_inv1(d.y, eps), rec_inv1(d.z, eps), rec_inv1(d.w, eps));
     }
 }
 
@@ -326,12 +362,13 @@ __global__ void k_update_rec(int64_t n, float *num, const float *__restrict__ r,
     for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < n; m += (int64_t)gridDim.x * blockDim.x) {
         const float nv = num[m], rv = __ldg(r + m);
         num[m] = 0.f;
-        if (!(rv > 0.f)) continue;
-        float xv = u.strict16 ? as_f32<X>(x16[m]) : u.x32[m];
-        xv = fmaf(sc * weight_at(u, m), nv * rv, xv);
-        if (u.clamp) xv = fmaxf(xv, 0.f);
-        if (!u.strict16) u.x32[m] = xv;
-        if (x16) x16[m] = from_f32r<X>(xv);
+        if (rv > 0.f) {
+            float xv = u.strict16 ? as_f32<X>(x16[m]) : u.x32[m];
+            xv = fmaf(sc * weight_at(u, m), nv * rv, xv);
+            if (u.clamp) xv = fmaxf(xv, 0.f);
+            if (!u.strict16) u.x32[m] = xv;
+            if (x16) x16[m] = from_f32r<X>(xv);
+        }
     }
 }
 
@@ -348,18 +385,25 @@ static cudaError_t rec_dispatch(cyl_dtype t, F &&f)
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_rec_count(const ScanDev &sd, int n_proj, int lgP, uint32_t *cnt, int64_t *row_off,
-                             cudaStream_t st)
+cudaError_t launch_rec_rows(const ScanDev &sd, int n_proj, const uint32_t *cnt, int64_t *row_off, cudaStream_t st)
 {
-    const int64_t npix = (int64_t)sd.g.det_w * sd.g.det_h, n_rays = (int64_t)n_proj * npix;
+    const int64_t npix = (int64_t)sd.g.det_w * sd.g.det_h;
     const int64_t tpv = (npix + 31) >> 5, n_tasks = (int64_t)n_proj * tpv;
     if (n_tasks <= 0) return cudaSuccess;
-    const size_t smem = sizeof(float2) * (size_t)sd.g.n_t;
-    k_rec_walk<<<(unsigned)((n_rays + 255) / 256), 256, smem, st>>>(sd, n_rays, lgP, 0, cnt, nullptr, nullptr,
-                                                                     nullptr, nullptr);
     k_rec_rows<<<(unsigned)((n_tasks + 7) / 8), 256, 0, st>>>(cnt, npix, n_tasks, tpv, row_off);
     k_rec_scan<<<1, 1024, 0, st>>>(row_off, n_tasks);
     return cudaGetLastError();
+}
+
+cudaError_t launch_rec_count(const ScanDev &sd, int n_proj, int lgP, uint32_t *cnt, int64_t *row_off,
+                             cudaStream_t st)
+{
+    const int64_t n_rays = (int64_t)n_proj * sd.g.det_w * sd.g.det_h;
+    if (n_rays <= 0) return cudaSuccess;
+    const size_t smem = sizeof(float2) * (size_t)sd.g.n_t;
+    k_rec_walk<<<(unsigned)((n_rays + 255) / 256), 256, smem, st>>>(sd, n_rays, lgP, 0, cnt, nullptr, nullptr,
+                                                                     nullptr, nullptr);
+    return launch_rec_rows(sd, n_proj, cnt, row_off, st);
 }
 
 cudaError_t launch_rec_fill(const ScanDev &sd, int n_proj, int lgP, uint32_t *cnt, const int64_t *row_off,
@@ -416,15 +460,29 @@ cudaError_t launch_rec_sart(const RecDev &rd, int p0, int np, const void *x, cyl
     return cudaSuccess;
 }
 
-cudaError_t launch_rec_inv_den(const RecDev &rd, int p0, int np, int64_t n_vox, double *den, float *r,
-                               cudaStream_t st)
+cudaError_t launch_rec_inv_den(const RecDev &rd, int p0, int np, int64_t n_vox, float *den32, double *den64,
+                               float *r, cudaStream_t st)
 {
     if (np <= 0) return cudaSuccess;
-    const int64_t t0 = (int64_t)p0 * rd.tpv, n_task = (int64_t)np * rd.tpv;
-    const unsigned blocks = (unsigned)std::min<int64_t>(((n_task << rd.lgP) + 7) / 8, 152 * 8);
-    k_rec_den<<<blocks, 256, 0, st>>>(rd, t0, n_task, den);
-    k_rec_inv<<<(unsigned)std::min<int64_t>((n_vox + 255) / 256, 152 * 8), 256, 0, st>>>(n_vox, den, rd.eps, r);
-    return cudaGetLastError();
+    const int64_t n4 = (n_vox + 3) / 4;
+    const unsigned ve = (unsigned)std::min<int64_t>((n4 + 255) / 256, 152 * 8);
+    for (int v = 0; v < np; ++v) {
+        const int64_t t0 = (int64_t)(p0 + v) * rd.tpv;
+        const unsigned blocks = (unsigned)std::min<int64_t>(((rd.tpv << rd.lgP) + 7) / 8, 152 * 8);
+        k_rec_den<<<blocks, 256, 0, st>>>(rd, t0, rd.tpv, den32);
+        if (np > 1) {
+            k_rec_acc<<<ve, 256, 0, st>>>(n_vox, den32, den64);
+            const cudaError_t e = cudaMemsetAsync(den32, 0, sizeof(float) * 4 * n4, st);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    // r and the sums are padded to 4 ceil(V / 4) entries, the pad zero: its r entries are 0
+    k_rec_inv4<<<ve, 256, 0, st>>>(n4, reinterpret_cast<const float4 *>(den32),
+                                   np > 1 ? reinterpret_cast<const double2 *>(den64) : nullptr, rd.eps,
+                                   reinterpret_cast<float4 *>(r));
+    const cudaError_t e = np > 1 ? cudaMemsetAsync(den64, 0, sizeof(double) * 4 * n4, st)
+                                 : cudaMemsetAsync(den32, 0, sizeof(float) * 4 * n4, st);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_update_rec(int64_t n_vox, float *num, const float *r, const UpdateArgs &u, cudaStream_t st)
