@@ -116,12 +116,17 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def workload(rank: int = 0):
+def workload(rank: int = 0, views: int = 0):
     """The medium scan, its line integrals (analytic, of the continuous part with one insert
-    removed), the defect-free warm start and the ROI weights."""
+    removed), the defect-free warm start and the ROI weights.  views > 0: an evenly spaced
+    selection of that many of its views (a small case of the same grid and detector for
+    profiling captures)."""
+    import dataclasses
     from paper_2005_11976_gb300 import synth
     rng = synth.rng_for("medium", rank)
     scan = synth.medium_scan(rng)
+    if views > 0:
+        scan = dataclasses.replace(scan, angles=scan.angles[::max(1, scan.n_proj // views)][:views])
     az = synth.insert_azimuths(rng)
     removed = int(rng.integers(8))
     p_part = synth.part_line_integrals(scan, az, removed=removed)   # the scanned part
@@ -200,6 +205,9 @@ def main():
                     help="skip the bounded batched-vs-plain and served-vs-plain comparisons")
     ap.add_argument("--no-fused", action="store_true",
                     help="two launches per subset (projector, back-projector) instead of one")
+    ap.add_argument("--views", type=int, default=0,
+                    help="medium: run an evenly spaced selection of this many of the 180 views (a small "
+                         "case for profiling captures; the JSON line then describes that case)")
     ap.add_argument("--record-runs", type=int, default=0,
                     help="medium: runs per ray of the stored segment records (0: the library's default)")
     ap.add_argument("--no-records", action="store_true",
@@ -241,7 +249,7 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
 
-    scan, p_part, x_warm, w, removed = workload(rank)
+    scan, p_part, x_warm, w, removed = workload(rank, args.views)
     n_vox, n_pix = scan.n_vox, scan.det_w * scan.det_h
     plan = cylct.Plan(scan, device=local)
     pose = (scan.alpha, scan.beta, scan.gamma, scan.tx, scan.ty, scan.tz)
@@ -413,7 +421,7 @@ def main():
         import dataclasses
         import oracle
         oracle.build()
-        view = 37
+        view = min(37, scan.n_proj - 1)
         counts_v = oracle_view_counts(scan, p_part, view)
         oracle_sample(scan, x_warm, counts_v, w, view)          # warm-up (pages, threads)
         runs = [oracle_sample(scan, x_warm, counts_v, w, view) for _ in range(3)]
@@ -466,7 +474,9 @@ def main():
                        launch="one captured CUDA graph per sweep, CUDA events captured between its "
                               "kernels (kernel times: the last sweep of every timed step)" if not args.eager
                        else "eager, a CUDA event between launches",
-                       parallelism="replicas" if world > 1 else "single GPU"),
+                       parallelism="replicas" if world > 1 else "single GPU",
+                       **({"views": f"{scan.n_proj} evenly spaced of the 180 views (profiling case)"}
+                          if args.views else {})),
         "grays_per_s": grays, "rel_err_vs_oracle_one_subset": parity, "set_pose_ms": set_pose_ms,
         "segment_records": {"used": rec_ready, "bytes": rec_bytes,
                             "note": "each pose's pieces written once at set-up (inside every timed step) "
@@ -576,6 +586,20 @@ def batched_compare(torch, cylct, n, ids=None):
     e1.record()
     e1.synchronize()
     t_plain = e0.elapsed_time(e1) / 1e3
+    # plain with stored segment records: each scan writes its records and column sums, is
+    # solved, and frees them (all scans' records at once would not fit); the record
+    # set-up is inside the timed region
+    outs_r = [torch.empty(s.vol_shape, device=dev) for s in scans]
+    e0.record()
+    for i in range(n):
+        plans[i].cyl_plan_set_records(1)
+        plans[i].cyl_sart_solve(sinos[i], cylct.CYL_F32, x0, wd, prm, outs_r[i], cylct.CYL_F32)
+        plans[i].cyl_plan_set_records(0)
+    e1.record()
+    e1.synchronize()
+    t_rec = e0.elapsed_time(e1) / 1e3
+    err_rec = max(float((outs_r[i] - outs_p[i]).norm() / outs_p[i].norm()) for i in range(n))
+    del outs_r
     errs = [float((outs_b[i] - outs_p[i]).norm() / outs_p[i].norm()) for i in range(n)]
     err = max(errs)
     views = sum(s.n_proj for s in scans)
@@ -584,6 +608,8 @@ def batched_compare(torch, cylct, n, ids=None):
     return {"scans": n, "views": views, "per_scan_rel_err": errs, "batched_scans_per_s": n / t_batch, "plain_scans_per_s": n / t_plain,
             "batched_over_plain": t_plain / t_batch, "max_rel_err_batched_vs_plain": err,
             "batched_s": t_batch, "plain_s": t_plain,
+            "plain_records_scans_per_s": n / t_rec, "batched_over_plain_records": t_rec / t_batch,
+            "max_rel_err_plain_records_vs_plain": err_rec,
             "pieces_per_ray_tuned": {"projector": pieces[0], "back_projector": pieces[1]},
             "sart_iters_per_s_batched": n * 10 / t_batch,
             "grays_per_s_batched": 2 * 10 * views * scans[0].det_w * scans[0].det_h / t_batch / 1e9,
