@@ -283,7 +283,7 @@ k_rec_sart(RecDev rd, int64_t t0, int64_t n_task, const T *__restrict__ x, const
         float acc = 0.f, comp = 0.f;
 #pragma unroll 4
         for (int64_t s = a; s < b; ++s) {
-            const uint32_t v = __ldcs(rp + s * 32);
+            const uint32_t v = __ldg(rp + s * 32);
             const float yv = fmaf(rec_len(v), as_f32<T>(__ldg(x + idx)), -comp);
             const float t = acc + yv;
             comp = (t - acc) - yv;
@@ -299,13 +299,14 @@ k_rec_sart(RecDev rd, int64_t t0, int64_t n_task, const T *__restrict__ x, const
             const float L = __ldg(reinterpret_cast<const float *>(rd.ray_c + ray) + 2);
             const float yv =
                 L > 0.f ? (float)(((double)as_f32<S>(y[(p - p_first) * rd.npix + pix]) - q) / fmaxf(L, rd.eps)) : 0.f;
-            // backward: t_jl r_j into num, one reduction per visit of an aligned quad
+            // backward: t_jl r_j into num, one reduction per visit of an aligned quad; the
+            // run's records are read again, most of them from L1 or L2
             idx = start;
             int qc = -1;
             float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
 #pragma unroll 4
             for (int64_t s = a; s < b; ++s) {
-                const uint32_t v = __ldcs(rp + s * 32);
+                const uint32_t v = __ldg(rp + s * 32);
                 const float av = rec_len(v) * yv;
                 const int qn = idx >> 2, sl = idx & 3;
                 const bool flush = qn != qc;
