@@ -479,8 +479,10 @@ def main():
                           if args.views else {})),
         "grays_per_s": grays, "rel_err_vs_oracle_one_subset": parity, "set_pose_ms": set_pose_ms,
         "segment_records": {"used": rec_ready, "bytes": rec_bytes,
+                            "bytes_per_view": rec_bytes / scan.n_proj,
                             "note": "each pose's pieces written once at set-up (inside every timed step) "
-                                    "and replayed by the subsets"} if use_rec else {"used": False},
+                                    "and replayed by the subsets, read twice per subset (forward and back)"}
+                           if use_rec else {"used": False},
         "rel_err_bound": "<=1e-5 rel L2 per projection and per iterate (tests)",
         "wall_s_timed": t_wall, "clocks": clk, "gpu_launches": n_launch,
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
