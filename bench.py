@@ -208,6 +208,9 @@ def main():
     ap.add_argument("--views", type=int, default=0,
                     help="medium: run an evenly spaced selection of this many of the 180 views (a small "
                          "case for profiling captures; the JSON line then describes that case)")
+    ap.add_argument("--record-form", type=int, default=1, choices=[1, 2],
+                    help="medium: 1 back-projects by gathering per voxel from the records' transpose, "
+                         "2 by replaying the records into a numerator")
     ap.add_argument("--record-runs", type=int, default=0,
                     help="medium: runs per ray of the stored segment records (0: the library's default)")
     ap.add_argument("--no-records", action="store_true",
@@ -271,8 +274,8 @@ def main():
     plan.cyl_plan_set_fused(not args.no_fused)
     use_rec = not args.no_records and not args.no_fused
     if use_rec:
-        plan.cyl_plan_set_records(1, args.record_runs, stream)
-    rec_ready, rec_bytes = plan.cyl_plan_records()
+        plan.cyl_plan_set_records(args.record_form, args.record_runs, stream)
+    rec_ready, rec_bytes, rec_gather, gather_bytes = plan.cyl_plan_records_full()
 
     def step(st):
         plan.cyl_plan_set_pose(pose, st)
@@ -372,6 +375,10 @@ def main():
             names = ["forward projection (k_fp)", "back-projection into (num, den) (k_bp)",
                      "SART voxel update (k_update_nd4)"]
             per = [fwd, back, upd]
+        elif rec_ready and rec_gather:
+            names = ["projection and residual from the stored segment records (k_rec_sart, forward replay)",
+                     None, "back-projection gathered per voxel with its column sums and the update (k_vox_sart)"]
+            per = [fwd, 0.0, back + upd]
         elif rec_ready:
             names = ["projection, residual and back-projection from the stored segment records (k_rec_sart)",
                      None, "SART voxel update with the pose's column sums (k_update_rec4)"]
@@ -461,11 +468,13 @@ def main():
             r = serving_compare(torch, cylct, 24, rate, 60.0, ("small", "medium"))
             serving[key] = {k: v for k, v in r.items() if k not in ("latencies_s", "plain_latencies_s")}
 
-    # per step: ray records + cuts (set_pose; with segment records also their rows, scan
-    # and record walk, and the pose's column sums, two launches per view), log, weight
-    # max + scale, and per subset the projector, the back-projector and the update
-    n_launch = args.steps * (2 + (3 + 2 * scan.n_proj if rec_ready else 0) + 1 + 2
-                             + N_ITER * scan.n_proj * (3 if args.no_fused else 2))
+    # per step: ray records + cuts (set_pose, with the segment records' launches), log,
+    # weight max + scale, and per subset the projector, the back-projector and the update
+    per_pose = 0
+    if rec_ready:   # rows, scan, record walk; then the transpose (count, three scan passes,
+        # base, fill per view) or the column sums (two per view)
+        per_pose = 3 + (6 * scan.n_proj if rec_gather else 2 * scan.n_proj)
+    n_launch = args.steps * (2 + per_pose + 1 + 2 + N_ITER * scan.n_proj * (3 if args.no_fused else 2))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -480,6 +489,7 @@ def main():
         "grays_per_s": grays, "rel_err_vs_oracle_one_subset": parity, "set_pose_ms": set_pose_ms,
         "segment_records": {"used": rec_ready, "bytes": rec_bytes,
                             "bytes_per_view": rec_bytes / scan.n_proj,
+                            "gather_per_voxel": rec_gather, "transpose_bytes": gather_bytes,
                             "note": "each pose's pieces written once at set-up (inside every timed step) "
                                     "and replayed by the subsets, read twice per subset (forward and back)"}
                            if use_rec else {"used": False},

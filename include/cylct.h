@@ -345,23 +345,37 @@ int cyl_plan_set_fused(cyl_plan *plan, int32_t enable);
 int cyl_plan_set_sart_pieces(cyl_plan *plan, int32_t pieces);
 /* Stored segment records (Eq. 6: each ray's row of the system matrix, t_jl and voxel l of
  * every piece).  Every subset of Eq. 7 needs each of its rays' rows twice, for q_j and
- * for the back-projection of r_j, and the rows depend only on the pose.  enable = 1: at
- * this call and at every later cyl_plan_set_pose, each ray is walked once and its pieces
- * are written as 4-byte records (the FP32 length rounded to 20 mantissa bits, relative
- * error <= 2^-21, with the move to the next piece's voxel in the low 3 bits); the
- * one-launch subsets of cyl_sart_solve then replay the records instead of walking each
- * ray twice.  runs (0: the default, 8; else 1, 2, 4, 8, 16 or 32) cuts each ray's pieces
- * into that many runs of consecutive pieces, replayed by as many lanes.  The records take
- * about 4 bytes per piece of the whole scan (about 16 GB for 180 views of a 256 x 256
- * detector through a (128, 512, 128) grid); they are kept only where they fit within
- * 40 % of the device with 1 GiB free beside them, and otherwise the subsets walk the
- * rays (cyl_plan_records reports which).  Dense plans only (compact plans walk); the
+ * for the back-projection of r_j, and the rows depend only on the pose.  enable = 1 or
+ * 2: at this call and at every later cyl_plan_set_pose, each ray is walked once and its
+ * pieces are written as 4-byte records (the FP32 length rounded to 20 mantissa bits,
+ * relative error <= 2^-21, with the move to the next piece's voxel in the low 3 bits);
+ * the one-launch subsets of cyl_sart_solve then replay the records instead of walking
+ * each ray twice.
+ *   enable = 1: the records are also transposed (per view and voxel, the pixel and
+ *     length of every piece that crosses the voxel), and a subset is the records'
+ *     forward replay for the residuals, then one pass over the voxels that gathers the
+ *     back-projection and the column sums of Eq. 7 and updates x, without atomics.
+ *     Where the transpose does not fit, as for enable = 2.
+ *   enable = 2: the back-projection replays the records again into a numerator, with
+ *     the column sums summed once per pose and subset size.
+ * runs (0: the default, 8; else 1, 2, 4, 8, 16 or 32) cuts each ray's pieces into that
+ * many runs of consecutive pieces, replayed side by side by as many warps.  The records
+ * take about 4 bytes per piece of the whole scan (about 16 GB for 180 views of a
+ * 256 x 256 detector through a (128, 512, 128) grid), the transpose about 8 bytes per
+ * piece and 4 per voxel and view (about 33 GB there), the column sums of enable = 2 4
+ * bytes per voxel and subset; the records are kept only where they fit within 40 % of
+ * the device, the transpose where records and transpose fit within half of it, each
+ * with 1 GiB free beside them, and otherwise the subsets walk the rays
+ * (cyl_plan_records reports which).  Dense plans only (compact plans walk); the
  * two-launch form (cyl_plan_set_fused(0)), the projector and the back-projector always
- * walk.  enable = 0 (the default) frees them.  Synchronises `stream`.  Errors: CYL_EINVAL
- * (null plan, enable not 0 or 1, runs not as above), CYL_EDEVICE. */
+ * walk.  enable = 0 (the default) frees them.  Synchronises `stream`.  Errors:
+ * CYL_EINVAL (null plan, enable not 0, 1 or 2, runs not as above), CYL_EDEVICE. */
 int cyl_plan_set_records(cyl_plan *plan, int32_t enable, int32_t runs, void *stream);
-/* ready = 1 if the plan holds the records of its current pose; rec_bytes their size. */
-int cyl_plan_records(const cyl_plan *plan, int32_t *ready, int64_t *rec_bytes);
+/* ready = 1 if the plan holds the records of its current pose, rec_bytes their size;
+ * gather = 1 if it also holds their transpose (the gather form), gather_bytes its size.
+ * Any output may be null. */
+int cyl_plan_records(const cyl_plan *plan, int32_t *ready, int64_t *rec_bytes, int32_t *gather,
+                     int64_t *gather_bytes);
 int cyl_plan_set_pieces(cyl_plan *plan, int32_t fp_pieces, int32_t bp_pieces);
 int cyl_plan_get_pieces(const cyl_plan *plan, int32_t *fp_pieces, int32_t *bp_pieces);
 

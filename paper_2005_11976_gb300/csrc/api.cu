@@ -275,7 +275,7 @@ extern "C" int cyl_plan_set_sart_pieces(cyl_plan *plan, int32_t pieces)
 extern "C" int cyl_plan_set_records(cyl_plan *plan, int32_t enable, int32_t runs, void *stream)
 {
     if (!plan) return set_error(CYL_EINVAL, "plan is null");
-    if (enable != 0 && enable != 1) return set_error(CYL_EINVAL, "enable must be 0 or 1");
+    if (enable < 0 || enable > 2) return set_error(CYL_EINVAL, "enable must be 0, 1 or 2");
     int lg = 0;
     while (lg < 5 && (1 << lg) < runs) ++lg;
     if (runs != 0 && (runs < 0 || (1 << lg) != runs)) return set_error(CYL_EINVAL, "runs must be 0, 1, 2, 4, 8, 16 or 32");
@@ -296,11 +296,17 @@ extern "C" int cyl_plan_set_records(cyl_plan *plan, int32_t enable, int32_t runs
     return CYL_OK;
 }
 
-extern "C" int cyl_plan_records(const cyl_plan *plan, int32_t *ready, int64_t *rec_bytes)
+extern "C" int cyl_plan_records(const cyl_plan *plan, int32_t *ready, int64_t *rec_bytes, int32_t *gather,
+                                int64_t *gather_bytes)
 {
     if (!plan) return set_error(CYL_EINVAL, "plan is null");
     if (ready) *ready = plan->rec_ready ? 1 : 0;
     if (rec_bytes) *rec_bytes = plan->rec_ready ? plan->rec_rows * 32 * (int64_t)sizeof(uint32_t) : 0;
+    if (gather) *gather = plan->vox_ready ? 1 : 0;
+    if (gather_bytes)
+        *gather_bytes = plan->vox_ready ? plan->vox_entries * (int64_t)sizeof(uint2) +
+                                              (plan->n_vox + 1) * plan->geom.n_proj * (int64_t)sizeof(uint32_t)
+                                        : 0;
     return CYL_OK;
 }
 

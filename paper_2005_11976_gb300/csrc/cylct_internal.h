@@ -79,6 +79,16 @@ struct RecDev {
     float eps;                // floor of Eq. 7's sums
 };
 
+// Transpose of a pose's records (gather.cu): per view and voxel, the (pixel, length) of
+// every piece that crosses the voxel, for the back-projection by gathering per voxel.
+struct VoxDev {
+    const uint2 *ent;         // entries (pixel, FP32 length bits), view after view
+    const int64_t *ebase;     // [n_proj + 1]: first entry of each view
+    const uint32_t *off;      // [view][V + 1]: each voxel's first entry within its view
+    int64_t n_vox, npix;
+    float eps;                // floor of Eq. 7's sums
+};
+
 // SART update of one subset (Eq. 7): x += scale * w * num / den where den > 0.
 struct UpdateArgs {
     float *x32;             // FP32 iterate (null in strict 16-bit mode)
@@ -172,9 +182,11 @@ RecDev rec_dev(const ScanDev &sd, int lgP, const uint32_t *rec, const int64_t *r
                const int32_t *idx0);
 // One SART subset of views p0 .. p0+np-1 from the records: the projections, the residuals
 // against y and their back-projection into num (the numerator of Eq. 7, 4 ceil(V / 4)
-// floats, 16-byte aligned).  sched: two ints of scheduler state, zero at rest.
+// floats, 16-byte aligned); with resid (np x H x W floats) instead, the residuals are
+// written there and nothing is back-projected.  sched: two ints of scheduler state, zero
+// at rest.
 cudaError_t launch_rec_sart(const RecDev &rd, int p0, int np, const void *x, cyl_dtype xt, const void *y,
-                            cyl_dtype yt, float *num, int *sched, cudaStream_t st);
+                            cyl_dtype yt, float *num, float *resid, int *sched, cudaStream_t st);
 // The reciprocal column sums r (4 ceil(V / 4) floats, 16-byte aligned) of the subset of
 // views p0 .. p0+np-1 (Eq. 7's normalisation): each view's sums in FP32 into den32
 // (4 ceil(V / 4) floats), added across the subset's views in FP64 into den64 (as many
@@ -183,6 +195,18 @@ cudaError_t launch_rec_inv_den(const RecDev &rd, int p0, int np, int64_t n_vox, 
                                float *r, cudaStream_t st);
 // x += s w num r, num cleared.
 cudaError_t launch_update_rec(int64_t n_vox, float *num, const float *r, const UpdateArgs &u, cudaStream_t st);
+// Transpose (gather.cu), per pose: count the pieces of every voxel of every view and scan
+// them into off ([view][V + 1]) and ebase ([n_proj + 1]; cnt: V, tsum: ceil(V / 2048)
+// scratch); then, with ent sized for ebase[n_proj] entries (h_ebase: ebase on the host),
+// fill the entries (cur: V scratch).
+cudaError_t launch_vox_count(const RecDev &rd, int n_proj, int64_t n_vox, uint32_t *cnt, uint32_t *off,
+                             uint32_t *tsum, int64_t *ebase, cudaStream_t st);
+cudaError_t launch_vox_fill(const RecDev &rd, int n_proj, int64_t n_vox, const uint32_t *off, const int64_t *h_ebase,
+                            uint32_t *cur, uint2 *ent, cudaStream_t st);
+// Eq. 7 for the subset of views p0 .. p0+np-1 by gathering per voxel over the subset's
+// residuals resid ([np][H][W]): back-projection, column sums and update in one pass.
+cudaError_t launch_vox_sart(const VoxDev &vd, int p0, int np, const float *resid, const UpdateArgs &u,
+                            cudaStream_t st);
 cudaError_t launch_count_rays(const ScanDev &sd, int p0, int np, unsigned long long *counts,
                               cudaStream_t st,
                               const RayList &rl = RayList{nullptr, nullptr});

@@ -165,8 +165,21 @@ void cyl_plan::release(void **p, size_t &cap)
     drop_graphs();
 }
 
+void cyl_plan::free_gather()
+{
+    release((void **)&d_vent, vent_cap);
+    release((void **)&d_voff, voff_cap);
+    release((void **)&d_vcnt, vcnt_cap);
+    release((void **)&d_vcur, vcur_cap);
+    release((void **)&d_vtsum, vtsum_cap);
+    release((void **)&d_vebase, vebase_cap);
+    vox_ready = false;
+    vox_entries = 0;
+}
+
 void cyl_plan::free_records()
 {
+    free_gather();
     release((void **)&d_rinv, rinv_cap);
     release((void **)&d_den64, den64_cap);
     release((void **)&d_den32, den32_cap);
@@ -185,11 +198,14 @@ int cyl_plan::build_records(cudaStream_t st, bool counted)
 {
     // captured sweeps launch the record kernels with the buffers' addresses: they stay
     // valid while the records do (a reallocation drops them in ensure)
-    const bool was = rec_ready;
+    const bool was = rec_ready, was_vox = vox_ready;
     rec_ready = false;
+    vox_ready = false;
     rinv_sub = 0;             // the column sums belong to the pose
-    const int rc = write_records(st, counted);
-    if (rec_ready != was) drop_graphs();
+    int rc = write_records(st, counted);
+    if (!rc && rec_ready && rec_mode == 1) rc = build_gather(st);
+    else if (rec_mode != 1) free_gather();
+    if (rec_ready != was || vox_ready != was_vox) drop_graphs();
     return rc;
 }
 
@@ -231,10 +247,54 @@ int cyl_plan::write_records(cudaStream_t st, bool counted)
     return CYL_OK;
 }
 
-bool cyl_plan::prepare_records(int subset, cudaStream_t st, int &rc)
+int cyl_plan::build_gather(cudaStream_t st)
+{
+    const int64_t nt = (n_vox + 2047) / 2048;
+    const size_t off_bytes = sizeof(uint32_t) * (size_t)(n_vox + 1) * geom.n_proj;
+    size_t fr = 0, tot = 0;
+    PL_CUDA(cudaMemGetInfo(&fr, &tot));
+    // the transpose takes about twice the records: keep records and transpose within half
+    // of the device with 1 GiB free; otherwise the subsets replay with reductions
+    const size_t recb = (size_t)rec_rows * 128;
+    if (off_bytes > voff_cap && (off_bytes + ((size_t)1 << 30) > fr + voff_cap || recb + off_bytes > tot / 2)) {
+        free_gather();
+        return CYL_OK;
+    }
+    int rc;
+    if ((rc = ensure((void **)&d_voff, voff_cap, off_bytes))) return rc;
+    if ((rc = ensure((void **)&d_vcnt, vcnt_cap, sizeof(uint32_t) * n_vox))) return rc;
+    if ((rc = ensure((void **)&d_vcur, vcur_cap, sizeof(uint32_t) * n_vox))) return rc;
+    if ((rc = ensure((void **)&d_vtsum, vtsum_cap, sizeof(uint32_t) * nt))) return rc;
+    if ((rc = ensure((void **)&d_vebase, vebase_cap, sizeof(int64_t) * (geom.n_proj + 1)))) return rc;
+    const RecDev rd = rec_dev();
+    PL_CUDA(launch_vox_count(rd, geom.n_proj, n_vox, d_vcnt, d_voff, d_vtsum, d_vebase, st));
+    std::vector<int64_t> eb(geom.n_proj + 1);
+    PL_CUDA(cudaMemcpyAsync(eb.data(), d_vebase, sizeof(int64_t) * eb.size(), cudaMemcpyDeviceToHost, st));
+    PL_CUDA(cudaStreamSynchronize(st));
+    const int64_t total = eb[geom.n_proj];
+    const size_t ent_bytes = sizeof(uint2) * (size_t)std::max<int64_t>(total, 1);
+    if (ent_bytes > vent_cap) {
+        PL_CUDA(cudaMemGetInfo(&fr, &tot));
+        if (ent_bytes + ((size_t)1 << 30) > fr + vent_cap || recb + off_bytes + ent_bytes > tot / 2) {
+            free_gather();
+            return CYL_OK;
+        }
+        if (ensure((void **)&d_vent, vent_cap, ent_bytes + ent_bytes / 16)) {
+            free_gather();
+            return CYL_OK;
+        }
+    }
+    PL_CUDA(launch_vox_fill(rd, geom.n_proj, n_vox, d_voff, eb.data(), d_vcur, d_vent, st));
+    vox_entries = total;
+    vox_ready = true;
+    return CYL_OK;
+}
+
+int cyl_plan::prepare_records(int subset, cudaStream_t st, int &rc)
 {
     rc = CYL_OK;
-    if (!rec_ready) return false;
+    if (!rec_ready) return 0;
+    if (vox_ready) return 2;   // the gather form needs no column sums of its own
     const int n_sub = (geom.n_proj + subset - 1) / subset;
     const size_t nv4 = (size_t)((n_vox + 3) / 4) * 4;
     if (rinv_sub != subset) {
@@ -243,21 +303,21 @@ bool cyl_plan::prepare_records(int subset, cudaStream_t st, int &rc)
             size_t fr = 0, tot = 0;
             if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
                 cudaGetLastError();
-                return false;
+                return 0;
             }
-            if (want + ((size_t)1 << 30) > fr + rinv_cap) return false;   // walk instead
+            if (want + ((size_t)1 << 30) > fr + rinv_cap) return 0;   // walk instead
         }
-        if (ensure((void **)&d_rinv, rinv_cap, want)) return false;
-        if ((rc = ensure((void **)&d_den32, den32_cap, sizeof(float) * nv4))) return false;
+        if (ensure((void **)&d_rinv, rinv_cap, want)) return 0;
+        if ((rc = ensure((void **)&d_den32, den32_cap, sizeof(float) * nv4))) return 0;
         if (cudaMemsetAsync(d_den32, 0, sizeof(float) * nv4, st) != cudaSuccess) {
             rc = cuda_error(cudaGetLastError(), "cudaMemsetAsync");
-            return false;
+            return 0;
         }
         if (subset > 1) {
-            if ((rc = ensure((void **)&d_den64, den64_cap, sizeof(double) * nv4))) return false;
+            if ((rc = ensure((void **)&d_den64, den64_cap, sizeof(double) * nv4))) return 0;
             if (cudaMemsetAsync(d_den64, 0, sizeof(double) * nv4, st) != cudaSuccess) {
                 rc = cuda_error(cudaGetLastError(), "cudaMemsetAsync");
-                return false;
+                return 0;
             }
         }
         const RecDev rd = rec_dev();
@@ -267,17 +327,17 @@ bool cyl_plan::prepare_records(int subset, cudaStream_t st, int &rc)
                 launch_rec_inv_den(rd, p0, np, n_vox, d_den32, d_den64, d_rinv + (size_t)k * nv4, st);
             if (e != cudaSuccess) {
                 rc = cuda_error(e, "launch_rec_inv_den");
-                return false;
+                return 0;
             }
         }
         rinv_sub = subset;
     }
-    if ((rc = ensure((void **)&d_num, num_cap, sizeof(float) * nv4))) return false;
+    if ((rc = ensure((void **)&d_num, num_cap, sizeof(float) * nv4))) return 0;
     if (cudaMemsetAsync(d_num, 0, sizeof(float) * nv4, st) != cudaSuccess) {
         rc = cuda_error(cudaGetLastError(), "cudaMemsetAsync");
-        return false;
+        return 0;
     }
-    return true;
+    return 1;
 }
 
 cudaEvent_t *cyl_plan::next_events(int n)
@@ -337,11 +397,22 @@ int cyl_plan::queue_sweep(const SolveState &s, cudaStream_t st, bool timed, int 
         cudaEvent_t *ev = timed ? next_events(4) : nullptr;
         if (timed && !ev) return set_error(CYL_EDEVICE, "event creation failed");
         if (ev) PL_CUDA(cudaEventRecordWithFlags(ev[0], st, rec_flags));
-        if (s.rec) {
+        if (s.rec == 2) {
+            // the records' forward replay writes the residuals; one pass over the voxels
+            // gathers their back-projection and column sums and updates x
+            PL_CUDA(launch_rec_sart(rec_dev(), p0, np, s.x_proj, s.x_proj_t, sino_p, s.sino_t, nullptr, d_q,
+                                    d_sched + 8, st));
+            if (ev) PL_CUDA(cudaEventRecordWithFlags(ev[1], st, rec_flags));
+            if (ev) PL_CUDA(cudaEventRecordWithFlags(ev[2], st, rec_flags));
+            PL_CUDA(launch_vox_sart(vox_dev(), p0, np, d_q, upd, st));
+            if (ev) PL_CUDA(cudaEventRecordWithFlags(ev[3], st, rec_flags));
+            continue;
+        }
+        if (s.rec == 1) {
             // the same subset replaying the pose's stored records into the numerator; the
             // update divides by the pose's column sums
-            PL_CUDA(launch_rec_sart(rec_dev(), p0, np, s.x_proj, s.x_proj_t, sino_p, s.sino_t, d_num, d_sched + 8,
-                                    st));
+            PL_CUDA(launch_rec_sart(rec_dev(), p0, np, s.x_proj, s.x_proj_t, sino_p, s.sino_t, d_num, nullptr,
+                                    d_sched + 8, st));
             if (ev) PL_CUDA(cudaEventRecordWithFlags(ev[1], st, rec_flags));
             if (ev) PL_CUDA(cudaEventRecordWithFlags(ev[2], st, rec_flags));
             PL_CUDA(launch_update_rec(n_vox, d_num, d_rinv + (size_t)k * (((size_t)n_vox + 3) / 4 * 4), upd, st));
@@ -439,7 +510,7 @@ int cyl_plan::solve(const void *sino, cyl_dtype sino_t, const void *x0, const vo
         PL_CUDA(launch_convert(d_xo, x_t, d_x32, CYL_F32, n_vox, ws));
     }
     if (d_w) PL_CUDA(launch_weight_scale(d_w, w_t, n_vox, prm.weight_mode, (float)prm.lambda, d_wscale, ws));
-    s.rec = fused && prepare_records(subset, ws, rc) ? 1 : 0;
+    s.rec = fused ? prepare_records(subset, ws, rc) : 0;
     if (rc) return rc;
     if (!s.rec)
         for (int k = 0; k < 2; ++k) PL_CUDA(cudaMemsetAsync(d_nd[k], 0, sizeof(float2) * n_vox, ws));

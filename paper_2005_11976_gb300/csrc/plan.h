@@ -40,7 +40,7 @@ struct SolveState {
     double lambda = 0.5;
     int clamp = 0;
     int subset = 1;
-    int rec = 0;                   // subsets replay the pose's stored records
+    int rec = 0;                   // subsets replay the pose's stored records (1) and gather per voxel (2)
 
     bool operator==(const SolveState &o) const
     {
@@ -147,6 +147,15 @@ struct cyl_plan {
     double *d_den64 = nullptr;
     size_t num_cap = 0, rinv_cap = 0, den32_cap = 0, den64_cap = 0;
     int rinv_sub = 0;
+    // The records' transpose (gather.cu; rec_mode 1, where it fits): per view and voxel the
+    // pieces that cross the voxel, so that the subsets back-project by gathering per voxel
+    // (vox_ready).  off [view][V + 1], ent (pixel, length) view after view, ebase per view.
+    bool vox_ready = false;
+    uint32_t *d_voff = nullptr, *d_vcnt = nullptr, *d_vcur = nullptr, *d_vtsum = nullptr;
+    uint2 *d_vent = nullptr;
+    int64_t *d_vebase = nullptr;
+    size_t voff_cap = 0, vcnt_cap = 0, vcur_cap = 0, vtsum_cap = 0, vent_cap = 0, vebase_cap = 0;
+    int64_t vox_entries = 0;
     float *d_x32 = nullptr;
     size_t x32_cap = 0;
     void *d_stage[4] = {nullptr, nullptr, nullptr, nullptr};  // sino, x0, w, x_out
@@ -189,6 +198,10 @@ struct cyl_plan {
     }
     cylct::RayList ray_list() const { return cylct::RayList{use_list ? d_act : nullptr, d_act_off}; }
     cylct::RecDev rec_dev() const { return cylct::rec_dev(scan_dev(), rec_lgP, d_rec, d_rrow, d_rcnt, d_ridx0); }
+    cylct::VoxDev vox_dev() const
+    {
+        return cylct::VoxDev{d_vent, d_vebase, d_voff, n_vox, n_pix, g.eps};
+    }
 
     template <class T> int alloc(T **p, size_t nbytes)
     {
@@ -213,8 +226,12 @@ struct cyl_plan {
     int build_records(cudaStream_t st, bool counted = false);   // counted: d_rcnt holds the pose's counts
     int write_records(cudaStream_t st, bool counted);
     void free_records();
-    // Record buffers of a solve with subsets of `subset` views; false: walk instead.
-    bool prepare_records(int subset, cudaStream_t st, int &rc);
+    // The records' transpose for the gather form (rec_mode 1); vox_ready tells whether it fits.
+    int build_gather(cudaStream_t st);
+    void free_gather();
+    // Record buffers of a solve with subsets of `subset` views: 0 walk, 1 replay with the
+    // pose's reciprocal column sums, 2 gather per voxel.
+    int prepare_records(int subset, cudaStream_t st, int &rc);
     cudaEvent_t *next_events(int n);
     // Queue one sweep; `parity` is the subset counter's parity at its first subset.
     int queue_sweep(const cylct::SolveState &s, cudaStream_t st, bool timed, int parity);

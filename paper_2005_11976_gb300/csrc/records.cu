@@ -27,39 +27,9 @@
 #include <algorithm>
 #include <type_traits>
 
-#include "device_common.cuh"
+#include "records.cuh"
 
 namespace cylct {
-
-// voxel index change of each move code (codes whose changes coincide on a small grid are
-// interchangeable: a replay only adds the change)
-__host__ __device__ inline void move_deltas(int n_t, int n_r, int d[kRecMoves])
-{
-    const int st = n_r, sh = n_t * n_r, wrap = (n_t - 1) * n_r;
-    d[0] = 1;       // shell +1
-    d[1] = -1;      // shell -1
-    d[2] = st;      // wedge +1
-    d[3] = -st;     // wedge -1
-    d[4] = -wrap;   // wedge N_theta - 1 -> 0
-    d[5] = wrap;    // wedge 0 -> N_theta - 1
-    d[6] = sh;      // slab +1
-    d[7] = -sh;     // slab -1
-}
-
-__device__ __forceinline__ uint32_t move_code(int dd, const int d[kRecMoves])
-{
-    uint32_t c = kRecMoves - 1;
-#pragma unroll
-    for (int k = kRecMoves - 2; k >= 0; --k) c = dd == d[k] ? (uint32_t)k : c;
-    return c;
-}
-
-__device__ __forceinline__ uint32_t rec_encode(float len, uint32_t code)
-{
-    return ((__float_as_uint(len) + 4u) & ~7u) | code;   // round to 20 mantissa bits
-}
-
-__device__ __forceinline__ float rec_len(uint32_t v) { return __uint_as_float(v & ~7u); }
 
 // mode 0: count the steps of every ray into cnt.  mode 1: write the records at their
 // task's rows (row s, lane pixel % 32) and, for every run of ch = ceil(rows / P) rows of
@@ -157,13 +127,6 @@ __global__ void __launch_bounds__(1024) k_rec_scan(int64_t *v, int64_t n)
     }
 }
 
-__device__ __forceinline__ void red_add4f_if(bool c, float *p, float a, float b, float d, float e)
-{
-    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %5, 0;\n\t"
-                 "@q red.global.add.v4.f32 [%0], {%1, %2, %3, %4};\n\t}"
-                 ::"l"(p), "f"(a), "f"(b), "f"(d), "f"(e), "r"((unsigned)c) : "memory");
-}
-
 // Column sums of Eq. 7 over one view (tasks [t0, t0 + n_task)): den_m = sum_j t_jm.  One
 // warp per run of a task, as the subsets replay them: the 32 rays side by side, the
 // pieces of a lane that fall in one aligned quad of voxels going out as one 4 x FP32
@@ -249,10 +212,12 @@ __global__ void k_rec_inv4(int64_t n4, const float4 *__restrict__ den32, const d
 // aligned quad of voxels go out as one 4 x FP32 reduction.  y holds the launch's views
 // from the first task's view on.  sched[0] hands out tasks to blocks; sched[1] counts
 // the blocks that found none left, and the last resets both.
-template <class T, class S>
+// Without BACK (the gather path, gather.cu) the kernel stops after the forward replay and
+// writes each ray's residual r_j to resid (the launch's views from the first one on).
+template <class T, class S, bool BACK>
 __global__ void __launch_bounds__(1024)
 k_rec_sart(RecDev rd, int64_t t0, int64_t n_task, const T *__restrict__ x, const S *__restrict__ y, float *num,
-           int *sched)
+           float *resid, int *sched)
 {
     extern __shared__ double s_q[];          // [P][32] run sums
     __shared__ int s_d[kRecMoves];
@@ -295,7 +260,12 @@ k_rec_sart(RecDev rd, int64_t t0, int64_t n_task, const T *__restrict__ x, const
         __syncthreads();
         double q = 0.0;
         for (int j = 0; j < P; ++j) q += s_q[j * 32 + lane];
-        if (b > a) {   // per lane; every lane of the block reaches the next fetch's barrier
+        if (!BACK && k == 0 && c > 0) {   // the gather path back-projects per voxel
+            const float L = __ldg(reinterpret_cast<const float *>(rd.ray_c + ray) + 2);
+            resid[(p - p_first) * rd.npix + pix] =
+                L > 0.f ? (float)(((double)as_f32<S>(y[(p - p_first) * rd.npix + pix]) - q) / fmaxf(L, rd.eps)) : 0.f;
+        }
+        if (BACK && b > a) {   // per lane; every lane of the block reaches the next fetch's barrier
             const float L = __ldg(reinterpret_cast<const float *>(rd.ray_c + ray) + 2);
             const float yv =
                 L > 0.f ? (float)(((double)as_f32<S>(y[(p - p_first) * rd.npix + pix]) - q) / fmaxf(L, rd.eps)) : 0.f;
@@ -436,7 +406,7 @@ RecDev rec_dev(const ScanDev &sd, int lgP, const uint32_t *rec, const int64_t *r
 }
 
 cudaError_t launch_rec_sart(const RecDev &rd, int p0, int np, const void *x, cyl_dtype xt, const void *y,
-                            cyl_dtype yt, float *num, int *sched, cudaStream_t st)
+                            cyl_dtype yt, float *num, float *resid, int *sched, cudaStream_t st)
 {
     if (np <= 0) return cudaSuccess;
     // a launch counts its fetches in 32 bits
@@ -451,9 +421,13 @@ cudaError_t launch_rec_sart(const RecDev &rd, int p0, int np, const void *x, cyl
                 const S *yc = static_cast<const S *>(y) + (int64_t)c0 * rd.npix;
                 const int threads = 32 << rd.lgP;
                 const size_t smem = sizeof(double) * (size_t)threads;
-                const unsigned blocks = persistent_blocks((const void *)k_rec_sart<T, S>, smem, 0, threads);
-                k_rec_sart<T, S><<<blocks, threads, smem, st>>>(rd, t0, n_task, (const T *)x, yc, num, sched);
-                return cudaGetLastError();
+                float *rc = resid ? resid + (int64_t)c0 * rd.npix : nullptr;
+                auto go = [&](auto kern) {
+                    const unsigned blocks = persistent_blocks((const void *)kern, smem, 0, threads);
+                    kern<<<blocks, threads, smem, st>>>(rd, t0, n_task, (const T *)x, yc, num, rc, sched);
+                    return cudaGetLastError();
+                };
+                return resid ? go(k_rec_sart<T, S, false>) : go(k_rec_sart<T, S, true>);
             });
         });
         if (e != cudaSuccess) return e;

@@ -130,7 +130,8 @@ SIGNATURES = {
     "cyl_plan_set_fused": (ctypes.c_int, [_VP, _I32]),
     "cyl_plan_set_sart_pieces": (ctypes.c_int, [_VP, _I32]),
     "cyl_plan_set_records": (ctypes.c_int, [_VP, _I32, _I32, _VP]),
-    "cyl_plan_records": (ctypes.c_int, [_VP, ctypes.POINTER(_I32), ctypes.POINTER(_I64)]),
+    "cyl_plan_records": (ctypes.c_int, [_VP, ctypes.POINTER(_I32), ctypes.POINTER(_I64), ctypes.POINTER(_I32),
+                                        ctypes.POINTER(_I64)]),
     "cyl_binary_version": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_I32)]),
     "cyl_project_noalloc": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _I32, _I32, _VP, ctypes.c_int, _VP]),
     "cyl_backproject": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _I32, _I32, _VP, _VP, _VP]),
@@ -354,9 +355,14 @@ class Plan:
 
     def cyl_plan_records(self):
         """(ready, bytes) of the plan's stored segment records."""
-        r, b = _I32(), _I64()
-        _check(load().cyl_plan_records(self.h, ctypes.byref(r), ctypes.byref(b)), "cyl_plan_records")
-        return bool(r.value), b.value
+        return self.cyl_plan_records_full()[:2]
+
+    def cyl_plan_records_full(self):
+        """(ready, record bytes, gather form, transpose bytes) of the plan's stored records."""
+        r, b, g, gb = _I32(), _I64(), _I32(), _I64()
+        _check(load().cyl_plan_records(self.h, ctypes.byref(r), ctypes.byref(b), ctypes.byref(g),
+                                       ctypes.byref(gb)), "cyl_plan_records")
+        return bool(r.value), b.value, bool(g.value), gb.value
 
     def cyl_plan_set_timing(self, enable: bool):
         _check(load().cyl_plan_set_timing(self.h, int(enable)), "cyl_plan_set_timing")

@@ -1,6 +1,7 @@
 """Stored segment records (cyl_plan_set_records): SART subsets that replay each pose's
-pieces instead of walking the rays, against the FP64 oracle and against the walking
-subsets.
+pieces instead of walking the rays, back-projecting either by gathering per voxel from
+the records' transpose (form 1) or by replaying the records again into a numerator
+(form 2), against the FP64 oracle and against the walking subsets.
 
 The records round each piece's length to 20 mantissa bits (relative error <= 2^-21),
 so the FP32 bound of 1e-5 relative L2 per iterate still holds with margin; the walking
@@ -44,29 +45,38 @@ def tilted_scan(n_proj=8, det_w=77, det_h=45):
 def test_records_report_and_release(lib):
     s = tilted_scan(n_proj=3)
     with cylct.Plan(s) as plan:
-        assert plan.cyl_plan_records() == (False, 0)
+        assert plan.cyl_plan_records_full() == (False, 0, False, 0)
         base = plan.sizes()[3]
-        plan.cyl_plan_set_records(1)
-        ready, nbytes = plan.cyl_plan_records()
-        assert ready and nbytes > 0 and nbytes % 128 == 0
-        # about 4 bytes per piece: at least the exact piece count, padded to whole rows
         segs = int(gu.count_segments(plan).sum())
-        assert 4 * segs <= nbytes <= 4 * 32 * segs
-        assert plan.sizes()[3] >= base + nbytes
+        for form in (2, 1):
+            plan.cyl_plan_set_records(form)
+            ready, nbytes, gather, gbytes = plan.cyl_plan_records_full()
+            assert ready and nbytes > 0 and nbytes % 128 == 0
+            # about 4 bytes per piece: at least the exact piece count, padded to whole rows
+            assert 4 * segs <= nbytes <= 4 * 32 * segs
+            assert gather == (form == 1)
+            if gather:
+                # 8 bytes per piece (zero-length pieces included) and 4 per voxel and view
+                assert 8 * segs + 4 * (s.n_vox + 1) * s.n_proj <= gbytes
+                assert gbytes <= 8 * 2 * segs + 4 * (s.n_vox + 1) * s.n_proj
+            assert plan.sizes()[3] >= base + nbytes + gbytes
         plan.cyl_plan_set_records(0)
-        assert plan.cyl_plan_records() == (False, 0)
+        assert plan.cyl_plan_records_full() == (False, 0, False, 0)
         assert plan.sizes()[3] == base
         with pytest.raises(cylct.CylError):
-            plan.cyl_plan_set_records(2)
+            plan.cyl_plan_set_records(3)
         with pytest.raises(cylct.CylError):
             plan.cyl_plan_set_records(1, runs=3)
 
 
+@pytest.mark.parametrize("form", [1, 2])
 @pytest.mark.parametrize("runs", [0, 1, 4, 32])
 @pytest.mark.parametrize("kw", [dict(subset_size=1, clamp_nonneg=False, weight_mode=1),
                                 dict(subset_size=3, clamp_nonneg=True, weight_mode=1),
                                 dict(subset_size=2, clamp_nonneg=False, weight_mode=0, lam=0.2)])
-def test_records_sart_matches_oracle_and_walk(lib, orc, kw, runs):
+def test_records_sart_matches_oracle_and_walk(lib, orc, kw, runs, form):
+    # form 1: back-projection gathered per voxel from the records' transpose; form 2:
+    # replayed into a numerator with the pose's column sums
     s = tilted_scan()
     rng = np.random.default_rng(21)
     x0 = rng.uniform(0.0, 0.05, size=s.vol_shape)
@@ -77,8 +87,8 @@ def test_records_sart_matches_oracle_and_walk(lib, orc, kw, runs):
     ref = orc.sart(osetup(orc, s), p, x0=x0, w=w, n_iter=2, lam=lam, **kw)
     with cylct.Plan(s) as plan:
         walk = gu.sart(plan, p, x0=x0, w=w, n_iter=2, lam=lam, **kw)
-        plan.cyl_plan_set_records(1, runs=runs)
-        assert plan.cyl_plan_records()[0]
+        plan.cyl_plan_set_records(form, runs=runs)
+        assert plan.cyl_plan_records_full()[0] and plan.cyl_plan_records_full()[2] == (form == 1)
         got = gu.sart(plan, p, x0=x0, w=w, n_iter=2, lam=lam, **kw)
         eager = gu.sart(plan, p, x0=x0, w=w, n_iter=2, lam=lam, use_graph=False, **kw)
     assert gu.rel_l2(got, ref) <= TOL_FP32
@@ -86,8 +96,10 @@ def test_records_sart_matches_oracle_and_walk(lib, orc, kw, runs):
     assert gu.rel_l2(eager, got) <= 1e-6
 
 
-def test_records_follow_the_pose(lib, orc):
-    # a new pose rebuilds the records: the result equals a fresh plan's at that pose
+@pytest.mark.parametrize("form", [1, 2])
+def test_records_follow_the_pose(lib, orc, form):
+    # a new pose rebuilds the records (and their transpose): the result equals a fresh
+    # plan's at that pose
     s = tilted_scan(n_proj=5)
     s2 = dataclasses.replace(s, alpha=1.3, beta=-0.1, gamma=0.2, tx=-0.5, ty=0.9, tz=-0.2)
     rng = np.random.default_rng(5)
@@ -95,7 +107,7 @@ def test_records_follow_the_pose(lib, orc):
     p = rng.uniform(0.0, 1.0, size=s.sino_shape)
     ref = orc.sart(osetup(orc, s2), p, x0=x0, n_iter=2, lam=0.5)
     with cylct.Plan(s) as plan:
-        plan.cyl_plan_set_records(1)
+        plan.cyl_plan_set_records(form)
         gu.sart(plan, p, x0=x0, n_iter=1, lam=0.5)        # captures a sweep at the first pose
         plan.cyl_plan_set_pose((s2.alpha, s2.beta, s2.gamma, s2.tx, s2.ty, s2.tz))
         assert plan.cyl_plan_records()[0]
@@ -149,7 +161,8 @@ def test_records_compact_plan_walks(lib, orc):
     assert gu.rel_l2(got, orc.sart(osetup(orc, s), p, x0=x0, n_iter=2, lam=0.5)) <= TOL_FP32
 
 
-def test_records_medium_two_sweeps_per_iterate(lib, orc):
+@pytest.mark.parametrize("form", [1, 2])
+def test_records_medium_two_sweeps_per_iterate(lib, orc, form):
     # the medium workload at full size on 8 of its 180 views (as the walking test of the
     # same name): both sweeps against the FP64 oracle fed the FP32 values the GPU holds
     full = synth.medium_scan(synth.rng_for("medium"))
@@ -164,8 +177,8 @@ def test_records_medium_two_sweeps_per_iterate(lib, orc):
     ref1 = orc.sart(o, p, x0=x0, w=w, n_iter=1, lam=0.5)
     ref2 = orc.sart(o, p, x0=ref1, w=w, n_iter=1, lam=0.5)
     with cylct.Plan(s) as plan:
-        plan.cyl_plan_set_records(1)
-        assert plan.cyl_plan_records()[0]
+        plan.cyl_plan_set_records(form)
+        assert plan.cyl_plan_records_full()[0] and plan.cyl_plan_records_full()[2] == (form == 1)
         got1 = gu.sart(plan, p, x0=x0, w=w, n_iter=1, lam=0.5)
         got2 = gu.sart(plan, p, x0=x0, w=w, n_iter=2, lam=0.5)
     assert gu.rel_l2(got1, ref1) <= TOL_FP32
@@ -174,9 +187,10 @@ def test_records_medium_two_sweeps_per_iterate(lib, orc):
     assert gu.rel_l2(got2 - ref1, ref2 - ref1) <= TOL_FP32 * 10
 
 
+@pytest.mark.parametrize("form", [1, 2])
 @pytest.mark.parametrize("x_dt", [cylct.CYL_F16, cylct.CYL_BF16])
 @pytest.mark.parametrize("strict", [False, True])
-def test_records_tiny_16bit_storage(lib, orc, x_dt, strict):
+def test_records_tiny_16bit_storage(lib, orc, x_dt, strict, form):
     # as the walking test of 16-bit storage: the oracle gets the same 16-bit sinogram; the
     # strict mode (16-bit iterate rounded after every subset) against its looser bounds
     from test_gpu_parity import STRICT_BOUND, TOL_16
@@ -186,13 +200,14 @@ def test_records_tiny_16bit_storage(lib, orc, x_dt, strict):
     p16 = gu.to_np(gu.to_dev(orc.project(o, x_true), x_dt))
     ref = orc.sart(o, p16, n_iter=10, lam=0.5)
     with cylct.Plan(s) as plan:
-        plan.cyl_plan_set_records(1)
+        plan.cyl_plan_set_records(form)
         got = gu.sart(plan, p16, n_iter=10, lam=0.5, x_dt=x_dt, sino_dt=x_dt, strict_16bit=strict)
     err = gu.rel_l2(got, ref)
     assert err <= (STRICT_BOUND[x_dt] if strict else TOL_16), err
 
 
-def test_records_column_sums_follow_subset_size(lib, orc):
+@pytest.mark.parametrize("form", [1, 2])
+def test_records_column_sums_follow_subset_size(lib, orc, form):
     # the pose's column sums are kept per subset size: solves with subsets of 1, then 3,
     # then 1 view again each match the oracle
     s = tilted_scan(n_proj=7)
@@ -201,7 +216,7 @@ def test_records_column_sums_follow_subset_size(lib, orc):
     p = rng.uniform(0.0, 1.0, size=s.sino_shape)
     o = osetup(orc, s)
     with cylct.Plan(s) as plan:
-        plan.cyl_plan_set_records(1)
+        plan.cyl_plan_set_records(form)
         for ss in (1, 3, 1):
             got = gu.sart(plan, p, x0=x0, n_iter=2, lam=0.5, subset_size=ss)
             assert gu.rel_l2(got, orc.sart(o, p, x0=x0, n_iter=2, lam=0.5, subset_size=ss)) <= TOL_FP32, ss
