@@ -36,10 +36,11 @@ UNIT = "SART iters/s"
 N_ITER = 20
 # DRAM bytes (read + write) per launch of each kernel at the medium workload (one launch =
 # one view), from one ncu capture of the same kernels on the medium grid and detector
-# (k_rec_sart and k_update_rec4 on 8 of the 180 views; k_fp and k_bp, the two-launch
-# form, from an earlier capture of the same walks).
+# (k_rec_sart, k_update_rec4 and k_vox_sart1 on 8 of the 180 views; k_fp and k_bp, the
+# two-launch form, from an earlier capture of the same walks).  k_rec_sart is the fused
+# replay of the numerator form; the gather form's dominant kernel is k_vox_sart1.
 TRAFFIC: dict = {"k_sart": 183.69e6, "k_update_nd4": 115.70e6, "k_fp": 73.27e6, "k_bp": 82.10e6,
-                 "k_rec_sart": 181.85e6, "k_update_rec4": 122.61e6}
+                 "k_rec_sart": 181.85e6, "k_update_rec4": 122.61e6, "k_vox_sart1": 245.82e6}
 # DRAM bytes per scan of the corner pass on Table 1 scans (FP16), from one ncu capture of
 # 20 scans (profiles/pose_corners_table1.md); a launch's traffic scales with its scans.
 TRAFFIC_PER_SCAN: dict = {"k_corners": 2.5122e9 / 20}
@@ -377,7 +378,7 @@ def main():
             per = [fwd, back, upd]
         elif rec_ready and rec_gather:
             names = ["projection and residual from the stored segment records (k_rec_sart, forward replay)",
-                     None, "back-projection gathered per voxel with its column sums and the update (k_vox_sart)"]
+                     None, "back-projection gathered per voxel with its column sums and the update (k_vox_sart1)"]
             per = [fwd, 0.0, back + upd]
         elif rec_ready:
             names = ["projection, residual and back-projection from the stored segment records (k_rec_sart)",

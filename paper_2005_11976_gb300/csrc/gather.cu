@@ -47,16 +47,32 @@ __global__ void __launch_bounds__(256) k_vox_pieces(RecDev rd, int64_t t0, int64
         if (b > a) {   // per lane; the warp takes its next item together
             int idx = __ldg(rd.idx0 + (ray << lgP) + k);
             const uint32_t *rp = rd.rec + r0 * 32 + lane;
+            if (cnt) {
 #pragma unroll 4
-            for (int64_t s = a; s < b; ++s) {
-                const uint32_t v = __ldg(rp + s * 32);
-                if (cnt) {
+                for (int64_t s = a; s < b; ++s) {
+                    const uint32_t v = __ldg(rp + s * 32);
                     atomicAdd(cnt + idx, 1u);
-                } else {
-                    const uint32_t slot = atomicAdd(cur + idx, 1u);
-                    ent[slot] = make_uint2((uint32_t)pix, v & ~7u);
+                    idx += s_d[v & 7u];
                 }
-                idx += s_d[v & 7u];
+            } else {
+                // four slots taken before the four entries are written, so that the
+                // atomics' round trips overlap instead of each waiting on the last store
+                for (int64_t s = a; s < b; s += 4) {
+                    uint32_t v[4], slot[4];
+                    int id[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) v[i] = s + i < b ? __ldg(rp + (s + i) * 32) : 0u;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        id[i] = idx;
+                        idx += s_d[v[i] & 7u];
+                    }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) slot[i] = s + i < b ? atomicAdd(cur + id[i], 1u) : 0u;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        if (s + i < b) ent[slot[i]] = make_uint2((uint32_t)pix, v[i] & ~7u);
+                }
             }
         }
         __syncwarp();
@@ -170,34 +186,25 @@ __device__ __forceinline__ void vox_sums(const uint2 *__restrict__ ent, const fl
 // max(den_m, eps) where den_m > 0 (optionally x >= 0).  One view's den is summed in
 // FP32 (a voxel meets about two pieces of a view, each length carrying 20 mantissa bits,
 // so the sum is exact unless two of them differ by more than 16x); the views of a subset
-// add in FP64.  resid holds the subset's residuals, view by view.  ONE: a subset of one
-// view (the pointers of that view hoisted out of the voxel loop).
-template <class X, bool ONE>
+// add in FP64.  resid holds the subset's residuals, view by view.
+template <class X>
 __global__ void __launch_bounds__(256) k_vox_sart(VoxDev vd, int p0, int np, const float *__restrict__ resid,
                                                   UpdateArgs u)
 {
     const float sc = u.wscale ? *u.wscale : u.lambda;
     X *x16 = static_cast<X *>(u.x16);
-    const uint32_t *off1 = vd.off + (int64_t)p0 * (vd.n_vox + 1);
-    const uint2 *ent1 = vd.ent + __ldg(vd.ebase + p0);
     const uint32_t nv = (uint32_t)vd.n_vox, stride = gridDim.x * blockDim.x;
     for (uint32_t m = blockIdx.x * blockDim.x + threadIdx.x; m < nv; m += stride) {
-        float num = 0.f, d;
-        if (ONE) {
+        float num = 0.f;
+        double den = 0.0;
+        for (int v = 0; v < np; ++v) {
+            const uint32_t *off = vd.off + (int64_t)(p0 + v) * (vd.n_vox + 1);
             float dv = 0.f;
-            vox_sums(ent1, resid, __ldg(off1 + m), __ldg(off1 + m + 1), num, dv);
-            d = dv;
-        } else {
-            double den = 0.0;
-            for (int v = 0; v < np; ++v) {
-                const uint32_t *off = vd.off + (int64_t)(p0 + v) * (vd.n_vox + 1);
-                float dv = 0.f;
-                vox_sums(vd.ent + __ldg(vd.ebase + p0 + v), resid + (int64_t)v * vd.npix, __ldg(off + m),
-                         __ldg(off + m + 1), num, dv);
-                den += (double)dv;
-            }
-            d = (float)den;
+            vox_sums(vd.ent + __ldg(vd.ebase + p0 + v), resid + (int64_t)v * vd.npix, __ldg(off + m),
+                     __ldg(off + m + 1), num, dv);
+            den += (double)dv;
         }
+        const float d = (float)den;
         if (d > 0.f) {
             float xv = u.strict16 ? as_f32<X>(x16[m]) : u.x32[m];
             xv = fmaf(sc * weight_at(u, m), num / fmaxf(d, vd.eps), xv);
@@ -205,6 +212,83 @@ __global__ void __launch_bounds__(256) k_vox_sart(VoxDev vd, int p0, int np, con
             if (!u.strict16) u.x32[m] = xv;
             if (x16) x16[m] = from_f32r<X>(xv);
         }
+    }
+}
+
+// The same for a subset of one view (the kernel the default one-view subsets run),
+// software-pipelined: while voxel m is summed, the offsets of voxel m + 2s (s: the grid's
+// thread count) and the first kVoxQ entries, x and w of voxel m + s are already on their
+// way, so a thread keeps three voxels' loads in flight instead of waiting on the offsets
+// -> entries -> residuals chain of each.  The pieces are summed in entry order, as above
+// (same rounding).
+constexpr int kVoxQ = 4;
+
+template <class X>
+__global__ void __launch_bounds__(256, 5) k_vox_sart1(VoxDev vd, int p0, const float *__restrict__ resid,
+                                                       UpdateArgs u)
+{
+    const float sc = u.wscale ? *u.wscale : u.lambda;
+    X *x16 = static_cast<X *>(u.x16);
+    const uint32_t *off = vd.off + (int64_t)p0 * (vd.n_vox + 1);
+    const uint2 *ent = vd.ent + __ldg(vd.ebase + p0);
+    const uint32_t nv = (uint32_t)vd.n_vox, stride = gridDim.x * blockDim.x;
+    uint32_t m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= nv) return;   // no barrier below
+    auto x_at = [&](uint32_t i) { return u.strict16 ? as_f32<X>(x16[i]) : u.x32[i]; };
+    uint32_t a0 = __ldg(off + m), a1 = __ldg(off + m + 1), b0 = 0, b1 = 0;
+    if (m + stride < nv) {
+        b0 = __ldg(off + m + stride);
+        b1 = __ldg(off + m + stride + 1);
+    }
+    uint2 q[kVoxQ];
+#pragma unroll
+    for (int k = 0; k < kVoxQ; ++k) q[k] = a0 + k < a1 ? __ldg(ent + a0 + k) : make_uint2(0u, 0u);
+    float xv = x_at(m), wv = weight_at(u, m);
+    for (;;) {
+        const uint32_t mn = m + stride, mnn = mn + stride;
+        uint32_t c0 = 0, c1 = 0;
+        if (mnn < nv) {
+            c0 = __ldg(off + mnn);
+            c1 = __ldg(off + mnn + 1);
+        }
+        uint2 qn[kVoxQ];
+        float xn = 0.f, wn = 0.f;
+#pragma unroll
+        for (int k = 0; k < kVoxQ; ++k) qn[k] = make_uint2(0u, 0u);
+        if (mn < nv) {
+#pragma unroll
+            for (int k = 0; k < kVoxQ; ++k)
+                if (b0 + k < b1) qn[k] = __ldg(ent + b0 + k);
+            xn = x_at(mn);
+            wn = weight_at(u, mn);
+        }
+        float r[kVoxQ];
+#pragma unroll
+        for (int k = 0; k < kVoxQ; ++k) r[k] = a0 + k < a1 ? __ldg(resid + q[k].x) : 0.f;
+        float num = 0.f, den = 0.f;
+#pragma unroll
+        for (int k = 0; k < kVoxQ; ++k) {
+            const float t = __uint_as_float(q[k].y);   // 0 past the voxel's last piece
+            num = fmaf(t, r[k], num);
+            den += t;
+        }
+        if (a0 + kVoxQ < a1) vox_sums(ent, resid, a0 + kVoxQ, a1, num, den);
+        if (den > 0.f) {
+            xv = fmaf(sc * wv, num / fmaxf(den, vd.eps), xv);
+            if (u.clamp) xv = fmaxf(xv, 0.f);
+            if (!u.strict16) u.x32[m] = xv;
+            if (x16) x16[m] = from_f32r<X>(xv);
+        }
+        if (mn >= nv) break;
+        m = mn;
+        a0 = b0;
+        a1 = b1;
+        b0 = c0;
+        b1 = c1;
+#pragma unroll
+        for (int k = 0; k < kVoxQ; ++k) q[k] = qn[k];
+        xv = xn;
+        wv = wn;
     }
 }
 
@@ -257,8 +341,10 @@ cudaError_t launch_vox_sart(const VoxDev &vd, int p0, int np, const float *resid
     const cyl_dtype xt = u.x16 ? u.x16_t : CYL_F32;
     auto go = [&](auto *tx) {
         using X = std::remove_pointer_t<decltype(tx)>;
-        if (np == 1) k_vox_sart<X, true><<<blocks, 256, 0, st>>>(vd, p0, np, resid, u);
-        else k_vox_sart<X, false><<<blocks, 256, 0, st>>>(vd, p0, np, resid, u);
+        if (np == 1)
+            k_vox_sart1<X><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((vd.n_vox + 255) / 256, 152 * 5)),
+                             256, 0, st>>>(vd, p0, resid, u);
+        else k_vox_sart<X><<<blocks, 256, 0, st>>>(vd, p0, np, resid, u);
         return cudaGetLastError();
     };
     switch (xt) {
