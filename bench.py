@@ -40,7 +40,7 @@ N_ITER = 20
 # two-launch form, from an earlier capture of the same walks).  k_rec_sart is the fused
 # replay of the numerator form; the gather form's dominant kernel is k_vox_sart1.
 TRAFFIC: dict = {"k_sart": 183.69e6, "k_update_nd4": 115.70e6, "k_fp": 73.27e6, "k_bp": 82.10e6,
-                 "k_rec_sart": 181.85e6, "k_update_rec4": 122.61e6, "k_vox_sart1": 245.82e6}
+                 "k_rec_sart": 181.85e6, "k_update_rec4": 122.61e6, "k_vox_sart1": 229.23e6}
 # DRAM bytes per scan of the corner pass on Table 1 scans (FP16), from one ncu capture of
 # 20 scans (profiles/pose_corners_table1.md); a launch's traffic scales with its scans.
 TRAFFIC_PER_SCAN: dict = {"k_corners": 2.5122e9 / 20}

@@ -219,12 +219,13 @@ __global__ void __launch_bounds__(256) k_vox_sart(VoxDev vd, int p0, int np, con
 // software-pipelined: while voxel m is summed, the offsets of voxel m + 2s (s: the grid's
 // thread count) and the first kVoxQ entries, x and w of voxel m + s are already on their
 // way, so a thread keeps three voxels' loads in flight instead of waiting on the offsets
-// -> entries -> residuals chain of each.  The pieces are summed in entry order, as above
-// (same rounding).
+// -> entries -> residuals chain of each.  The offsets and entries are read once per sweep
+// and loaded evict-first, so that L2 keeps x, w and the residuals for the next subset's
+// kernels.  The pieces are summed in entry order, as above (same rounding).
 constexpr int kVoxQ = 4;
 
 template <class X>
-__global__ void __launch_bounds__(256, 5) k_vox_sart1(VoxDev vd, int p0, const float *__restrict__ resid,
+__global__ void __launch_bounds__(256, 6) k_vox_sart1(VoxDev vd, int p0, const float *__restrict__ resid,
                                                        UpdateArgs u)
 {
     const float sc = u.wscale ? *u.wscale : u.lambda;
@@ -235,21 +236,21 @@ __global__ void __launch_bounds__(256, 5) k_vox_sart1(VoxDev vd, int p0, const f
     uint32_t m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= nv) return;   // no barrier below
     auto x_at = [&](uint32_t i) { return u.strict16 ? as_f32<X>(x16[i]) : u.x32[i]; };
-    uint32_t a0 = __ldg(off + m), a1 = __ldg(off + m + 1), b0 = 0, b1 = 0;
+    uint32_t a0 = __ldcs(off + m), a1 = __ldcs(off + m + 1), b0 = 0, b1 = 0;
     if (m + stride < nv) {
-        b0 = __ldg(off + m + stride);
-        b1 = __ldg(off + m + stride + 1);
+        b0 = __ldcs(off + m + stride);
+        b1 = __ldcs(off + m + stride + 1);
     }
     uint2 q[kVoxQ];
 #pragma unroll
-    for (int k = 0; k < kVoxQ; ++k) q[k] = a0 + k < a1 ? __ldg(ent + a0 + k) : make_uint2(0u, 0u);
+    for (int k = 0; k < kVoxQ; ++k) q[k] = a0 + k < a1 ? __ldcs(ent + a0 + k) : make_uint2(0u, 0u);
     float xv = x_at(m), wv = weight_at(u, m);
     for (;;) {
         const uint32_t mn = m + stride, mnn = mn + stride;
         uint32_t c0 = 0, c1 = 0;
         if (mnn < nv) {
-            c0 = __ldg(off + mnn);
-            c1 = __ldg(off + mnn + 1);
+            c0 = __ldcs(off + mnn);
+            c1 = __ldcs(off + mnn + 1);
         }
         uint2 qn[kVoxQ];
         float xn = 0.f, wn = 0.f;
@@ -258,7 +259,7 @@ __global__ void __launch_bounds__(256, 5) k_vox_sart1(VoxDev vd, int p0, const f
         if (mn < nv) {
 #pragma unroll
             for (int k = 0; k < kVoxQ; ++k)
-                if (b0 + k < b1) qn[k] = __ldg(ent + b0 + k);
+                if (b0 + k < b1) qn[k] = __ldcs(ent + b0 + k);
             xn = x_at(mn);
             wn = weight_at(u, mn);
         }
@@ -342,7 +343,7 @@ cudaError_t launch_vox_sart(const VoxDev &vd, int p0, int np, const float *resid
     auto go = [&](auto *tx) {
         using X = std::remove_pointer_t<decltype(tx)>;
         if (np == 1)
-            k_vox_sart1<X><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((vd.n_vox + 255) / 256, 152 * 5)),
+            k_vox_sart1<X><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((vd.n_vox + 255) / 256, 152 * 6)),
                              256, 0, st>>>(vd, p0, resid, u);
         else k_vox_sart<X><<<blocks, 256, 0, st>>>(vd, p0, np, resid, u);
         return cudaGetLastError();

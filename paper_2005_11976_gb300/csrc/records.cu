@@ -213,7 +213,9 @@ __global__ void k_rec_inv4(int64_t n4, const float4 *__restrict__ den32, const d
 // from the first task's view on.  sched[0] hands out tasks to blocks; sched[1] counts
 // the blocks that found none left, and the last resets both.
 // Without BACK (the gather path, gather.cu) the kernel stops after the forward replay and
-// writes each ray's residual r_j to resid (the launch's views from the first one on).
+// writes each ray's residual r_j to resid (the launch's views from the first one on); its
+// records are then read once per subset and loaded evict-first (with BACK the backward
+// replay reads them again, from L1 or L2).
 template <class T, class S, bool BACK>
 __global__ void __launch_bounds__(1024)
 k_rec_sart(RecDev rd, int64_t t0, int64_t n_task, const T *__restrict__ x, const S *__restrict__ y, float *num,
@@ -248,7 +250,7 @@ k_rec_sart(RecDev rd, int64_t t0, int64_t n_task, const T *__restrict__ x, const
         float acc = 0.f, comp = 0.f;
 #pragma unroll 4
         for (int64_t s = a; s < b; ++s) {
-            const uint32_t v = __ldg(rp + s * 32);
+            const uint32_t v = BACK ? __ldg(rp + s * 32) : __ldcs(rp + s * 32);
             const float yv = fmaf(rec_len(v), as_f32<T>(__ldg(x + idx)), -comp);
             const float t = acc + yv;
             comp = (t - acc) - yv;
